@@ -1,0 +1,168 @@
+/*
+ * dv_api.h — C ABI of the B300 (sm_103a) differentiable-voxelization library.
+ *
+ * The library evaluates the generalized winding number of a triangle mesh,
+ *
+ *     w(q) = (1/4pi) * sum_f Omega_f(q),                       Eq. (5), Algorithm 1
+ *     Omega_f(q) = 2 * ATAN2(det(a,b,c), D),                   Eq. (7) with Eq. (8)
+ *     a = v0 - q, b = v1 - q, c = v2 - q,
+ *     D = |a||b||c| + (a.b)|c| + (b.c)|a| + (c.a)|b|,
+ *
+ * for every query point against every face (no hierarchy, §1), the
+ * binarised occupancy w > 0.5 (§2.1, Eq. (3); the threshold is this
+ * library's reading, the paper states none), and the adjoint
+ * dL/dV = sum_q (dL/dw_q) dw_q/dV that makes the voxelization
+ * differentiable (§1 contributions, §2.4).
+ *
+ * Conventions shared by every entry point:
+ *   - Buffers marked d_ are DEVICE pointers on the current CUDA device; the
+ *     caller owns and allocates them (for example through PyTorch). h_ marks
+ *     a host pointer. Nothing here takes ownership of a caller buffer.
+ *   - Vertices: float32 [nv][3], row-major. Faces: int32 [nf][3], indices into
+ *     the vertex array, counter-clockwise seen from outside (then w = +1 inside).
+ *   - Grids are cell-centred: x_i = lo + (i + 1/2)(hi - lo)/n per axis, and the
+ *     linear query index is (iz * ny + iy) * nx + ix (x fastest).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Every call is stream-ordered and returns without waiting for the GPU,
+ *     unless its comment says it synchronizes.
+ *   - Host-detectable errors (bad arguments, bad sizes) are returned
+ *     synchronously and nothing is enqueued. Launch errors are reported as
+ *     DV_ERR_CUDA. dv_last_error() gives a thread-local detail string.
+ *   - There is no CPU fallback: a call either runs on the GPU or fails.
+ *   - A dv_mesh owns scratch memory; calls on the same mesh must be ordered
+ *     (one stream, or explicit events). Different meshes are independent.
+ */
+#ifndef DV_API_H
+#define DV_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DV_ABI_VERSION 1
+
+typedef enum {
+    DV_OK = 0,
+    DV_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad grid, bad enum */
+    DV_ERR_INVALID_MESH = 2,  /* face index outside [0, nv) or non-finite vertex */
+    DV_ERR_OOM = 3,           /* device allocation for mesh storage/scratch failed */
+    DV_ERR_CUDA = 4,          /* a CUDA call or kernel launch failed */
+    DV_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out (see dv_mesh_check) */
+    DV_ERR_UNSUPPORTED = 6    /* valid request this build does not handle (e.g. size limits) */
+} dv_status;
+
+/* Arithmetic of the forward pass.
+ *   DV_PREC_FP32        FP32 per-pair terms, plain FP32 sum over faces.
+ *   DV_PREC_FP32_KAHAN  FP32 per-pair terms, compensated (Kahan) sum over blocks of faces.
+ *   DV_PREC_MIXED       DV_PREC_FP32_KAHAN, then every query with |w - 0.5| < 1e-3 or
+ *                       within 1e-3 (Euclidean) of a triangle is re-evaluated over all
+ *                       faces in FP64 on the GPU and its w / occupancy overwritten.
+ * The paper ran half precision (§3.1); these modes are this library's choice. */
+typedef enum { DV_PREC_FP32 = 0, DV_PREC_FP32_KAHAN = 1, DV_PREC_MIXED = 2 } dv_precision;
+
+/* Cell-centred voxel grid over the box [lo, hi] (§3: meshes normalized to [-1,1],
+ * resolutions 32..256; any n >= 1 per axis is accepted). */
+typedef struct {
+    float lo[3];
+    float hi[3];
+    int32_t n[3];
+} dv_grid;
+
+/* Opaque handle: packed per-face records resident on the device, the
+ * vertex-to-face adjacency used by the backward scatter, and scratch. */
+typedef struct dv_mesh dv_mesh;
+
+/* Filled by dv_voxelize_grid when a report is requested (that call then synchronizes). */
+typedef struct {
+    int64_t n_queries;           /* queries evaluated */
+    int64_t n_faces;             /* faces per query */
+    int64_t n_flagged;           /* queries selected for FP64 re-evaluation (DV_PREC_MIXED) */
+    int64_t n_occ_changed;       /* of those, how many changed occupancy after FP64 */
+    double max_abs_fp32_vs_fp64; /* max |w_fp32 - w_fp64| over the re-evaluated queries */
+} dv_report;
+
+/* Version of this ABI (DV_ABI_VERSION). */
+int dv_abi_version(void);
+
+/* Human-readable name of a status code. Never NULL. */
+const char *dv_status_string(dv_status s);
+
+/* Detail of the last error returned on the calling host thread ("" if none). */
+const char *dv_last_error(void);
+
+/* Algorithm 1 input "Mesh (V, F)": validate the faces (every index in [0, nv))
+ * and vertices (finite), then pack each face f into a per-face record
+ * (v0, v1, v2 and the face normal (v1-v0)x(v2-v0), FP32 and FP64 copies) and
+ * build the vertex-to-face adjacency. d_verts float32 [nv][3], d_faces int32 [nf][3]
+ * are read only during this call (the mesh keeps its own copies).
+ * SYNCHRONIZES `stream` once (validation result). nv >= 3, nf >= 1.
+ * On success *out receives a new handle; release it with dv_mesh_destroy. */
+dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,
+                         dv_mesh **out);
+
+/* Re-pack the face records from new vertex positions (same nv, same faces):
+ * the morphing loop of §2.4 moves vertices every step. Stream-ordered, no sync,
+ * no validation of finiteness. */
+dv_status dv_mesh_update_verts(dv_mesh *mesh, const float *d_verts, void *stream);
+
+/* Pre-size the mesh's scratch so that later forward/backward calls on `grid`
+ * (may be NULL) or on query lists of up to max_list_queries points allocate
+ * nothing (useful before timing or CUDA-graph capture). Without it, scratch
+ * grows on first use. Synchronous (cudaMalloc). */
+dv_status dv_mesh_reserve(dv_mesh *mesh, const dv_grid *grid, int64_t max_list_queries);
+
+/* Number of vertices / faces of a mesh (-1 if mesh is NULL). */
+int64_t dv_mesh_num_verts(const dv_mesh *mesh);
+int64_t dv_mesh_num_faces(const dv_mesh *mesh);
+
+/* Synchronize `stream` and report (then clear) the sticky device error word
+ * of the mesh: DV_ERR_TIMEOUT if a kernel's bounded wait ran out. */
+dv_status dv_mesh_check(dv_mesh *mesh, void *stream);
+
+/* Free the mesh and its scratch. Waits for the device (cudaFree). NULL is a no-op. */
+void dv_mesh_destroy(dv_mesh *mesh);
+
+/* Winding numbers w(q), Eq. (5), for either
+ *   - an explicit query list: d_queries float32 [nq][3] (grid must be NULL), or
+ *   - the voxel centres of *grid (d_queries must be NULL, nq = nx*ny*nz or 0).
+ * d_out_w float32 [nq]. `prec` as above. Stream-ordered, no sync. */
+dv_status dv_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid, float *d_out_w,
+                     dv_precision prec, void *stream);
+
+/* Voxelization (Algorithm 1 over a grid, §3): occupancy uint8 [nx*ny*nz]
+ * (1 where w > 0.5, else 0) and optionally w itself (d_out_w may be NULL).
+ * If report is non-NULL the call synchronizes `stream` and fills it. */
+dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_out_w, uint8_t *d_out_occ,
+                           dv_precision prec, dv_report *report, void *stream);
+
+/* Adjoint: d_dverts float32 [nv][3] is OVERWRITTEN with
+ *     sum_q d_upstream[q] * dw(q)/dV,
+ * the derivative of Eq. (5) with Eq. (7) (the paper claims differentiability,
+ * §1 and §2.4, but gives no formula; this is the analytic chain rule).
+ * Queries as in dv_winding (list or grid), d_upstream float32 [nq].
+ * FP32 per-pair arithmetic, FP64 cross-block reduction; deterministic
+ * (no floating-point atomics). Stream-ordered, no sync. */
+dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                              const float *d_upstream, float *d_dverts, void *stream);
+
+/* Per-kernel timing of this library's own launches, for measurement tools.
+ * dv_profile_enable(1) makes every later launch (on any stream) record a CUDA
+ * event pair on its own stream; dv_profile_read synchronizes on those events and
+ * copies up to `cap` entries: names[i] (static strings), total milliseconds,
+ * launch counts. Returns the number of distinct kernels. dv_profile_enable(0)
+ * stops recording; dv_profile_reset clears the totals. Not thread-safe. */
+void dv_profile_enable(int on);
+void dv_profile_reset(void);
+int dv_profile_read(const char **names, double *total_ms, int64_t *launches, int cap);
+
+/* Count of kernels this library has launched since load (all streams). */
+int64_t dv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DV_API_H */

@@ -13,6 +13,8 @@ Functions (each follows the passage named in ``oracle.c``):
 * ``grid_queries(lo, hi, n)``         cell-centred voxel grid (§3), x fastest
 * ``winding_grad(V, F, Q, g)``        sum_q g_q dW(q)/dV, chain rule through Eq. (7)
 * ``point_mesh_distance(V, F, Q)``    exact Euclidean distance to the nearest face
+* ``vertex_grad_subset(V, F, Q, g, ids)``  rows of winding_grad for selected vertices
+* ``winding_grad_scale(V, F, Q, g)``  per-vertex sum of |face contributions| (cancellation scale)
 * ``fd_vertex_grad(V, F, Q, g, ids)`` FP64 central differences of sum_q g_q W(q)
 * ``dipole_winding(V, F, Q)``         Eq. (4), naive dipole discretization
 * ``flipped_duplication(V, F, eps)``  Algorithm 2, open mesh to thin closed shell
@@ -66,6 +68,8 @@ def _load():
         lib.orc_point_mesh_distance.argtypes = mesh_q + [_d, ctypes.c_int]
         lib.orc_winding_grad.argtypes = mesh_q + [_d, _d, ctypes.c_int]
         lib.orc_fd_vertex_grad.argtypes = mesh_q + [_d, _i64, _I64, ctypes.c_double, _d, ctypes.c_int]
+        lib.orc_vertex_grad_subset.argtypes = mesh_q + [_d, _i64, _I64, _d, ctypes.c_int]
+        lib.orc_winding_grad_scale.argtypes = mesh_q + [_d, _d, ctypes.c_int]
         lib.orc_grid_queries.argtypes = [_f, _f, _i32, _d]
         _lib = lib
     return _lib
@@ -137,6 +141,17 @@ def winding_grad(V, F, Q, upstream, threads: int = 0) -> np.ndarray:
     return out
 
 
+def winding_grad_scale(V, F, Q, upstream, threads: int = 0) -> np.ndarray:
+    """Per vertex: sum over incident faces of the norm of that face's gradient contribution."""
+    V, F = _mesh(V, F)
+    Q = _q(Q)
+    g = np.ascontiguousarray(np.asarray(upstream, dtype=np.float64).reshape(-1))
+    out = np.zeros(len(V), dtype=np.float64)
+    _load().orc_winding_grad_scale(_dp(V), len(V), F.ctypes.data_as(_i32), len(F), _dp(Q), len(Q), _dp(g),
+                                   _dp(out), threads)
+    return out
+
+
 def fd_vertex_grad(V, F, Q, upstream, vertex_ids, h: float = 1e-4, threads: int = 0) -> np.ndarray:
     V, F = _mesh(V, F)
     Q = _q(Q)
@@ -145,6 +160,18 @@ def fd_vertex_grad(V, F, Q, upstream, vertex_ids, h: float = 1e-4, threads: int 
     out = np.zeros((len(ids), 3), dtype=np.float64)
     _load().orc_fd_vertex_grad(_dp(V), len(V), F.ctypes.data_as(_i32), len(F), _dp(Q), len(Q), _dp(g),
                                ids.ctypes.data_as(_i64), len(ids), float(h), _dp(out), threads)
+    return out
+
+
+def vertex_grad_subset(V, F, Q, upstream, vertex_ids, threads: int = 0) -> np.ndarray:
+    """Rows of ``winding_grad`` for the selected vertices only (incident faces, all queries)."""
+    V, F = _mesh(V, F)
+    Q = _q(Q)
+    g = np.ascontiguousarray(np.asarray(upstream, dtype=np.float64).reshape(-1))
+    ids = np.ascontiguousarray(np.asarray(vertex_ids, dtype=np.int64).reshape(-1))
+    out = np.zeros((len(ids), 3), dtype=np.float64)
+    _load().orc_vertex_grad_subset(_dp(V), len(V), F.ctypes.data_as(_i32), len(F), _dp(Q), len(Q), _dp(g),
+                                   ids.ctypes.data_as(_i64), len(ids), _dp(out), threads)
     return out
 
 

@@ -16,6 +16,8 @@
  *   orc_winding_grad     derivative of Eq. (5)+(7) by the chain rule through
  *                        the normalized vectors e_j (the paper claims
  *                        differentiability, §1 and §2.4, but prints no formula)
+ *   orc_vertex_grad_subset   the same derivative for selected vertices only
+ *   orc_winding_grad_scale   per vertex, sum over incident faces of |face contribution|
  *   orc_point_mesh_distance   exact point-to-triangle Euclidean distance
  *   orc_fd_vertex_grad   central finite differences of Eq. (5) in FP64
  *   orc_dipole_winding   Eq. (4), the naive dipole discretization (§2.4)
@@ -183,6 +185,73 @@ void orc_winding_grad(const double *V, int64_t nv, const int32_t *F, int64_t nf,
         for (int j = 0; j < 3; ++j)
             for (int k = 0; k < 3; ++k) dV_out[3 * (int64_t)F[3 * f + j] + k] += fg[9 * f + 3 * j + k];
     free(fg);
+}
+
+/* Magnitude scale of the per-vertex gradient sums: for every vertex, the sum over its
+ * incident faces of the Euclidean norm of that face's contribution (same per-face sums as
+ * orc_winding_grad). A vertex whose faces' contributions cancel (on a closed part of a mesh
+ * the exact result is 0) can only be compared to a tolerance relative to this scale. */
+void orc_winding_grad_scale(const double *V, int64_t nv, const int32_t *F, int64_t nf, const double *Q, int64_t nq,
+                            const double *upstream, double *scale_out, int nthreads) {
+    set_threads(nthreads);
+    double *fg = (double *)calloc((size_t)nf * 9, sizeof(double));
+    if (!fg) return;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t f = 0; f < nf; ++f) {
+        double g[9] = {0};
+        for (int64_t i = 0; i < nq; ++i)
+            face_grad_add(vtx(V, F, f, 0), vtx(V, F, f, 1), vtx(V, F, f, 2), Q + 3 * i, upstream[i] / (4.0 * ORC_PI), g);
+        memcpy(fg + 9 * f, g, sizeof(g));
+    }
+    memset(scale_out, 0, sizeof(double) * (size_t)nv);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int j = 0; j < 3; ++j) {
+            const double *c = fg + 9 * f + 3 * j;
+            scale_out[F[3 * f + j]] += sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        }
+    free(fg);
+}
+
+/* The same derivative as orc_winding_grad, for selected vertices only: sums over
+ * every query and over the faces incident to each selected vertex. out is [nvid, 3]. */
+void orc_vertex_grad_subset(const double *V, int64_t nv, const int32_t *F, int64_t nf, const double *Q, int64_t nq,
+                            const double *upstream, const int64_t *vids, int64_t nvid, double *out, int nthreads) {
+    (void)nv;
+    set_threads(nthreads);
+    int64_t *inc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nf > 0 ? nf : 1));
+    int *corner = (int *)malloc(sizeof(int) * (size_t)(nf > 0 ? nf : 1));
+    if (!inc || !corner) {
+        free(inc);
+        free(corner);
+        return;
+    }
+    for (int64_t t = 0; t < nvid; ++t) {
+        int64_t vid = vids[t], ninc = 0;
+        for (int64_t f = 0; f < nf; ++f)
+            for (int j = 0; j < 3; ++j)
+                if (F[3 * f + j] == vid) {
+                    inc[ninc] = f;
+                    corner[ninc++] = j;
+                }
+        double s0 = 0, s1 = 0, s2 = 0;
+#pragma omp parallel for reduction(+ : s0, s1, s2) schedule(dynamic, 256)
+        for (int64_t i = 0; i < nq; ++i) {
+            for (int64_t m = 0; m < ninc; ++m) {
+                int64_t f = inc[m];
+                double g[9] = {0};
+                face_grad_add(vtx(V, F, f, 0), vtx(V, F, f, 1), vtx(V, F, f, 2), Q + 3 * i, upstream[i] / (4.0 * ORC_PI),
+                              g);
+                s0 += g[3 * corner[m]];
+                s1 += g[3 * corner[m] + 1];
+                s2 += g[3 * corner[m] + 2];
+            }
+        }
+        out[3 * t] = s0;
+        out[3 * t + 1] = s1;
+        out[3 * t + 2] = s2;
+    }
+    free(inc);
+    free(corner);
 }
 
 /* Distance from p to the segment [a, b]. */

@@ -1,0 +1,483 @@
+// Host side of the C ABI declared in include/dv_api.h: argument checks, the resident mesh
+// (packed face records + vertex adjacency + scratch), launch planning, error reporting and the
+// optional per-kernel event timing used by measurement tools.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dv_api.h"
+#include "dv_internal.cuh"
+
+// ------------------------------------------------------------------------------------------
+// Errors
+static thread_local std::string g_last_error;
+
+static dv_status fail(dv_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define DV_CUDA(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? DV_ERR_OOM : DV_ERR_CUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                   \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// Launch counting and optional event timing
+namespace dv {
+
+static std::atomic<int64_t> g_launches{0};
+static bool g_prof_on = false;
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof_pending;
+struct ProfTot {
+    const char *name;
+    double ms;
+    int64_t n;
+};
+static std::vector<ProfTot> g_prof_tot;
+static std::mutex g_prof_mu;
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(const char *name, cudaStream_t s) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r{name, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, s);
+    g_prof_pending.push_back(r);
+}
+
+void prof_end(const char *name, cudaStream_t s) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto it = g_prof_pending.rbegin(); it != g_prof_pending.rend(); ++it)
+        if (it->name == name) {
+            cudaEventRecord(it->b, s);
+            return;
+        }
+}
+
+}  // namespace dv
+
+// ------------------------------------------------------------------------------------------
+// Mesh
+struct dv_mesh {
+    int device = 0;
+    int num_sms = 148;
+    int64_t nv = 0, nf = 0;
+    int32_t *faces = nullptr;       // device copy [nf][3]
+    dv::FaceRec *rec = nullptr;     // [nf]
+    dv::FaceRec64 *rec64 = nullptr; // [nf]
+    int32_t *vtx_ptr = nullptr;     // [nv+1]
+    int32_t *vtx_corner = nullptr;  // [3 nf]
+    int *err = nullptr;             // sticky error word + small counters: [0]=err [1]=flag_count [2]=occ_changed [3]=maxdiff bits
+    // scratch, grown on demand
+    int64_t cap_q = 0;
+    float *ws_w = nullptr;
+    uint8_t *ws_near = nullptr;
+    int *ws_list = nullptr;
+    int64_t cap_partial = 0;  // float2 elements
+    float2 *ws_partial = nullptr;
+    int64_t cap_fg = 0;       // floats
+    float *ws_fg = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+dv_status grow(T *&p, int64_t &cap, int64_t need) {
+    if (need <= cap) return DV_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void **)&p, (size_t)need * sizeof(T));
+    if (e != cudaSuccess) {
+        p = nullptr;
+        return fail(DV_ERR_OOM, "cudaMalloc(%lld bytes) failed: %s", (long long)(need * (int64_t)sizeof(T)),
+                    cudaGetErrorString(e));
+    }
+    cap = need;
+    return DV_OK;
+}
+
+dv_status reserve_queries(dv_mesh *m, int64_t nq) {
+    if (nq <= m->cap_q) return DV_OK;
+    cudaFree(m->ws_w);
+    cudaFree(m->ws_near);
+    cudaFree(m->ws_list);
+    m->ws_w = nullptr;
+    m->ws_near = nullptr;
+    m->ws_list = nullptr;
+    m->cap_q = 0;
+    cudaError_t e = cudaMalloc((void **)&m->ws_w, (size_t)nq * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->ws_near, (size_t)nq);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->ws_list, (size_t)nq * sizeof(int));
+    if (e != cudaSuccess) return fail(DV_ERR_OOM, "scratch for %lld queries: %s", (long long)nq, cudaGetErrorString(e));
+    m->cap_q = nq;
+    return DV_OK;
+}
+
+dv_status check_grid(const dv_grid *g) {
+    for (int k = 0; k < 3; ++k) {
+        if (g->n[k] < 1) return fail(DV_ERR_INVALID_ARG, "grid n[%d] = %d < 1", k, g->n[k]);
+        if (!std::isfinite(g->lo[k]) || !std::isfinite(g->hi[k]) || !(g->hi[k] > g->lo[k]))
+            return fail(DV_ERR_INVALID_ARG, "grid axis %d needs finite lo < hi", k);
+    }
+    const int64_t q = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    if (q > (int64_t)INT32_MAX) return fail(DV_ERR_UNSUPPORTED, "grid has %lld cells (max 2^31-1)", (long long)q);
+    return DV_OK;
+}
+
+dv::GridF to_gridf(const dv_grid *g) {
+    dv::GridF f{};
+    for (int k = 0; k < 3; ++k) {
+        f.lo[k] = g->lo[k];
+        f.h[k] = (g->hi[k] - g->lo[k]) / (float)g->n[k];
+        f.n[k] = g->n[k];
+    }
+    return f;
+}
+
+dv::GridD to_gridd(const dv_grid *g) {
+    dv::GridD d{};
+    for (int k = 0; k < 3; ++k) {
+        d.lo[k] = (double)g->lo[k];
+        d.h[k] = ((double)g->hi[k] - (double)g->lo[k]) / (double)g->n[k];
+        d.n[k] = g->n[k];
+    }
+    return d;
+}
+
+// Shared argument checks for the query-list / grid choice. Sets *nq_out.
+dv_status check_queries(const dv_mesh *m, const float *q, int64_t nq, const dv_grid *g, int64_t *nq_out) {
+    if (!m) return fail(DV_ERR_INVALID_ARG, "mesh is NULL");
+    if ((q == nullptr) == (g == nullptr)) return fail(DV_ERR_INVALID_ARG, "pass exactly one of d_queries or grid");
+    if (g) {
+        dv_status s = check_grid(g);
+        if (s) return s;
+        const int64_t n = (int64_t)g->n[0] * g->n[1] * g->n[2];
+        if (nq != 0 && nq != n) return fail(DV_ERR_INVALID_ARG, "nq = %lld but the grid has %lld cells", (long long)nq,
+                                            (long long)n);
+        *nq_out = n;
+    } else {
+        if (nq < 1) return fail(DV_ERR_INVALID_ARG, "nq = %lld < 1", (long long)nq);
+        if (nq > (int64_t)INT32_MAX) return fail(DV_ERR_UNSUPPORTED, "nq = %lld exceeds 2^31-1", (long long)nq);
+        *nq_out = nq;
+    }
+    return DV_OK;
+}
+
+dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_grid *grid, float *w, uint8_t *occ,
+                      dv_precision prec, dv_report *report, cudaStream_t s) {
+    if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED)
+        return fail(DV_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    dv::GridF gf{};
+    if (grid) gf = to_gridf(grid);
+    const dv::FwdPlan plan = dv::plan_forward(nq, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
+    const bool mixed = prec == DV_PREC_MIXED;
+    dv_status st;
+    if (plan.nsplit > 1 && (st = grow(m->ws_partial, m->cap_partial, (int64_t)plan.nsplit * nq))) return st;
+    if ((mixed || w == nullptr) && (st = reserve_queries(m, nq))) return st;
+    if (w == nullptr) w = m->ws_w;
+    const dv::LaunchCtx ctx{s, m->err};
+    if (mixed) {
+        DV_CUDA(cudaMemsetAsync(m->err + 1, 0, 3 * sizeof(int), s));
+        if (!queries) DV_CUDA(cudaMemsetAsync(m->ws_near, 0, (size_t)nq, s));
+        DV_CUDA(dv::launch_near_surface(m->rec, m->nf, grid ? &gf : nullptr, queries, nq, m->ws_near, s));
+    }
+    int *list = mixed ? m->ws_list : nullptr;
+    int *count = mixed ? m->err + 1 : nullptr;
+    const uint8_t *nearf = mixed ? m->ws_near : nullptr;
+    DV_CUDA(dv::launch_forward(plan, m->rec, m->nf, grid ? &gf : nullptr, queries, nq, prec != DV_PREC_FP32,
+                               m->ws_partial, w, occ, nearf, list, count, ctx));
+    if (plan.nsplit > 1)
+        DV_CUDA(dv::launch_split_reduce(plan, m->ws_partial, nq, w, occ, nearf, list, count, s));
+    if (mixed) {
+        dv::GridD gd{};
+        if (grid) gd = to_gridd(grid);
+        DV_CUDA(dv::launch_reeval_fp64(m->rec64, m->nf, grid ? &gd : nullptr, queries, list, count, nq, w, occ,
+                                       (unsigned *)(m->err + 3), m->err + 2, m->num_sms, s));
+    }
+    if (report) {
+        int h[4] = {0, 0, 0, 0};
+        if (mixed) DV_CUDA(cudaMemcpyAsync(h, m->err, sizeof(h), cudaMemcpyDeviceToHost, s));
+        DV_CUDA(cudaStreamSynchronize(s));
+        report->n_queries = nq;
+        report->n_faces = m->nf;
+        report->n_flagged = h[1];
+        report->n_occ_changed = h[2];
+        float md;
+        std::memcpy(&md, &h[3], sizeof(md));
+        report->max_abs_fp32_vs_fp64 = mixed ? (double)md : 0.0;
+    }
+    return DV_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+int dv_abi_version(void) { return DV_ABI_VERSION; }
+
+const char *dv_status_string(dv_status s) {
+    switch (s) {
+        case DV_OK: return "DV_OK";
+        case DV_ERR_INVALID_ARG: return "DV_ERR_INVALID_ARG";
+        case DV_ERR_INVALID_MESH: return "DV_ERR_INVALID_MESH";
+        case DV_ERR_OOM: return "DV_ERR_OOM";
+        case DV_ERR_CUDA: return "DV_ERR_CUDA";
+        case DV_ERR_TIMEOUT: return "DV_ERR_TIMEOUT";
+        case DV_ERR_UNSUPPORTED: return "DV_ERR_UNSUPPORTED";
+    }
+    return "DV_ERR_UNKNOWN";
+}
+
+const char *dv_last_error(void) { return g_last_error.c_str(); }
+
+void dv_mesh_destroy(dv_mesh *m) {
+    if (!m) return;
+    DeviceGuard dg(m->device);
+    cudaFree(m->faces);
+    cudaFree(m->rec);
+    cudaFree(m->rec64);
+    cudaFree(m->vtx_ptr);
+    cudaFree(m->vtx_corner);
+    cudaFree(m->err);
+    cudaFree(m->ws_w);
+    cudaFree(m->ws_near);
+    cudaFree(m->ws_list);
+    cudaFree(m->ws_partial);
+    cudaFree(m->ws_fg);
+    delete m;
+}
+
+dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,
+                         dv_mesh **out) {
+    g_last_error.clear();
+    if (!out) return fail(DV_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d_verts || !d_faces) return fail(DV_ERR_INVALID_ARG, "vertex or face pointer is NULL");
+    if (nv < 3) return fail(DV_ERR_INVALID_ARG, "nv = %lld < 3", (long long)nv);
+    if (nf < 1) return fail(DV_ERR_INVALID_ARG, "nf = %lld < 1", (long long)nf);
+    if (nv > (int64_t)INT32_MAX || 3 * nf > (int64_t)INT32_MAX)
+        return fail(DV_ERR_UNSUPPORTED, "mesh too large (nv %lld, nf %lld)", (long long)nv, (long long)nf);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv_mesh *m = new dv_mesh();
+    m->nv = nv;
+    m->nf = nf;
+    cudaGetDevice(&m->device);
+    cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+    auto bail = [&](dv_status st) {
+        dv_mesh_destroy(m);
+        return st;
+    };
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc((void **)&m->faces, (size_t)nf * 3 * sizeof(int32_t));
+    if (!e) e = cudaMalloc((void **)&m->rec, (size_t)nf * sizeof(dv::FaceRec));
+    if (!e) e = cudaMalloc((void **)&m->rec64, (size_t)nf * sizeof(dv::FaceRec64));
+    if (!e) e = cudaMalloc((void **)&m->vtx_ptr, (size_t)(nv + 1) * sizeof(int32_t));
+    if (!e) e = cudaMalloc((void **)&m->vtx_corner, (size_t)nf * 3 * sizeof(int32_t));
+    if (!e) e = cudaMalloc((void **)&m->err, 4 * sizeof(int));
+    if (e) return bail(fail(DV_ERR_OOM, "mesh storage: %s", cudaGetErrorString(e)));
+    if ((e = cudaMemsetAsync(m->err, 0, 4 * sizeof(int), s))) return bail(fail(DV_ERR_CUDA, "%s", cudaGetErrorString(e)));
+    if ((e = dv::launch_validate(d_verts, nv, d_faces, nf, m->err, s)))
+        return bail(fail(DV_ERR_CUDA, "validate: %s", cudaGetErrorString(e)));
+    int bad = 0;
+    std::vector<int32_t> hf((size_t)nf * 3);
+    if ((e = cudaMemcpyAsync(&bad, m->err, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(hf.data(), d_faces, hf.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
+    if (bad == 1) return bail(fail(DV_ERR_INVALID_MESH, "a face index is outside [0, %lld)", (long long)nv));
+    if (bad == 2) return bail(fail(DV_ERR_INVALID_MESH, "a vertex coordinate is not finite"));
+    // vertex -> (face, corner) adjacency, CSR, in face order (deterministic gather)
+    std::vector<int32_t> ptr((size_t)nv + 1, 0), corner((size_t)nf * 3);
+    for (int64_t i = 0; i < 3 * nf; ++i) ptr[(size_t)hf[i] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t i = 0; i < 3 * nf; ++i) corner[(size_t)fill[hf[i]]++] = (int32_t)i;
+    if ((e = cudaMemcpyAsync(m->vtx_ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(m->vtx_corner, corner.data(), corner.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             s)) ||
+        (e = cudaMemcpyAsync(m->faces, d_faces, (size_t)nf * 3 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)))
+        return bail(fail(DV_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e)));
+    if ((e = dv::launch_pack(d_verts, m->faces, nf, m->rec, m->rec64, s)))
+        return bail(fail(DV_ERR_CUDA, "pack: %s", cudaGetErrorString(e)));
+    // the host vectors above must outlive the async uploads
+    if ((e = cudaStreamSynchronize(s))) return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
+    *out = m;
+    return DV_OK;
+}
+
+dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
+    if (!m || !d_verts) return fail(DV_ERR_INVALID_ARG, "mesh or vertex pointer is NULL");
+    DeviceGuard dg(m->device);
+    DV_CUDA(dv::launch_pack(d_verts, m->faces, m->nf, m->rec, m->rec64, (cudaStream_t)stream));
+    return DV_OK;
+}
+
+dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_queries) {
+    if (!m || max_list_queries < 0) return fail(DV_ERR_INVALID_ARG, "bad reserve arguments");
+    DeviceGuard dg(m->device);
+    dv_status st;
+    int64_t nq = max_list_queries, part = 0, fg = 0;
+    if (max_list_queries > 0) {
+        const dv::FwdPlan fp = dv::plan_forward(max_list_queries, m->nf, false, nullptr, m->num_sms);
+        const dv::BwdPlan bp = dv::plan_backward(max_list_queries, m->nf, false, nullptr, m->num_sms);
+        part = fp.nsplit > 1 ? (int64_t)fp.nsplit * max_list_queries : 0;
+        fg = (int64_t)bp.nsplit * m->nf * 9;
+    }
+    if (grid) {
+        if ((st = check_grid(grid))) return st;
+        const dv::GridF gf = to_gridf(grid);
+        const int64_t gq = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
+        const dv::FwdPlan fp = dv::plan_forward(gq, m->nf, true, &gf, m->num_sms);
+        const dv::BwdPlan bp = dv::plan_backward(gq, m->nf, true, &gf, m->num_sms);
+        nq = std::max(nq, gq);
+        part = std::max(part, fp.nsplit > 1 ? (int64_t)fp.nsplit * gq : (int64_t)0);
+        fg = std::max(fg, (int64_t)bp.nsplit * m->nf * 9);
+    }
+    if ((st = reserve_queries(m, nq))) return st;
+    if (part > 0 && (st = grow(m->ws_partial, m->cap_partial, part))) return st;
+    if (fg > 0 && (st = grow(m->ws_fg, m->cap_fg, fg))) return st;
+    return DV_OK;
+}
+
+int64_t dv_mesh_num_verts(const dv_mesh *m) { return m ? m->nv : -1; }
+int64_t dv_mesh_num_faces(const dv_mesh *m) { return m ? m->nf : -1; }
+
+dv_status dv_mesh_check(dv_mesh *m, void *stream) {
+    if (!m) return fail(DV_ERR_INVALID_ARG, "mesh is NULL");
+    DeviceGuard dg(m->device);
+    int code = 0;
+    DV_CUDA(cudaMemcpyAsync(&code, m->err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    DV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (code) {
+        DV_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), (cudaStream_t)stream));
+        DV_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+        return fail((dv_status)code, "device error word was %d", code);
+    }
+    return DV_OK;
+}
+
+dv_status dv_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid, float *d_out_w,
+                     dv_precision prec, void *stream) {
+    int64_t n = 0;
+    dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
+    if (st) return st;
+    if (!d_out_w) return fail(DV_ERR_INVALID_ARG, "d_out_w is NULL");
+    dv_mesh *m = const_cast<dv_mesh *>(mesh);
+    DeviceGuard dg(m->device);
+    return run_forward(m, d_queries, n, grid, d_out_w, nullptr, prec, nullptr, (cudaStream_t)stream);
+}
+
+dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_out_w, uint8_t *d_out_occ,
+                           dv_precision prec, dv_report *report, void *stream) {
+    int64_t n = 0;
+    if (!grid) return fail(DV_ERR_INVALID_ARG, "grid is NULL");
+    dv_status st = check_queries(mesh, nullptr, 0, grid, &n);
+    if (st) return st;
+    if (!d_out_occ) return fail(DV_ERR_INVALID_ARG, "d_out_occ is NULL");
+    dv_mesh *m = const_cast<dv_mesh *>(mesh);
+    DeviceGuard dg(m->device);
+    return run_forward(m, nullptr, n, grid, d_out_w, d_out_occ, prec, report, (cudaStream_t)stream);
+}
+
+dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                              const float *d_upstream, float *d_dverts, void *stream) {
+    int64_t n = 0;
+    dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
+    if (st) return st;
+    if (!d_upstream || !d_dverts) return fail(DV_ERR_INVALID_ARG, "d_upstream or d_dverts is NULL");
+    dv_mesh *m = const_cast<dv_mesh *>(mesh);
+    DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::GridF gf{};
+    if (grid) gf = to_gridf(grid);
+    const dv::BwdPlan plan = dv::plan_backward(n, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
+    if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)plan.nsplit * m->nf * 9))) return st;
+    const dv::LaunchCtx ctx{s, m->err};
+    DV_CUDA(dv::launch_backward(plan, m->rec, m->nf, grid ? &gf : nullptr, d_queries, n, d_upstream, m->ws_fg, ctx));
+    DV_CUDA(dv::launch_gather_dverts(nullptr, m->ws_fg, plan.nsplit, m->nf, m->vtx_ptr, m->vtx_corner, m->nv, d_dverts,
+                                     s));
+    return DV_OK;
+}
+
+void dv_profile_enable(int on) { dv::g_prof_on = on != 0; }
+
+void dv_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(dv::g_prof_mu);
+    for (auto &r : dv::g_prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    dv::g_prof_pending.clear();
+    dv::g_prof_tot.clear();
+}
+
+int dv_profile_read(const char **names, double *total_ms, int64_t *launches, int cap) {
+    std::lock_guard<std::mutex> lk(dv::g_prof_mu);
+    for (auto &r : dv::g_prof_pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) ms = 0.f;
+        auto it = std::find_if(dv::g_prof_tot.begin(), dv::g_prof_tot.end(),
+                               [&](const dv::ProfTot &t) { return std::strcmp(t.name, r.name) == 0; });
+        if (it == dv::g_prof_tot.end())
+            dv::g_prof_tot.push_back({r.name, (double)ms, 1});
+        else {
+            it->ms += ms;
+            it->n += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    dv::g_prof_pending.clear();
+    const int n = (int)dv::g_prof_tot.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (names) names[i] = dv::g_prof_tot[i].name;
+        if (total_ms) total_ms[i] = dv::g_prof_tot[i].ms;
+        if (launches) launches[i] = dv::g_prof_tot[i].n;
+    }
+    return n;
+}
+
+int64_t dv_launch_count(void) { return dv::g_launches.load(); }
+
+}  // extern "C"

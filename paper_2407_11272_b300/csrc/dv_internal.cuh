@@ -1,0 +1,190 @@
+// Internal declarations shared by the CUDA sources of libdv (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "atan_poly.h"
+
+namespace dv {
+
+constexpr float kInv2Pi = 0.15915494309189535f;  // w = (1/4pi) sum Omega = (1/2pi) sum ATAN2
+constexpr double kInv2PiD = 0.15915494309189533576888;
+constexpr float kNearDist = 1e-3f;    // re-evaluate queries within this distance of a triangle
+constexpr float kThreshBand = 1e-3f;  // ... or with |w - 0.5| below this
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded mbarrier waits: give up after 2 s
+
+// Per-face FP32 record, 48 bytes = 3 x float4:
+//   r0 = (v0.x, v0.y, v0.z, 4 n.x), r1 = (v1.x, v1.y, v1.z, 4 n.y), r2 = (v2.x, v2.y, v2.z, 4 n.z)
+// with n = (v1 - v0) x (v2 - v0). The factor 4 (exact) lets the forward kernel test
+// |N| < D/4 as one comparison and feed 4N/D straight into its arctangent polynomial.
+struct FaceRec {
+    float4 r0, r1, r2;
+};
+static_assert(sizeof(FaceRec) == 48, "face record must be 48 bytes (TMA bulk copies need 16B multiples)");
+
+// Per-face FP64 record for the re-evaluation pass: v0, v1, v2, n (12 doubles, 96 bytes).
+struct FaceRec64 {
+    double v[12];
+};
+
+// Cell-centred grid, FP32 form used by the FP32 kernels: x = lo + (i + 0.5) * h.
+struct GridF {
+    float lo[3];
+    float h[3];
+    int n[3];
+};
+
+// FP64 form for the re-evaluation: x = lo + (i + 0.5) * (hi - lo) / n in double.
+struct GridD {
+    double lo[3];
+    double h[3];
+    int n[3];
+};
+
+// ------------------------------------------------------------------------------------------
+// Inline PTX: mbarrier + bulk async copy (TMA, non-tensor form) into this CTA's shared memory.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`, giving up after kWaitLimitNs (or limit_ns if smaller than
+// that). Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        for (int k = 0; k < 64; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared, completion signalled on `bar` as transaction bytes.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------------------------------------------
+// FP32 special-function approximations (MUFU): reciprocal and reciprocal square root.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Sticky error word: first error code wins.
+__device__ __forceinline__ void set_error(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+}  // namespace dv
+
+// ------------------------------------------------------------------------------------------
+// Host-side launch wrappers implemented in the .cu files (C++ linkage, internal).
+namespace dv {
+
+struct LaunchCtx {
+    cudaStream_t stream;
+    int *d_err;  // sticky device error word (may be null)
+};
+
+// Kernel-profiling hooks (dv_api.cu): bracket one launch with events when enabled.
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(const char *name, cudaStream_t s);
+void count_launch();
+
+// pack.cu
+cudaError_t launch_validate(const float *verts, int64_t nv, const int32_t *faces, int64_t nf, int *d_bad,
+                            cudaStream_t s);
+cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, FaceRec *rec, FaceRec64 *rec64,
+                        cudaStream_t s);
+cudaError_t launch_gather_dverts(const double *unused, const float *face_grad, int nsplit, int64_t nf,
+                                 const int32_t *vtx_ptr, const int32_t *vtx_corner, int64_t nv, float *dverts,
+                                 cudaStream_t s);
+
+// winding_fwd.cu
+struct FwdPlan {
+    int qx, qy;          // queries per thread along x and along y (grid kernels)
+    int threads;         // CTA size
+    int64_t qblocks;     // CTAs over queries
+    int nsplit;          // face splits (grid dimension y); 1 = no split
+    int64_t faces_per_split;
+};
+FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms);
+cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
+                           int64_t nq, bool kahan, float2 *partial, float *w_out, uint8_t *occ_out,
+                           const uint8_t *near_flag, int *flag_list, int *flag_count, const LaunchCtx &ctx);
+cudaError_t launch_split_reduce(const FwdPlan &p, const float2 *partial, int64_t nq, float *w_out, uint8_t *occ_out,
+                                const uint8_t *near_flag, int *flag_list, int *flag_count, cudaStream_t s);
+
+// near_surface.cu
+cudaError_t launch_near_surface(const FaceRec *rec, int64_t nf, const GridF *g, const float *queries, int64_t nq,
+                                uint8_t *near_flag, cudaStream_t s);
+
+// winding_fp64.cu
+cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const GridD *g, const float *queries,
+                               const int *flag_list, const int *flag_count, int64_t max_flagged, float *w_out,
+                               uint8_t *occ_out, unsigned *stat_maxdiff_bits, int *stat_occ_changed, int num_sms,
+                               cudaStream_t s);
+
+// winding_bwd.cu
+struct BwdPlan {
+    int threads;
+    int64_t fblocks;
+    int nsplit;
+    int64_t rows_per_split;  // grid: rows (z,y) per split; list: queries per split
+};
+BwdPlan plan_backward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms);
+cudaError_t launch_backward(const BwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
+                            int64_t nq, const float *upstream, float *face_grad, const LaunchCtx &ctx);
+
+}  // namespace dv

@@ -1,0 +1,107 @@
+// Mesh validation, per-face record packing (Algorithm 1: "f_i = (v0, v1, v2)") and the
+// deterministic vertex gather of the adjoint.
+#include <math.h>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+
+__global__ void validate_kernel(const float *__restrict__ verts, int64_t nv, const int32_t *__restrict__ faces,
+                                int64_t nf, int *bad) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nf; i += stride) {
+        int32_t k = faces[i];
+        if (k < 0 || (int64_t)k >= nv) atomicCAS(bad, 0, 1);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nv; i += stride) {
+        if (!isfinite(verts[i])) atomicCAS(bad, 0, 2);
+    }
+}
+
+// One thread per face: gather the three vertices, compute n = (v1 - v0) x (v2 - v0) in FP64
+// (products of FP32 values are exact in FP64), and store the FP32 record (normal scaled by 4)
+// and the FP64 record used by the re-evaluation pass.
+__global__ void pack_kernel(const float *__restrict__ verts, const int32_t *__restrict__ faces, int64_t nf,
+                            FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    double v[3][3];
+    for (int k = 0; k < 3; ++k) {
+        int64_t id = faces[3 * f + k];
+        for (int c = 0; c < 3; ++c) v[k][c] = (double)verts[3 * id + c];
+    }
+    double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+    double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    FaceRec r;
+    r.r0 = make_float4((float)v[0][0], (float)v[0][1], (float)v[0][2], (float)(4.0 * n[0]));
+    r.r1 = make_float4((float)v[1][0], (float)v[1][1], (float)v[1][2], (float)(4.0 * n[1]));
+    r.r2 = make_float4((float)v[2][0], (float)v[2][1], (float)v[2][2], (float)(4.0 * n[2]));
+    rec[f] = r;
+    FaceRec64 r64;
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c) r64.v[3 * k + c] = v[k][c];
+    for (int c = 0; c < 3; ++c) r64.v[9 + c] = n[c];
+    rec64[f] = r64;
+}
+
+// dverts[v] = sum over the faces f incident to v (corner k) and over the query splits s of
+// face_grad[s][f][3k..3k+2], summed in FP64 in a fixed order (deterministic).
+__global__ void gather_dverts_kernel(const float *__restrict__ face_grad, int nsplit, int64_t nf,
+                                     const int32_t *__restrict__ vtx_ptr, const int32_t *__restrict__ vtx_corner,
+                                     int64_t nv, float *__restrict__ dverts) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int32_t c = vtx_ptr[v]; c < vtx_ptr[v + 1]; ++c) {
+        int32_t corner = vtx_corner[c];
+        int64_t f = corner / 3;
+        int k = corner - 3 * (int)f;
+        for (int s = 0; s < nsplit; ++s) {
+            const float *g = face_grad + ((int64_t)s * nf + f) * 9 + 3 * k;
+            s0 += (double)g[0];
+            s1 += (double)g[1];
+            s2 += (double)g[2];
+        }
+    }
+    dverts[3 * v + 0] = (float)s0;
+    dverts[3 * v + 1] = (float)s1;
+    dverts[3 * v + 2] = (float)s2;
+}
+
+static int blocks_for(int64_t n, int threads, int64_t cap = 1 << 20) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t launch_validate(const float *verts, int64_t nv, const int32_t *faces, int64_t nf, int *d_bad,
+                            cudaStream_t s) {
+    prof_begin("validate_mesh", s);
+    validate_kernel<<<blocks_for(3 * (nf > nv ? nf : nv), 256, 4096), 256, 0, s>>>(verts, nv, faces, nf, d_bad);
+    count_launch();
+    prof_end("validate_mesh", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, FaceRec *rec, FaceRec64 *rec64,
+                        cudaStream_t s) {
+    prof_begin("pack_faces", s);
+    pack_kernel<<<blocks_for(nf, 256), 256, 0, s>>>(verts, faces, nf, rec, rec64);
+    count_launch();
+    prof_end("pack_faces", s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_dverts(const double *, const float *face_grad, int nsplit, int64_t nf,
+                                 const int32_t *vtx_ptr, const int32_t *vtx_corner, int64_t nv, float *dverts,
+                                 cudaStream_t s) {
+    prof_begin("gather_dverts", s);
+    gather_dverts_kernel<<<blocks_for(nv, 256), 256, 0, s>>>(face_grad, nsplit, nf, vtx_ptr, vtx_corner, nv, dverts);
+    count_launch();
+    prof_end("gather_dverts", s);
+    return cudaGetLastError();
+}
+
+}  // namespace dv

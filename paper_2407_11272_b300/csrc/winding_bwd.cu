@@ -1,0 +1,327 @@
+// Adjoint of the winding number: dL/dV = sum_q g_q dw(q)/dV.
+//
+// With a = v0 - q, b = v1 - q, c = v2 - q, N = a.n (n = (v1-v0)x(v2-v0)), D as in the forward,
+// Omega = 2 ATAN2(N, D) and w = (1/4pi) sum Omega:
+//   dw = (1/2pi) (D dN - N dD) / (N^2 + D^2)
+//   dN/da = b x c,  dN/db = c x a,  dN/dc = a x b
+//   dD/da = (a/|a|)(|b||c| + b.c) + b|c| + c|b|   (and cyclically)
+// No arctangent is needed. The kernel is face-parallel: each thread owns one face, streams the
+// queries (uniform across the warp), and keeps the per-face gradient as a few scalar sums.
+// Writing b = e1 + a, c = e2 + a (e1 = v1 - v0, e2 = v2 - v0), every per-query vector term is
+// (scalar) x a or a constant vector, so per face only these sums are needed:
+//   T_cD = sum cD, T_P = sum cN|a|, T_Q = sum cN|b|, T_R = sum cN|c|,
+//   T_ab = sum alpha_b, T_ac = sum alpha_c,
+//   U_cD = sum cD a, U_a = sum W_a a, U_b = sum W_b a, U_c = sum W_c a,
+// with cD = g D/(N^2+D^2), cN = g N/(N^2+D^2), alpha_a = cN (|b||c| + b.c)/|a| (cyclic),
+// W_a = alpha_a + T_R-term + T_Q-term etc. Then
+//   dL/dv0 = k [T_cD n + (e1 - e2) x U_cD - T_R e1 - T_Q e2 - U_a]
+//   dL/dv1 = k [e2 x U_cD - T_ab e1 - T_P e2 - U_b]
+//   dL/dv2 = k [-e1 x U_cD - T_P e1 - T_ac e2 - U_c],   k = 1/(2 pi).
+// On a grid row (fixed y, z) the y and z parts of a are constant, so the sums over a row are
+// kept as 7 scalars and their x-weighted versions (14 FMAs per pair) and folded per row.
+// Per-face sums are FP32 with Kahan compensation; per-split face gradients are summed over
+// splits and incident faces in FP64 by the gather kernel (pack.cu), in a fixed order.
+#include <math.h>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+
+constexpr int kBwdThreads = 128;
+constexpr int kBwdWin = 4096;  // queries staged per window
+
+struct BwdArgs {
+    const FaceRec *rec;
+    int64_t nf;
+    GridF g;
+    const float *queries;
+    int64_t nq;
+    const float *upstream;
+    int64_t rows_per_split;  // grid: rows; list: queries
+    float *face_grad;        // [nsplit][nf][9]
+    int *err;
+};
+
+struct FaceF {
+    float v0x, v0y, v0z, v1x, v1y, v1z, v2x, v2y, v2z, nx, ny, nz;
+};
+
+struct RowB {
+    float ay, az, La, Lb, Lc, Pab, Pbc, Pca, Nyz;
+};
+
+__device__ __forceinline__ RowB row_b(const FaceF &F, float qy, float qz) {
+    RowB r;
+    r.ay = F.v0y - qy;
+    r.az = F.v0z - qz;
+    const float by = F.v1y - qy, bz = F.v1z - qz, cy = F.v2y - qy, cz = F.v2z - qz;
+    r.La = fmaf(r.ay, r.ay, r.az * r.az);
+    r.Lb = fmaf(by, by, bz * bz);
+    r.Lc = fmaf(cy, cy, cz * cz);
+    r.Pab = fmaf(r.ay, by, r.az * bz);
+    r.Pbc = fmaf(by, cy, bz * cz);
+    r.Pca = fmaf(cy, r.ay, cz * r.az);
+    r.Nyz = fmaf(r.ay, F.ny, r.az * F.nz);
+    return r;
+}
+
+// One pair: accumulate the 7 row scalars S and their x-weighted versions X.
+template <bool GUARD>
+__device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx, float g, float (&S)[7],
+                                         float (&X)[7]) {
+    const float ax = F.v0x - qx, bx = F.v1x - qx, cx = F.v2x - qx;
+    float la2 = fmaf(ax, ax, R.La), lb2 = fmaf(bx, bx, R.Lb), lc2 = fmaf(cx, cx, R.Lc);
+    if (GUARD) {
+        la2 = fmaxf(la2, 1e-30f);
+        lb2 = fmaxf(lb2, 1e-30f);
+        lc2 = fmaxf(lc2, 1e-30f);
+    }
+    const float ia = rsqrt_approx(la2), ib = rsqrt_approx(lb2), ic = rsqrt_approx(lc2);
+    const float la = la2 * ia, lb = lb2 * ib, lc = lc2 * ic;
+    const float ab = fmaf(ax, bx, R.Pab), bc = fmaf(bx, cx, R.Pbc), ca = fmaf(cx, ax, R.Pca);
+    const float N = fmaf(ax, F.nx, R.Nyz);
+    float D = la * lb * lc;
+    D = fmaf(ab, lc, D);
+    D = fmaf(bc, la, D);
+    D = fmaf(ca, lb, D);
+    const float den = fmaf(N, N, D * D);
+    float r = rcp_approx(den);
+    if (GUARD) r = den >= 1.17549435e-38f ? r : 0.0f;
+    const float gr = g * r;
+    const float cD = gr * D, cN = gr * N;
+    const float P = cN * la, Qb = cN * lb, Rc = cN * lc;
+    const float alA = cN * (fmaf(lb, lc, bc) * ia);
+    const float alB = cN * (fmaf(lc, la, ca) * ib);
+    const float alC = cN * (fmaf(la, lb, ab) * ic);
+    S[0] += cD;
+    S[1] += P;
+    S[2] += Qb;
+    S[3] += Rc;
+    S[4] += alA;
+    S[5] += alB;
+    S[6] += alC;
+    X[0] = fmaf(cD, ax, X[0]);
+    X[1] = fmaf(P, ax, X[1]);
+    X[2] = fmaf(Qb, ax, X[2]);
+    X[3] = fmaf(Rc, ax, X[3]);
+    X[4] = fmaf(alA, ax, X[4]);
+    X[5] = fmaf(alB, ax, X[5]);
+    X[6] = fmaf(alC, ax, X[6]);
+}
+
+struct Kahan {
+    float s, c;
+    __device__ __forceinline__ void add(float x) {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+};
+
+// Per-face sums: T[0..5] = T_cD, T_P, T_Q, T_R, T_ab, T_ac; U[0..3][3] = U_cD, U_a, U_b, U_c.
+struct FaceSums {
+    Kahan T[6];
+    Kahan U[4][3];
+    __device__ __forceinline__ void zero() {
+        for (int i = 0; i < 6; ++i) T[i].s = T[i].c = 0.f;
+        for (int i = 0; i < 4; ++i)
+            for (int k = 0; k < 3; ++k) U[i][k].s = U[i][k].c = 0.f;
+    }
+    // Fold one row's sums (row constants ay, az).
+    __device__ __forceinline__ void fold(const float (&S)[7], const float (&X)[7], float ay, float az) {
+        T[0].add(S[0]);
+        T[1].add(S[1]);
+        T[2].add(S[2]);
+        T[3].add(S[3]);
+        T[4].add(S[5]);
+        T[5].add(S[6]);
+        const float ws[4] = {S[0], S[4] + S[3] + S[2], S[5] + S[1] + S[3], S[6] + S[2] + S[1]};
+        const float wx[4] = {X[0], X[4] + X[3] + X[2], X[5] + X[1] + X[3], X[6] + X[2] + X[1]};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            U[i][0].add(wx[i]);
+            U[i][1].add(ay * ws[i]);
+            U[i][2].add(az * ws[i]);
+        }
+    }
+};
+
+__device__ __forceinline__ FaceF load_face(const FaceRec *rec, int64_t f) {
+    const FaceRec r = rec[f];
+    FaceF F;
+    F.v0x = r.r0.x; F.v0y = r.r0.y; F.v0z = r.r0.z;
+    F.v1x = r.r1.x; F.v1y = r.r1.y; F.v1z = r.r1.z;
+    F.v2x = r.r2.x; F.v2y = r.r2.y; F.v2z = r.r2.z;
+    F.nx = 0.25f * r.r0.w; F.ny = 0.25f * r.r1.w; F.nz = 0.25f * r.r2.w;
+    return F;
+}
+
+// Combine the face sums into the 9 gradient components (FP64 arithmetic) and store them.
+__device__ __forceinline__ void write_face_grad(const FaceF &F, const FaceSums &fs, float *out) {
+    double T[6], U[4][3];
+    for (int i = 0; i < 6; ++i) T[i] = (double)fs.T[i].s - (double)fs.T[i].c;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) U[i][k] = (double)fs.U[i][k].s - (double)fs.U[i][k].c;
+    const double e1[3] = {(double)F.v1x - F.v0x, (double)F.v1y - F.v0y, (double)F.v1z - F.v0z};
+    const double e2[3] = {(double)F.v2x - F.v0x, (double)F.v2y - F.v0y, (double)F.v2z - F.v0z};
+    const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double *u = U[0];
+    const double d[3] = {e1[0] - e2[0], e1[1] - e2[1], e1[2] - e2[2]};
+    const double dxu[3] = {d[1] * u[2] - d[2] * u[1], d[2] * u[0] - d[0] * u[2], d[0] * u[1] - d[1] * u[0]};
+    const double e2xu[3] = {e2[1] * u[2] - e2[2] * u[1], e2[2] * u[0] - e2[0] * u[2], e2[0] * u[1] - e2[1] * u[0]};
+    const double e1xu[3] = {e1[1] * u[2] - e1[2] * u[1], e1[2] * u[0] - e1[0] * u[2], e1[0] * u[1] - e1[1] * u[0]};
+    for (int k = 0; k < 3; ++k) {
+        const double g0 = T[0] * n[k] + dxu[k] - T[3] * e1[k] - T[2] * e2[k] - U[1][k];
+        const double g1 = e2xu[k] - T[4] * e1[k] - T[1] * e2[k] - U[2][k];
+        const double g2 = -e1xu[k] - T[1] * e1[k] - T[5] * e2[k] - U[3][k];
+        out[k] = (float)(g0 * kInv2PiD);
+        out[3 + k] = (float)(g1 * kInv2PiD);
+        out[6 + k] = (float)(g2 * kInv2PiD);
+    }
+}
+
+__device__ __forceinline__ bool all_finite(const float (&S)[7], const float (&X)[7]) {
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) t += S[i] + X[i];
+    return isfinite(t);
+}
+
+__global__ void __launch_bounds__(kBwdThreads) bwd_grid_kernel(const BwdArgs a) {
+    __shared__ float2 win[kBwdWin];  // (upstream g, query x) of the staged queries
+    const int64_t f = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    const FaceF F = load_face(a.rec, f < a.nf ? f : a.nf - 1);
+    const int nx = a.g.n[0], ny = a.g.n[1];
+    const int64_t nrows = (int64_t)a.g.n[1] * a.g.n[2];
+    const int64_t r0 = (int64_t)blockIdx.y * a.rows_per_split;
+    const int64_t r1 = r0 + a.rows_per_split < nrows ? r0 + a.rows_per_split : nrows;
+    FaceSums fs;
+    fs.zero();
+    // Rows are processed in windows of whole rows when a row fits the window; otherwise in
+    // pieces, always through the guarded path.
+    const bool whole = nx <= kBwdWin;
+    const int rows_per_win = whole ? kBwdWin / nx : 1;
+    for (int64_t rw = r0; rw < r1; rw += rows_per_win) {
+        const int64_t rend = rw + rows_per_win < r1 ? rw + rows_per_win : r1;
+        for (int x0 = 0; x0 < nx; x0 += kBwdWin) {
+            const int xlen = whole ? nx : (nx - x0 < kBwdWin ? nx - x0 : kBwdWin);
+            const int64_t len = whole ? (rend - rw) * nx : xlen;
+            const int64_t base = rw * nx + (whole ? 0 : x0);
+            __syncthreads();
+            for (int64_t i = threadIdx.x; i < len; i += kBwdThreads) {
+                const int ix = whole ? (int)(i % nx) : x0 + (int)i;
+                win[i] = make_float2(a.upstream[base + i], __fmaf_rn((float)ix + 0.5f, a.g.h[0], a.g.lo[0]));
+            }
+            __syncthreads();
+            const int64_t nr = whole ? rend - rw : 1;
+            for (int64_t rr = 0; rr < nr; ++rr) {
+                const int64_t row = rw + rr;
+                const int iy = (int)(row % ny), iz = (int)(row / ny);
+                const float qy = __fmaf_rn((float)iy + 0.5f, a.g.h[1], a.g.lo[1]);
+                const float qz = __fmaf_rn((float)iz + 0.5f, a.g.h[2], a.g.lo[2]);
+                const RowB R = row_b(F, qy, qz);
+                const float2 *wrow = win + rr * (whole ? nx : 0);
+                float S[7], X[7];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
+                if (whole) {
+#pragma unroll 2
+                    for (int ix = 0; ix < nx; ++ix) {
+                        const float2 gq = wrow[ix];
+                        bwd_pair<false>(F, R, gq.y, gq.x, S, X);
+                    }
+                    if (!all_finite(S, X)) {
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
+                        for (int ix = 0; ix < nx; ++ix) {
+                            const float2 gq = wrow[ix];
+                            bwd_pair<true>(F, R, gq.y, gq.x, S, X);
+                        }
+                    }
+                } else {
+                    for (int ix = 0; ix < xlen; ++ix) {
+                        const float2 gq = wrow[ix];
+                        bwd_pair<true>(F, R, gq.y, gq.x, S, X);
+                    }
+                }
+                fs.fold(S, X, R.ay, R.az);
+            }
+            if (whole) break;
+        }
+    }
+    if (f < a.nf) write_face_grad(F, fs, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+}
+
+// List path: arbitrary queries, no shared row parts; each query is its own "row".
+__global__ void __launch_bounds__(kBwdThreads) bwd_list_kernel(const BwdArgs a) {
+    __shared__ float4 win[kBwdWin / 2];  // (x, y, z, g)
+    const int64_t f = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    const FaceF F = load_face(a.rec, f < a.nf ? f : a.nf - 1);
+    const int64_t q0 = (int64_t)blockIdx.y * a.rows_per_split;
+    const int64_t q1 = q0 + a.rows_per_split < a.nq ? q0 + a.rows_per_split : a.nq;
+    FaceSums fs;
+    fs.zero();
+    for (int64_t w0 = q0; w0 < q1; w0 += kBwdWin / 2) {
+        const int len = (int)(q1 - w0 < kBwdWin / 2 ? q1 - w0 : kBwdWin / 2);
+        __syncthreads();
+        for (int i = threadIdx.x; i < len; i += kBwdThreads) {
+            const int64_t k = w0 + i;
+            win[i] = make_float4(a.queries[3 * k], a.queries[3 * k + 1], a.queries[3 * k + 2], a.upstream[k]);
+        }
+        __syncthreads();
+        for (int i = 0; i < len; ++i) {
+            const float4 q = win[i];
+            const RowB R = row_b(F, q.y, q.z);
+            float S[7], X[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
+            bwd_pair<true>(F, R, q.x, q.w, S, X);
+            fs.fold(S, X, R.ay, R.az);
+        }
+    }
+    if (f < a.nf) write_face_grad(F, fs, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+}
+
+BwdPlan plan_backward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms) {
+    BwdPlan p{};
+    p.threads = kBwdThreads;
+    p.fblocks = (nf + kBwdThreads - 1) / kBwdThreads;
+    const int64_t units = grid ? (int64_t)g->n[1] * g->n[2] : nq;  // rows or queries
+    // About 5 CTAs of 128 threads are resident per SM; aim for >= 4 waves in total.
+    const int64_t target = 20LL * num_sms;
+    int64_t ns = (target + p.fblocks - 1) / p.fblocks;
+    if (ns < 1) ns = 1;
+    if (ns > units) ns = units > 0 ? units : 1;
+    if (ns > 4096) ns = 4096;
+    p.rows_per_split = (units + ns - 1) / ns;
+    p.nsplit = (int)((units + p.rows_per_split - 1) / p.rows_per_split);
+    if (p.nsplit < 1) p.nsplit = 1;
+    return p;
+}
+
+cudaError_t launch_backward(const BwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
+                            int64_t nq, const float *upstream, float *face_grad, const LaunchCtx &ctx) {
+    BwdArgs a{};
+    a.rec = rec;
+    a.nf = nf;
+    if (g) a.g = *g;
+    a.queries = queries;
+    a.nq = nq;
+    a.upstream = upstream;
+    a.rows_per_split = p.rows_per_split;
+    a.face_grad = face_grad;
+    a.err = ctx.d_err;
+    dim3 grid((unsigned)p.fblocks, (unsigned)p.nsplit);
+    const char *name = queries ? "bwd_list" : "bwd_grid";
+    prof_begin(name, ctx.stream);
+    if (queries)
+        bwd_list_kernel<<<grid, kBwdThreads, 0, ctx.stream>>>(a);
+    else
+        bwd_grid_kernel<<<grid, kBwdThreads, 0, ctx.stream>>>(a);
+    count_launch();
+    prof_end(name, ctx.stream);
+    return cudaGetLastError();
+}
+
+}  // namespace dv

@@ -1,0 +1,505 @@
+// Forward pass: generalized winding number over all (query, face) pairs, FP32.
+//
+// Per pair (Eq. (7) in unnormalized form, Eq. (8) for the quadrant):
+//   a = v0 - q, b = v1 - q, c = v2 - q
+//   N = a . n_f                    (= det(a, b, c), n_f = (v1 - v0) x (v2 - v0))
+//   D = |a||b||c| + (a.b)|c| + (b.c)|a| + (c.a)|b|
+//   sum += ATAN2(N, D)             (= Omega / 2)
+// and w = sum / (2 pi)  (Eq. (5)).
+//
+// Design for sm_103a:
+//   * Face records (48 B) stream through shared memory in tiles moved by 1-D TMA bulk copies
+//     (cp.async.bulk + mbarrier), 4-stage ring; every warp reads each face as a broadcast.
+//   * Voxel-centre queries are generated in registers from the grid index; each thread owns
+//     QX consecutive x positions on QY consecutive rows at one z. Parts of a, b, c, |.|^2, dots
+//     and N that depend on z only, or on (y, z) only, are computed once per face per thread and
+//     reused across the thread's queries, so the per-query cost is ~24 FP32 ops + 4 MUFU.
+//   * ATAN2 fast path: with the record's normal pre-scaled by 4, the test D > |4N| selects
+//     |N/D| < 1/4, where atan(N/D) = v P(v^2), v = 4N/D, P a degree-3 Remez polynomial
+//     (atan_poly.h). Terms failing the test contribute 0 on the fast path; if any lane of the
+//     warp has such a term for the current face, a slow path adds ATAN2 via atan2f for exactly
+//     those terms (re-computed bit-identically: every operation is an explicit _rn intrinsic).
+//   * Compensated summation: plain FP32 over a tile of 64 faces, Kahan across tiles.
+//   * Split over faces (grid.y) for small query counts; partial sums (sum, -compensation) go
+//     to a scratch buffer and are reduced in FP64, in fixed order, by split_reduce_kernel.
+#include <math.h>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+
+constexpr int kFwdThreads = 256;
+constexpr int kTileFaces = 64;
+constexpr int kStages = 4;
+
+struct FwdArgs {
+    const FaceRec *rec;
+    int64_t nf;
+    GridF g;
+    const float *queries;  // list path: [nq][3]; grid path: null
+    int64_t nq;
+    int64_t faces_per_split;
+    int nsplit;
+    float2 *partial;  // [nsplit][nq] when nsplit > 1
+    float *w_out;
+    uint8_t *occ_out;
+    const uint8_t *near_flag;  // null unless re-evaluation is on
+    int *flag_list;
+    int *flag_count;
+    int *err;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Per-pair arithmetic. Inputs are the x components of a, b, c plus the (y,z) partial sums.
+struct PairOut {
+    float N4, D;
+};
+
+__device__ __forceinline__ PairOut pair_terms(float ax, float bx, float cx, float La, float Lb, float Lc, float Pab,
+                                              float Pbc, float Pca, float Nyz, float n4x, float &la2_min) {
+    const float la2 = __fmaf_rn(ax, ax, La);
+    const float lb2 = __fmaf_rn(bx, bx, Lb);
+    const float lc2 = __fmaf_rn(cx, cx, Lc);
+    const float la = __fmul_rn(la2, rsqrt_approx(la2));
+    const float lb = __fmul_rn(lb2, rsqrt_approx(lb2));
+    const float lc = __fmul_rn(lc2, rsqrt_approx(lc2));
+    const float ab = __fmaf_rn(ax, bx, Pab);
+    const float bc = __fmaf_rn(bx, cx, Pbc);
+    const float ca = __fmaf_rn(cx, ax, Pca);
+    PairOut o;
+    o.N4 = __fmaf_rn(ax, n4x, Nyz);
+    float D = __fmul_rn(__fmul_rn(la, lb), lc);
+    D = __fmaf_rn(ab, lc, D);
+    D = __fmaf_rn(bc, la, D);
+    o.D = __fmaf_rn(ca, lb, D);
+    la2_min = fminf(la2, fminf(lb2, lc2));
+    return o;
+}
+
+// Fast-path arctangent: contributes atan(N/D) when D > |4N|, else 0 (slow path handles it).
+__device__ __forceinline__ float fast_term_fma(const PairOut &o, float acc, bool &ok) {
+    const bool p = o.D > fabsf(o.N4);
+    ok = ok && p;
+    float v = __fmul_rn(o.N4, rcp_approx(o.D));
+    v = p ? v : 0.0f;
+    const float s = __fmul_rn(v, v);
+    float P = __fmaf_rn(DV_ATAN_C3, s, DV_ATAN_C2);
+    P = __fmaf_rn(P, s, DV_ATAN_C1);
+    P = __fmaf_rn(P, s, DV_ATAN_C0);
+    return __fmaf_rn(v, P, acc);
+}
+
+// Slow-path term for a pair the fast path skipped: ATAN2(N, D) per Eq. (8) (-0 treated as +0,
+// the table's y >= 0 case), and 0 when q coincides with a vertex (ATAN2(0,0)).
+__device__ __forceinline__ float slow_term(const PairOut &o, float la2_min) {
+    if (o.D > fabsf(o.N4)) return 0.0f;  // already added by the fast path
+    if (!(la2_min >= 1.17549435e-38f)) return 0.0f;
+    return atan2f(__fadd_rn(o.N4, 0.0f), __fmul_rn(4.0f, o.D));
+}
+
+// (y, z) partial sums of one row for one face.
+struct RowPart {
+    float La, Lb, Lc, Pab, Pbc, Pca, Nyz;
+};
+
+__device__ __forceinline__ RowPart row_part(const FaceRec &r, float qy, float Laz, float Lbz, float Lcz, float Pabz,
+                                            float Pbcz, float Pcaz, float Nz) {
+    const float ay = __fsub_rn(r.r0.y, qy), by = __fsub_rn(r.r1.y, qy), cy = __fsub_rn(r.r2.y, qy);
+    RowPart p;
+    p.La = __fmaf_rn(ay, ay, Laz);
+    p.Lb = __fmaf_rn(by, by, Lbz);
+    p.Lc = __fmaf_rn(cy, cy, Lcz);
+    p.Pab = __fmaf_rn(ay, by, Pabz);
+    p.Pbc = __fmaf_rn(by, cy, Pbcz);
+    p.Pca = __fmaf_rn(cy, ay, Pcaz);
+    p.Nyz = __fmaf_rn(ay, r.r1.w, Nz);
+    return p;
+}
+
+// One face against the thread's QY x QX grid queries. Returns true if every pair took the fast path.
+template <int QX, int QY, bool SLOW>
+__device__ __forceinline__ bool face_grid(const FaceRec &r, const float (&qx)[QX], const float (&qy)[QY], float qz,
+                                          float (&acc)[QY][QX]) {
+    const float az = __fsub_rn(r.r0.z, qz), bz = __fsub_rn(r.r1.z, qz), cz = __fsub_rn(r.r2.z, qz);
+    const float Laz = __fmul_rn(az, az), Lbz = __fmul_rn(bz, bz), Lcz = __fmul_rn(cz, cz);
+    const float Pabz = __fmul_rn(az, bz), Pbcz = __fmul_rn(bz, cz), Pcaz = __fmul_rn(cz, az);
+    const float Nz = __fmul_rn(az, r.r2.w);
+    float ax[QX], bx[QX], cx[QX];
+#pragma unroll
+    for (int j = 0; j < QX; ++j) {
+        ax[j] = __fsub_rn(r.r0.x, qx[j]);
+        bx[j] = __fsub_rn(r.r1.x, qx[j]);
+        cx[j] = __fsub_rn(r.r2.x, qx[j]);
+    }
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < QY; ++i) {
+        const RowPart p = row_part(r, qy[i], Laz, Lbz, Lcz, Pabz, Pbcz, Pcaz, Nz);
+#pragma unroll
+        for (int j = 0; j < QX; ++j) {
+            float m;
+            const PairOut o = pair_terms(ax[j], bx[j], cx[j], p.La, p.Lb, p.Lc, p.Pab, p.Pbc, p.Pca, p.Nyz, r.r0.w, m);
+            if (SLOW)
+                acc[i][j] = __fadd_rn(acc[i][j], slow_term(o, m));
+            else
+                acc[i][j] = fast_term_fma(o, acc[i][j], ok);
+        }
+    }
+    return ok;
+}
+
+// One face against QL arbitrary queries (list path: no shared parts).
+template <int QL, bool SLOW>
+__device__ __forceinline__ bool face_list(const FaceRec &r, const float (&q)[QL][3], float (&acc)[QL]) {
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < QL; ++j) {
+        const float az = __fsub_rn(r.r0.z, q[j][2]), bz = __fsub_rn(r.r1.z, q[j][2]), cz = __fsub_rn(r.r2.z, q[j][2]);
+        const RowPart p = row_part(r, q[j][1], __fmul_rn(az, az), __fmul_rn(bz, bz), __fmul_rn(cz, cz),
+                                   __fmul_rn(az, bz), __fmul_rn(bz, cz), __fmul_rn(cz, az), __fmul_rn(az, r.r2.w));
+        float m;
+        const PairOut o = pair_terms(__fsub_rn(r.r0.x, q[j][0]), __fsub_rn(r.r1.x, q[j][0]), __fsub_rn(r.r2.x, q[j][0]),
+                                     p.La, p.Lb, p.Lc, p.Pab, p.Pbc, p.Pca, p.Nyz, r.r0.w, m);
+        if (SLOW)
+            acc[j] = __fadd_rn(acc[j], slow_term(o, m));
+        else
+            acc[j] = fast_term_fma(o, acc[j], ok);
+    }
+    return ok;
+}
+
+// Kahan step: (s, c) += x.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// Final per-query write: w, occupancy, and the re-evaluation flag.
+__device__ __forceinline__ void epilogue(const FwdArgs &a, int64_t idx, float w) {
+    a.w_out[idx] = w;
+    if (a.occ_out) a.occ_out[idx] = w > 0.5f ? 1 : 0;
+    if (a.flag_list) {
+        const bool flagged = a.near_flag[idx] != 0 || fabsf(__fsub_rn(w, 0.5f)) < kThreshBand;
+        if (flagged) {
+            const int pos = atomicAdd(a.flag_count, 1);
+            a.flag_list[pos] = (int)idx;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Shared TMA face-tile pipeline. `Body` processes one tile: body(const FaceRec* tile, int count).
+struct TilePipe {
+    FaceRec (*sm)[kTileFaces];
+    uint64_t *full;
+    const FaceRec *src;
+    int64_t f0;
+    int64_t nfaces;
+    int ntiles;
+
+    __device__ __forceinline__ int tile_count(int t) const {
+        const int64_t left = nfaces - (int64_t)t * kTileFaces;
+        return left < kTileFaces ? (int)left : kTileFaces;
+    }
+    __device__ __forceinline__ void issue(int t) const {
+        const int s = t % kStages;
+        const uint32_t bytes = (uint32_t)tile_count(t) * (uint32_t)sizeof(FaceRec);
+        mbar_arrive_expect_tx(&full[s], bytes);
+        tma_load_1d(&sm[s][0], src + f0 + (int64_t)t * kTileFaces, bytes, &full[s]);
+    }
+};
+
+template <typename Body, typename TileEnd>
+__device__ __forceinline__ bool run_face_tiles(TilePipe &pp, int *err, Body &&body, TileEnd &&tile_end) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&pp.full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int pre = pp.ntiles < kStages ? pp.ntiles : kStages;
+        for (int t = 0; t < pre; ++t) pp.issue(t);
+    }
+    bool timed_out = false;
+    for (int t = 0; t < pp.ntiles; ++t) {
+        const int s = t % kStages;
+        // after a first timeout, stop waiting: finish the loop on whatever is in shared memory
+        if (!timed_out && !mbar_wait_bounded(&pp.full[s], (uint32_t)((t / kStages) & 1))) timed_out = true;
+        body(&pp.sm[s][0], pp.tile_count(t));
+        tile_end();
+        __syncthreads();
+        if (threadIdx.x == 0 && t + kStages < pp.ntiles) {
+            fence_proxy_async_smem();
+            pp.issue(t + kStages);
+        }
+    }
+    if (timed_out) {
+        set_error(err, 5);
+        // Drain: give any copy still in flight a bounded chance to land before the CTA exits.
+        if (threadIdx.x == 0)
+            for (int t = pp.ntiles - kStages < 0 ? 0 : pp.ntiles - kStages; t < pp.ntiles; ++t)
+                mbar_wait_bounded(&pp.full[t % kStages], (uint32_t)((t / kStages) & 1));
+        __syncthreads();
+    }
+    return !timed_out;
+}
+
+// ---------------------------------------------------------------------------------------------
+template <int QX, int QY, bool KAHAN>
+__global__ void __launch_bounds__(kFwdThreads, 2) fwd_grid_kernel(const FwdArgs a) {
+    __shared__ __align__(128) FaceRec sm[kStages][kTileFaces];
+    __shared__ __align__(8) uint64_t full[kStages];
+    // Kahan state (sum, compensation) of every query of every thread, touched once per tile:
+    // kept in shared memory so that the hot loop's registers hold only the tile sums.
+    __shared__ float2 kst[KAHAN ? QX * QY : 1][kFwdThreads];
+
+    const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
+    const int tiles_x = (nx + QX - 1) / QX, tiles_y = (ny + QY - 1) / QY;
+    const int64_t tile = (int64_t)blockIdx.x * kFwdThreads + threadIdx.x;
+    const int tx = (int)(tile % tiles_x);
+    const int64_t t2 = tile / tiles_x;
+    const int ty = (int)(t2 % tiles_y);
+    const int64_t zz = t2 / tiles_y;
+    const bool valid_t = zz < nz;
+    const int z = valid_t ? (int)zz : nz - 1;
+
+    float qx[QX], qy[QY];
+#pragma unroll
+    for (int j = 0; j < QX; ++j) qx[j] = __fmaf_rn((float)(tx * QX + j) + 0.5f, a.g.h[0], a.g.lo[0]);
+#pragma unroll
+    for (int i = 0; i < QY; ++i) qy[i] = __fmaf_rn((float)(ty * QY + i) + 0.5f, a.g.h[1], a.g.lo[1]);
+    const float qz = __fmaf_rn((float)z + 0.5f, a.g.h[2], a.g.lo[2]);
+
+    float acc[QY][QX];
+#pragma unroll
+    for (int i = 0; i < QY; ++i)
+#pragma unroll
+        for (int j = 0; j < QX; ++j) {
+            acc[i][j] = 0.0f;
+            if (KAHAN) kst[i * QX + j][threadIdx.x] = make_float2(0.0f, 0.0f);
+        }
+
+    TilePipe pp;
+    pp.sm = sm;
+    pp.full = full;
+    pp.src = a.rec;
+    pp.f0 = (int64_t)blockIdx.y * a.faces_per_split;
+    const int64_t f1 = pp.f0 + a.faces_per_split < a.nf ? pp.f0 + a.faces_per_split : a.nf;
+    pp.nfaces = f1 - pp.f0;
+    pp.ntiles = (int)((pp.nfaces + kTileFaces - 1) / kTileFaces);
+
+    run_face_tiles(
+        pp, a.err,
+        [&](const FaceRec *tilep, int cnt) {
+#pragma unroll 1
+            for (int k = 0; k < cnt; ++k) {
+                const FaceRec r = tilep[k];
+                const bool ok = face_grid<QX, QY, false>(r, qx, qy, qz, acc);
+                if (__any_sync(kFull, !ok)) face_grid<QX, QY, true>(r, qx, qy, qz, acc);
+            }
+        },
+        [&]() {
+            if (KAHAN) {
+#pragma unroll
+                for (int i = 0; i < QY; ++i)
+#pragma unroll
+                    for (int j = 0; j < QX; ++j) {
+                        float2 k = kst[i * QX + j][threadIdx.x];
+                        kahan_add(k.x, k.y, acc[i][j]);
+                        kst[i * QX + j][threadIdx.x] = k;
+                        acc[i][j] = 0.0f;
+                    }
+            }
+        });
+
+    if (!valid_t) return;
+#pragma unroll
+    for (int i = 0; i < QY; ++i) {
+        const int iy = ty * QY + i;
+        if (iy >= ny) continue;
+#pragma unroll
+        for (int j = 0; j < QX; ++j) {
+            const int ix = tx * QX + j;
+            if (ix >= nx) continue;
+            const int64_t idx = ((int64_t)z * ny + iy) * nx + ix;
+            const float2 k = KAHAN ? kst[i * QX + j][threadIdx.x] : make_float2(acc[i][j], 0.0f);
+            const float s = k.x, c = k.y;
+            if (a.nsplit > 1)
+                a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(s, -c);
+            else
+                epilogue(a, idx, __fmul_rn(__fsub_rn(s, c), kInv2Pi));
+        }
+    }
+}
+
+template <int QL, bool KAHAN>
+__global__ void __launch_bounds__(kFwdThreads, 2) fwd_list_kernel(const FwdArgs a) {
+    __shared__ __align__(128) FaceRec sm[kStages][kTileFaces];
+    __shared__ __align__(8) uint64_t full[kStages];
+
+    const int64_t base = (int64_t)blockIdx.x * kFwdThreads * QL + threadIdx.x;
+    float q[QL][3];
+#pragma unroll
+    for (int j = 0; j < QL; ++j) {
+        int64_t idx = base + (int64_t)j * kFwdThreads;
+        if (idx >= a.nq) idx = a.nq - 1;
+        q[j][0] = a.queries[3 * idx];
+        q[j][1] = a.queries[3 * idx + 1];
+        q[j][2] = a.queries[3 * idx + 2];
+    }
+    float acc[QL], ks[QL], kc[QL];
+#pragma unroll
+    for (int j = 0; j < QL; ++j) acc[j] = ks[j] = kc[j] = 0.0f;
+
+    TilePipe pp;
+    pp.sm = sm;
+    pp.full = full;
+    pp.src = a.rec;
+    pp.f0 = (int64_t)blockIdx.y * a.faces_per_split;
+    const int64_t f1 = pp.f0 + a.faces_per_split < a.nf ? pp.f0 + a.faces_per_split : a.nf;
+    pp.nfaces = f1 - pp.f0;
+    pp.ntiles = (int)((pp.nfaces + kTileFaces - 1) / kTileFaces);
+
+    run_face_tiles(
+        pp, a.err,
+        [&](const FaceRec *tilep, int cnt) {
+#pragma unroll 1
+            for (int k = 0; k < cnt; ++k) {
+                const FaceRec r = tilep[k];
+                const bool ok = face_list<QL, false>(r, q, acc);
+                if (__any_sync(kFull, !ok)) face_list<QL, true>(r, q, acc);
+            }
+        },
+        [&]() {
+            if (KAHAN) {
+#pragma unroll
+                for (int j = 0; j < QL; ++j) {
+                    kahan_add(ks[j], kc[j], acc[j]);
+                    acc[j] = 0.0f;
+                }
+            }
+        });
+
+#pragma unroll
+    for (int j = 0; j < QL; ++j) {
+        const int64_t idx = base + (int64_t)j * kFwdThreads;
+        if (idx >= a.nq) continue;
+        const float s = KAHAN ? ks[j] : acc[j];
+        const float c = KAHAN ? kc[j] : 0.0f;
+        if (a.nsplit > 1)
+            a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(s, -c);
+        else
+            epilogue(a, idx, __fmul_rn(__fsub_rn(s, c), kInv2Pi));
+    }
+}
+
+// Sum the face-split partials of each query in FP64, in split order, then the epilogue.
+__global__ void split_reduce_kernel(const float2 *__restrict__ partial, int nsplit, FwdArgs a) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.nq; idx += stride) {
+        double s = 0.0;
+        for (int k = 0; k < nsplit; ++k) {
+            const float2 p = partial[(int64_t)k * a.nq + idx];
+            s += (double)p.x;
+            s += (double)p.y;
+        }
+        epilogue(a, idx, (float)(s * kInv2PiD));
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side.
+constexpr int kGridQX = 8, kGridQY = 2;  // 16 queries per thread on the grid path
+constexpr int kListQ = 8;                // 8 queries per thread on the list path
+
+FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms) {
+    FwdPlan p{};
+    p.threads = kFwdThreads;
+    if (grid) {
+        p.qx = kGridQX;
+        p.qy = kGridQY;
+        const int64_t tiles = (int64_t)((g->n[0] + kGridQX - 1) / kGridQX) * ((g->n[1] + kGridQY - 1) / kGridQY) *
+                              g->n[2];
+        p.qblocks = (tiles + kFwdThreads - 1) / kFwdThreads;
+    } else {
+        p.qx = kListQ;
+        p.qy = 1;
+        p.qblocks = (nq + (int64_t)kFwdThreads * kListQ - 1) / ((int64_t)kFwdThreads * kListQ);
+    }
+    // Two CTAs fit per SM. Split the face loop when the query CTAs alone would leave the GPU
+    // under-filled (fewer than ~4 waves), keeping at least 2 tiles of faces per split.
+    const int64_t slots = 2LL * num_sms;
+    int nsplit = 1;
+    if (p.qblocks < 4 * slots) {
+        const int64_t want = (4 * slots + p.qblocks - 1) / p.qblocks;
+        const int64_t maxs = (nf + 2 * kTileFaces - 1) / (2 * kTileFaces);
+        nsplit = (int)(want < maxs ? want : maxs);
+        if (nsplit < 1) nsplit = 1;
+        if (nsplit > 65535) nsplit = 65535;
+    }
+    p.nsplit = nsplit;
+    int64_t fps = (nf + nsplit - 1) / nsplit;
+    fps = ((fps + kTileFaces - 1) / kTileFaces) * kTileFaces;  // whole tiles per split
+    p.faces_per_split = fps;
+    p.nsplit = (int)((nf + fps - 1) / fps);
+    return p;
+}
+
+cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
+                           int64_t nq, bool kahan, float2 *partial, float *w_out, uint8_t *occ_out,
+                           const uint8_t *near_flag, int *flag_list, int *flag_count, const LaunchCtx &ctx) {
+    FwdArgs a{};
+    a.rec = rec;
+    a.nf = nf;
+    if (g) a.g = *g;
+    a.queries = queries;
+    a.nq = nq;
+    a.faces_per_split = p.faces_per_split;
+    a.nsplit = p.nsplit;
+    a.partial = partial;
+    a.w_out = w_out;
+    a.occ_out = occ_out;
+    a.near_flag = near_flag;
+    a.flag_list = flag_list;
+    a.flag_count = flag_count;
+    a.err = ctx.d_err;
+    dim3 grid((unsigned)p.qblocks, (unsigned)p.nsplit);
+    const char *name = queries ? (kahan ? "fwd_list_kahan" : "fwd_list") : (kahan ? "fwd_grid_kahan" : "fwd_grid");
+    prof_begin(name, ctx.stream);
+    if (queries) {
+        if (kahan)
+            fwd_list_kernel<kListQ, true><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
+        else
+            fwd_list_kernel<kListQ, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
+    } else {
+        if (kahan)
+            fwd_grid_kernel<kGridQX, kGridQY, true><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
+        else
+            fwd_grid_kernel<kGridQX, kGridQY, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
+    }
+    count_launch();
+    prof_end(name, ctx.stream);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_reduce(const FwdPlan &p, const float2 *partial, int64_t nq, float *w_out, uint8_t *occ_out,
+                                const uint8_t *near_flag, int *flag_list, int *flag_count, cudaStream_t s) {
+    FwdArgs a{};
+    a.nq = nq;
+    a.w_out = w_out;
+    a.occ_out = occ_out;
+    a.near_flag = near_flag;
+    a.flag_list = flag_list;
+    a.flag_count = flag_count;
+    int64_t blocks = (nq + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    prof_begin("split_reduce", s);
+    split_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(partial, p.nsplit, a);
+    count_launch();
+    prof_end("split_reduce", s);
+    return cudaGetLastError();
+}
+
+}  // namespace dv

@@ -1,0 +1,115 @@
+"""Adjoint parity: dL/dV from the CUDA path against the FP64 oracle's analytic
+gradient and against FP64 central finite differences.
+
+Upstream values are masked to 0 for queries within 1e-3 of the surface in every
+gradient comparison (there the terms grow like 1/d^2 and finite differences
+lose meaning); closed meshes, whose exact gradient is 0, are compared in
+absolute terms."""
+import numpy as np
+import pytest
+
+import oracle
+from _util import NEAR, grad_close, make_mesh, oracle_grid, to_dev
+from paper_2407_11272_b300 import dv, meshgen
+
+pytestmark = pytest.mark.gpu
+
+
+def _masked_upstream(n, d, seed=1):
+    g = meshgen.upstream_gradient(n, seed=seed).astype(np.float64)
+    g[d <= NEAR] = 0.0
+    return g
+
+
+@pytest.mark.parametrize("n", [24, 33])
+def test_small_torus_grid_gradient(cuda_device, n):
+    V, F = meshgen.jittered_torus(nu=60, nv=30, sigma=0.01, delete_frac=0.1, seed=0)
+    grid = dv.Grid.cube(n)
+    Q, _, d = oracle_grid(V, F, grid)
+    g = _masked_upstream(len(Q), d)
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    mesh = make_mesh(V, F, cuda_device)
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    grad_close(G, G_ref, f"torus grid {n}", oracle.winding_grad_scale(V, F, Q, g))
+
+
+def test_ragged_faces_odd_grid_gradient(cuda_device):
+    V, F = meshgen.jittered_torus(nu=20, nv=10, sigma=0.01, delete_frac=0.0, seed=1)
+    F = F[:129]
+    grid = dv.Grid((37, 23, 11), (-0.9, -1.1, -0.7), (1.2, 0.8, 0.9))
+    Q, _, d = oracle_grid(V, F, grid)
+    g = _masked_upstream(len(Q), d, seed=7)
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    mesh = make_mesh(V, F, cuda_device)
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    used = np.unique(F)
+    grad_close(G[used], G_ref[used], "ragged", oracle.winding_grad_scale(V, F, Q, g)[used])
+    unused = np.setdiff1d(np.arange(len(V)), used)
+    assert np.all(G[unused] == 0.0)
+
+
+def test_list_gradient(cuda_device):
+    V, F = meshgen.jittered_torus(nu=40, nv=20, sigma=0.01, delete_frac=0.1, seed=2)
+    rng = np.random.default_rng(31)
+    Q = rng.uniform(-1, 1, size=(5000, 3)).astype(np.float32)
+    d = oracle.point_mesh_distance(V, F, Q)
+    g = _masked_upstream(len(Q), d, seed=8)
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    mesh = make_mesh(V, F, cuda_device)
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device),
+                               queries=to_dev(Q, cuda_device)).cpu().numpy()
+    grad_close(G, G_ref, "list", oracle.winding_grad_scale(V, F, Q, g))
+
+
+def test_closed_mesh_gradient_is_cancellation_noise(cuda_device):
+    """Closed icosphere: exact dL/dV = 0. Remove one face and the same vertices get O(1) gradients;
+    the closed-mesh values must be orders of magnitude below those."""
+    V, F = meshgen.icosphere(3, 0.6)
+    grid = dv.Grid.cube(32)
+    Q, _, d = oracle_grid(V, F, grid, with_distance=True)
+    g = to_dev(_masked_upstream(len(Q), d).astype(np.float32), cuda_device)
+    Gc = dv.dv_winding_backward(make_mesh(V, F, cuda_device), g, grid=grid).cpu().numpy()
+    Go = dv.dv_winding_backward(make_mesh(V, F[1:], cuda_device), g, grid=grid).cpu().numpy()
+    hole = F[0]
+    assert np.abs(Gc).max() < 1e-4 * np.abs(Go[hole]).max()
+
+
+def test_deterministic_gradient(cuda_device):
+    V, F = meshgen.jittered_torus(nu=50, nv=25, sigma=0.01, delete_frac=0.1, seed=3)
+    grid = dv.Grid.cube(32)
+    mesh = make_mesh(V, F, cuda_device)
+    g = to_dev(meshgen.upstream_gradient(grid.num_queries), cuda_device)
+    a = dv.dv_winding_backward(mesh, g, grid=grid).cpu().numpy()
+    b = dv.dv_winding_backward(mesh, g, grid=grid).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_torus128_full_size_64_vertices(cuda_device):
+    """Open irregular torus, 128^3 grid, N(0,1) upstream: dL/dV on 64 seeded vertices against the
+    oracle's analytic gradient (all 2.1M queries), and against FP64 central differences (h = 1e-4)
+    on a seeded 20 000-query subsample through the list path."""
+    V, F = meshgen.jittered_torus()
+    grid = dv.Grid.cube(128)
+    mesh = make_mesh(V, F, cuda_device)
+    Q = oracle.grid_queries(grid.lo, grid.hi, grid.n)
+    g32 = meshgen.upstream_gradient(len(Q), seed=1)
+    # mask the near-surface queries using the GPU-independent conservative rule: the oracle distance
+    # is too slow at this size, so mask by a bounding distance to the vertices instead (a superset)
+    ids = meshgen.random_vertex_ids(len(V), 64, seed=2)
+    used = np.isin(ids, np.unique(F))
+    ids = ids[used]
+    inc = np.isin(F, ids).any(axis=1)
+    sub_d = oracle.point_mesh_distance(V, F[inc], Q)
+    g = g32.astype(np.float64)
+    g[sub_d <= 2e-2] = 0.0
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()[ids]
+    G_ref = oracle.vertex_grad_subset(V, F, Q, g, ids)
+    grad_close(G, G_ref, "torus128 analytic")
+    # finite differences on a query subsample (list path)
+    sub = meshgen.query_subsample(len(Q), 20000, seed=5)
+    Qs = Q[sub].astype(np.float32)
+    gs = g[sub]
+    Gs = dv.dv_winding_backward(mesh, to_dev(gs.astype(np.float32), cuda_device),
+                                queries=to_dev(Qs, cuda_device)).cpu().numpy()[ids]
+    fd = oracle.fd_vertex_grad(V, F, Qs, gs, ids, h=1e-4)
+    grad_close(Gs, fd, "torus128 finite differences")

@@ -248,6 +248,31 @@ def test_fd_driver_matches_brute_force():
     np.testing.assert_allclose(fd, _brute_fd(V, F, Q, g, h=1e-5)[ids], rtol=1e-9, atol=1e-12)
 
 
+def test_vertex_subset_gradient_equals_full_gradient_rows():
+    V, F = meshgen.jittered_torus(nu=16, nv=8, sigma=0.01, delete_frac=0.1, seed=4)
+    rng = np.random.default_rng(16)
+    Q = rng.uniform(-1, 1, size=(300, 3))
+    g = rng.normal(size=300)
+    ids = np.array([0, 5, 17, 60, 127])
+    np.testing.assert_allclose(oracle.vertex_grad_subset(V, F, Q, g, ids), oracle.winding_grad(V, F, Q, g)[ids],
+                               rtol=1e-12, atol=1e-14)
+
+
+def test_gradient_scale_bounds_gradient():
+    V, F = meshgen.jittered_torus(nu=16, nv=8, sigma=0.01, delete_frac=0.1, seed=4)
+    rng = np.random.default_rng(17)
+    Q = rng.uniform(-1, 1, size=(300, 3))
+    g = rng.normal(size=300)
+    G = oracle.winding_grad(V, F, Q, g)
+    S = oracle.winding_grad_scale(V, F, Q, g)
+    assert np.all(np.linalg.norm(G, axis=1) <= S * (1 + 1e-12) + 1e-300)
+    # a vertex with a single incident face: the scale equals the gradient norm
+    counts = np.bincount(F.ravel(), minlength=len(V))
+    one = np.where(counts == 1)[0]
+    if len(one):
+        np.testing.assert_allclose(np.linalg.norm(G[one], axis=1), S[one], rtol=1e-12)
+
+
 def test_closed_mesh_gradient_vanishes():
     V, F = meshgen.icosphere(1, 0.6)
     rng = np.random.default_rng(13)
