@@ -137,12 +137,12 @@ def _cpu_baseline(V, F, grid_n, budget_s=12.0, seed=4):
 
     Q = oracle.grid_queries([-1.0] * 3, [1.0] * 3, [grid_n] * 3)
     g = meshgen.upstream_gradient(len(Q), seed=1).astype(np.float64)
-    probe = meshgen.query_subsample(len(Q), 64, seed=seed)
+    probe = meshgen.query_subsample(len(Q), 512, seed=seed)
     t0 = time.perf_counter()
     oracle.winding(V, F, Q[probe])
     oracle.winding_grad(V, F, Q[probe], g[probe])
     t_probe = max(time.perf_counter() - t0, 1e-3)
-    n = int(np.clip(64 * budget_s / t_probe, 64, len(Q)))
+    n = int(np.clip(512 * budget_s / t_probe, 512, len(Q)))
     idx = meshgen.query_subsample(len(Q), n, seed=seed)
     t0 = time.perf_counter()
     oracle.winding(V, F, Q[idx])
@@ -165,11 +165,11 @@ def run_reference(args):
     Q = oracle.grid_queries([-1.0] * 3, [1.0] * 3, [n] * 3)
     g = meshgen.upstream_gradient(len(Q), seed=1).astype(np.float64)
     # size each step to a few seconds of CPU work
-    probe = meshgen.query_subsample(len(Q), 32, seed=6)
+    probe = meshgen.query_subsample(len(Q), 512, seed=6)
     t0 = time.perf_counter()
     oracle.winding(V, F, Q[probe])
     oracle.winding_grad(V, F, Q[probe], g[probe])
-    per_q = max(time.perf_counter() - t0, 1e-4) / 32
+    per_q = max(time.perf_counter() - t0, 1e-4) / 512
     nsamp = int(np.clip(4.0 / per_q, 32, len(Q)))
     times = []
     for step in range(args.warmup + args.steps):
@@ -226,11 +226,24 @@ def run_native(args):
     dV = torch.empty((len(V), 3), dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
     stream = torch.cuda.current_stream()
+    # The forward (+ FP64 re-evaluation) and the adjoint are independent given the packed mesh and
+    # use separate scratch, so they can run on two streams: the FP64 pass (FP64 pipe) then overlaps
+    # the adjoint (FP32 pipe). The forward stream has the higher priority so its CTAs are placed first.
+    s_fwd = torch.cuda.Stream(device=dev, priority=-1)
+    s_bwd = torch.cuda.Stream(device=dev, priority=0)
 
     def step():
-        dv.dv_mesh_update_verts(mesh, Vd)
-        dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision="mixed")
-        dv.dv_winding_backward(mesh, g, grid=grid, out=dV)
+        dv.dv_mesh_update_verts(mesh, Vd, stream=stream)
+        if args.streams == 1:
+            dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision="mixed", stream=stream)
+            dv.dv_winding_backward(mesh, g, grid=grid, out=dV, stream=stream)
+            return
+        s_fwd.wait_stream(stream)
+        s_bwd.wait_stream(stream)
+        dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision="mixed", stream=s_fwd)
+        dv.dv_winding_backward(mesh, g, grid=grid, out=dV, stream=s_bwd)
+        stream.wait_stream(s_fwd)
+        stream.wait_stream(s_bwd)
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -296,7 +309,7 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "faces": nf,
                        "queries": nq, "pairs_per_step": pairs, "parallelism": f"replicas{ws}",
-                       "l2": "flushed between timed steps (256 MB write)",
+                       "l2": "flushed between timed steps (256 MB write)", "streams": args.streams,
                        "fp64_reevaluated_queries": rep["n_flagged"]},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
@@ -362,6 +375,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="torus_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--streams", type=int, choices=[1, 2], default=1,
+                    help="1: one stream (default); 2: forward and adjoint on two streams")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps, whatever was asked
     if args.impl == "reference":

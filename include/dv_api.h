@@ -29,8 +29,12 @@
  *     synchronously and nothing is enqueued. Launch errors are reported as
  *     DV_ERR_CUDA. dv_last_error() gives a thread-local detail string.
  *   - There is no CPU fallback: a call either runs on the GPU or fails.
- *   - A dv_mesh owns scratch memory; calls on the same mesh must be ordered
- *     (one stream, or explicit events). Different meshes are independent.
+ *   - A dv_mesh owns scratch memory. Forward calls (dv_winding, dv_voxelize_grid)
+ *     on the same mesh must be ordered with each other (one stream, or events),
+ *     and so must backward calls; a forward and a backward on the same mesh use
+ *     separate scratch and may run concurrently on two streams once the mesh
+ *     is packed and its scratch reserved (dv_mesh_reserve). Different meshes are
+ *     independent.
  */
 #ifndef DV_API_H
 #define DV_API_H

@@ -16,9 +16,10 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // bounded mbarrier waits: give up after 2 s
 
 // Per-face FP32 record, 48 bytes = 3 x float4:
-//   r0 = (v0.x, v0.y, v0.z, 4 n.x), r1 = (v1.x, v1.y, v1.z, 4 n.y), r2 = (v2.x, v2.y, v2.z, 4 n.z)
-// with n = (v1 - v0) x (v2 - v0). The factor 4 (exact) lets the forward kernel test
-// |N| < D/4 as one comparison and feed 4N/D straight into its arctangent polynomial.
+//   r0 = (v0.x, v0.y, v0.z, 8 n.x), r1 = (v1.x, v1.y, v1.z, 8 n.y), r2 = (v2.x, v2.y, v2.z, 8 n.z)
+// with n = (v1 - v0) x (v2 - v0). The factor 8 (exact) lets the forward kernel test
+// |N| < D/8 as one comparison and feed 8N/D straight into its arctangent polynomial.
+constexpr float kNormalScale = 8.0f;
 struct FaceRec {
     float4 r0, r1, r2;
 };
@@ -109,7 +110,7 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t
 }
 
 // ------------------------------------------------------------------------------------------
-// FP32 special-function approximations (MUFU): reciprocal and reciprocal square root.
+// FP32 special-function approximations (MUFU): reciprocal, reciprocal square root, square root.
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -118,6 +119,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
 __device__ __forceinline__ float rsqrt_approx(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 

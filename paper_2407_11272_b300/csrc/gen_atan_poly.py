@@ -1,74 +1,91 @@
-"""Fit the minimax polynomial used by the kernels' arctangent fast path.
+"""Fit the minimax polynomials used by the kernels' arctangent fast paths.
 
-The forward kernel evaluates ATAN2(N, D) for the common case |N| < D/4
-(a face seen under a solid angle below about 0.49 sr). It stores the face
-normal pre-multiplied by 4, so it holds v = 4N/D in [-1, 1] and needs
+The FP32 forward kernel evaluates ATAN2(N, D) for the common case |N| < D/8
+(a face seen under a solid angle below about 0.25 sr). It stores the face
+normal pre-multiplied by 8, so it holds v = 8N/D in [-1, 1] and needs
 
-    atan(v / 4) ~= v * P(v^2),   P of degree ``DEG`` in s = v^2,
+    atan(v / 8) ~= v * P(v^2),   P of degree ``DEG32`` in s = v^2,
 
 with a small *relative* error, so that the error of a sum over faces stays
 proportional to the sum of |terms| (the faces far from a query have tiny
-solid angles). ``P`` is fitted here by the Remez exchange algorithm
-(E. Remez, 1934) on s in [0, 1] with weight 1/g(s), g(s) = atan(sqrt(s)/4)/sqrt(s),
-in float64 with numpy, then rounded to float32 and checked by evaluating the
-float32 Horner scheme exactly as the kernel does.
+solid angles). The FP64 re-evaluation kernel uses the same idea on u = N/D,
+|u| < 1/8:
+
+    atan(u) ~= u * Q(u^2),       Q of degree ``DEG64`` in s = u^2.
+
+Both are fitted by the Remez exchange algorithm (E. Remez, 1934) on the
+reduced variable in [0, 1] with weight 1/g (relative error), carried out in
+50-digit arithmetic with mpmath; the FP32 coefficients are then checked by
+evaluating the float32 Horner scheme exactly as the kernel does.
 
 Run ``python gen_atan_poly.py`` to regenerate ``atan_poly.h``.
 """
 from __future__ import annotations
 
-import math
 from pathlib import Path
 
+import mpmath as mp
 import numpy as np
 
-T = 0.25
-DEG = 3
+T = 0.125      # fast-path bound on |N/D| (both precisions)
+DEG32 = 2
+DEG64 = 6
+
+mp.mp.dps = 50
 
 
-def g(s):
-    s = np.asarray(s, dtype=np.float64)
-    r = np.sqrt(s)
-    out = np.empty_like(s)
-    small = r < 1e-8
-    out[small] = T
-    out[~small] = np.arctan(T * r[~small]) / r[~small]
-    return out
+def g_mp(s, scale):
+    """atan(scale * sqrt(s)) / sqrt(s), the function P must match (s in [0, 1])."""
+    s = mp.mpf(s)
+    if s == 0:
+        return mp.mpf(scale)
+    r = mp.sqrt(s)
+    return mp.atan(scale * r) / r
 
 
-def remez(deg: int, iters: int = 60):
+def remez(deg: int, scale: float, iters: int = 30, ngrid: int = 4000):
+    """Weighted (relative) minimax polynomial P(s) ~ g(s) on [0, 1]; returns mpf coefficients c0..c_deg."""
     n = deg + 2
-    # Chebyshev extrema as the first reference
-    x = 0.5 - 0.5 * np.cos(np.pi * np.arange(n) / (n - 1))
-    grid = np.linspace(0.0, 1.0, 200001)
+    x = [mp.mpf(1) / 2 - mp.cos(mp.pi * k / (n - 1)) / 2 for k in range(n)]
+    grid = [mp.mpf(k) / ngrid for k in range(ngrid + 1)]
+    gg = [g_mp(t, scale) for t in grid]
     coef = None
     for _ in range(iters):
-        A = np.zeros((n, n))
+        A = mp.matrix(n, n)
+        b = mp.matrix(n, 1)
         for i in range(n):
-            A[i, : deg + 1] = x[i] ** np.arange(deg + 1)
-            A[i, deg + 1] = (-1) ** i * g(x[i : i + 1])[0]
-        sol = np.linalg.solve(A, g(x))
-        coef = sol[: deg + 1]
-        err = (np.polyval(coef[::-1], grid) - g(grid)) / g(grid)
-        # new reference: one extremum per sign-alternating segment
-        sgn = np.sign(err)
+            gi = g_mp(x[i], scale)
+            for k in range(deg + 1):
+                A[i, k] = x[i] ** k
+            A[i, deg + 1] = (-1) ** i * gi
+            b[i] = gi
+        sol = mp.lu_solve(A, b)
+        coef = [sol[k] for k in range(deg + 1)]
+        err = [(mp.polyval(coef[::-1], t) - gv) / gv for t, gv in zip(grid, gg)]
+        # one extremum per run of equal sign
         idx, start = [], 0
         for k in range(1, len(grid) + 1):
-            if k == len(grid) or sgn[k] != sgn[start]:
-                seg = slice(start, k)
-                idx.append(start + int(np.argmax(np.abs(err[seg]))))
+            if k == len(grid) or mp.sign(err[k]) != mp.sign(err[start]):
+                idx.append(max(range(start, k), key=lambda j: abs(err[j])))
                 start = k
         if len(idx) < n:
             break
-        # keep the n largest consecutive alternating extrema
         while len(idx) > n:
-            e = np.abs(err[idx])
-            if e[0] < e[-1]:
+            if abs(err[idx[0]]) < abs(err[idx[-1]]):
                 idx.pop(0)
             else:
                 idx.pop()
-        x = grid[idx]
+        x = [grid[j] for j in idx]
     return coef
+
+
+def max_rel_err_mp(coef, scale, npts=4001):
+    worst = mp.mpf(0)
+    for k in range(npts):
+        s = mp.mpf(k) / (npts - 1)
+        gv = g_mp(s, scale)
+        worst = max(worst, abs((mp.polyval(coef[::-1], s) - gv) / gv))
+    return worst
 
 
 def eval_f32(coef32, v):
@@ -82,22 +99,33 @@ def eval_f32(coef32, v):
 
 
 def main():
-    coef = remez(DEG)
-    c32 = np.asarray(coef, dtype=np.float32)
+    c32 = remez(DEG32, T)
+    c32f = np.asarray([float(c) for c in c32], dtype=np.float32)
     v = np.linspace(-1.0, 1.0, 2000001)[1:-1]
     v = v[v != 0]
     ref = np.arctan(T * v.astype(np.float64))
-    rel = np.abs(eval_f32(c32, v).astype(np.float64) - ref) / np.abs(ref)
+    rel32 = float((np.abs(eval_f32(c32f, v).astype(np.float64) - ref) / np.abs(ref)).max())
+    # FP64 path: fit P(t) ~ atan(T sqrt(t)) / sqrt(t) on t in [0, 1], then substitute t = u^2 / T^2:
+    # atan(u) = (u / T) P(u^2 / T^2), i.e. Q(s) = sum_k c_k / T^(2k+1) s^k.
+    c64t = remez(DEG64, T)
+    e64 = max_rel_err_mp(c64t, T)
+    c64 = [c / mp.mpf(T) ** (2 * k + 1) for k, c in enumerate(c64t)]
     lines = [
-        "// Generated by gen_atan_poly.py (Remez minimax fit, relative error). Do not edit.",
-        f"// atan(v * {T}) ~= v * P(v*v) for |v| <= 1, P of degree {DEG};",
-        f"// measured max relative error of the float32 evaluation: {rel.max():.3e}",
+        "// Generated by gen_atan_poly.py (Remez minimax fits, relative error). Do not edit.",
+        f"// FP32: atan(v * {T}) ~= v * P(v*v) for |v| <= 1, P of degree {DEG32};",
+        f"//       max relative error of the float32 evaluation: {rel32:.3e}",
+        f"// FP64: atan(u) ~= u * Q(u*u) for |u| <= {T}, Q of degree {DEG64};",
+        f"//       max relative error of the polynomial itself: {float(e64):.3e}",
         "#pragma once",
         f"#define DV_ATAN_FAST_T {T}f",
-        f"#define DV_ATAN_FAST_DEG {DEG}",
+        f"#define DV_ATAN_FAST_DEG {DEG32}",
     ]
-    for k, c in enumerate(c32):
+    for k, c in enumerate(c32f):
         lines.append(f"#define DV_ATAN_C{k} {float(c)!r}f")
+    lines.append(f"#define DV_ATAN64_FAST_T {T}")
+    lines.append(f"#define DV_ATAN64_DEG {DEG64}")
+    for k, c in enumerate(c64):
+        lines.append(f"#define DV_ATAN64_C{k} {mp.nstr(c, 25)}")
     Path(__file__).with_name("atan_poly.h").write_text("\n".join(lines) + "\n")
     print("\n".join(lines))
 

@@ -19,7 +19,7 @@ __global__ void validate_kernel(const float *__restrict__ verts, int64_t nv, con
 }
 
 // One thread per face: gather the three vertices, compute n = (v1 - v0) x (v2 - v0) in FP64
-// (products of FP32 values are exact in FP64), and store the FP32 record (normal scaled by 4)
+// (products of FP32 values are exact in FP64), and store the FP32 record (normal scaled by 8)
 // and the FP64 record used by the re-evaluation pass.
 __global__ void pack_kernel(const float *__restrict__ verts, const int32_t *__restrict__ faces, int64_t nf,
                             FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
@@ -34,9 +34,9 @@ __global__ void pack_kernel(const float *__restrict__ verts, const int32_t *__re
     double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
     double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     FaceRec r;
-    r.r0 = make_float4((float)v[0][0], (float)v[0][1], (float)v[0][2], (float)(4.0 * n[0]));
-    r.r1 = make_float4((float)v[1][0], (float)v[1][1], (float)v[1][2], (float)(4.0 * n[1]));
-    r.r2 = make_float4((float)v[2][0], (float)v[2][1], (float)v[2][2], (float)(4.0 * n[2]));
+    r.r0 = make_float4((float)v[0][0], (float)v[0][1], (float)v[0][2], (float)(kNormalScale * n[0]));
+    r.r1 = make_float4((float)v[1][0], (float)v[1][1], (float)v[1][2], (float)(kNormalScale * n[1]));
+    r.r2 = make_float4((float)v[2][0], (float)v[2][1], (float)v[2][2], (float)(kNormalScale * n[2]));
     rec[f] = r;
     FaceRec64 r64;
     for (int k = 0; k < 3; ++k)

@@ -77,13 +77,13 @@ __device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx
         lc2 = fmaxf(lc2, 1e-30f);
     }
     const float ia = rsqrt_approx(la2), ib = rsqrt_approx(lb2), ic = rsqrt_approx(lc2);
-    const float la = la2 * ia, lb = lb2 * ib, lc = lc2 * ic;
+    const float la = sqrt_approx(la2), lb = sqrt_approx(lb2), lc = sqrt_approx(lc2);
     const float ab = fmaf(ax, bx, R.Pab), bc = fmaf(bx, cx, R.Pbc), ca = fmaf(cx, ax, R.Pca);
     const float N = fmaf(ax, F.nx, R.Nyz);
-    float D = la * lb * lc;
-    D = fmaf(ab, lc, D);
-    D = fmaf(bc, la, D);
-    D = fmaf(ca, lb, D);
+    const float tc = fmaf(la, lb, ab);  // |a||b| + a.b, also the numerator of alpha_c
+    float D = tc * lc;
+    D = fmaf(la, bc, D);
+    D = fmaf(lb, ca, D);
     const float den = fmaf(N, N, D * D);
     float r = rcp_approx(den);
     if (GUARD) r = den >= 1.17549435e-38f ? r : 0.0f;
@@ -92,7 +92,7 @@ __device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx
     const float P = cN * la, Qb = cN * lb, Rc = cN * lc;
     const float alA = cN * (fmaf(lb, lc, bc) * ia);
     const float alB = cN * (fmaf(lc, la, ca) * ib);
-    const float alC = cN * (fmaf(la, lb, ab) * ic);
+    const float alC = cN * (tc * ic);
     S[0] += cD;
     S[1] += P;
     S[2] += Qb;
@@ -153,7 +153,9 @@ __device__ __forceinline__ FaceF load_face(const FaceRec *rec, int64_t f) {
     F.v0x = r.r0.x; F.v0y = r.r0.y; F.v0z = r.r0.z;
     F.v1x = r.r1.x; F.v1y = r.r1.y; F.v1z = r.r1.z;
     F.v2x = r.r2.x; F.v2y = r.r2.y; F.v2z = r.r2.z;
-    F.nx = 0.25f * r.r0.w; F.ny = 0.25f * r.r1.w; F.nz = 0.25f * r.r2.w;
+    F.nx = r.r0.w * (1.0f / kNormalScale);
+    F.ny = r.r1.w * (1.0f / kNormalScale);
+    F.nz = r.r2.w * (1.0f / kNormalScale);
     return F;
 }
 

@@ -12,6 +12,9 @@ namespace dv {
 constexpr int kReThreads = 256;
 constexpr int kReQB = 4;
 
+// ATAN2(N, D) of one face in FP64. Fast path for D > 8|N| (a face seen under less than
+// ~0.25 sr, almost every face): atan(u) = u Q(u^2), u = N/D, Q a degree-6 Remez fit with
+// relative error below 2e-18 (atan_poly.h). Otherwise CUDA's atan2 with Eq. (8)'s conventions.
 __device__ __forceinline__ double half_angle64(const FaceRec64 &r, double qx, double qy, double qz) {
     const double ax = r.v[0] - qx, ay = r.v[1] - qy, az = r.v[2] - qz;
     const double bx = r.v[3] - qx, by = r.v[4] - qy, bz = r.v[5] - qz;
@@ -20,8 +23,20 @@ __device__ __forceinline__ double half_angle64(const FaceRec64 &r, double qx, do
     const double lb = sqrt(bx * bx + by * by + bz * bz);
     const double lc = sqrt(cx * cx + cy * cy + cz * cz);
     const double N = ax * r.v[9] + ay * r.v[10] + az * r.v[11];
-    const double D = la * lb * lc + (ax * bx + ay * by + az * bz) * lc + (bx * cx + by * cy + bz * cz) * la +
-                     (cx * ax + cy * ay + cz * az) * lb;
+    const double D = (la * lb + (ax * bx + ay * by + az * bz)) * lc + la * (bx * cx + by * cy + bz * cz) +
+                     lb * (cx * ax + cy * ay + cz * az);
+    if (D > 8.0 * fabs(N)) {
+        const double u = N / D;
+        const double s = u * u;
+        double P = DV_ATAN64_C6;
+        P = fma(P, s, DV_ATAN64_C5);
+        P = fma(P, s, DV_ATAN64_C4);
+        P = fma(P, s, DV_ATAN64_C3);
+        P = fma(P, s, DV_ATAN64_C2);
+        P = fma(P, s, DV_ATAN64_C1);
+        P = fma(P, s, DV_ATAN64_C0);
+        return u * P;
+    }
     if (N == 0.0 && D == 0.0) return 0.0;  // ATAN2(0, 0) = 0 (q on a vertex or an edge)
     return atan2(N + 0.0, D);              // -0 -> +0: the table's case y >= 0
 }

@@ -13,9 +13,10 @@
 //   * Voxel-centre queries are generated in registers from the grid index; each thread owns
 //     QX consecutive x positions on QY consecutive rows at one z. Parts of a, b, c, |.|^2, dots
 //     and N that depend on z only, or on (y, z) only, are computed once per face per thread and
-//     reused across the thread's queries, so the per-query cost is ~24 FP32 ops + 4 MUFU.
-//   * ATAN2 fast path: with the record's normal pre-scaled by 4, the test D > |4N| selects
-//     |N/D| < 1/4, where atan(N/D) = v P(v^2), v = 4N/D, P a degree-3 Remez polynomial
+//     reused across the thread's queries, so the per-query cost is ~18 FP32 ops + 4 MUFU
+//     (|a|, |b|, |c| by MUFU square root, D = (|a||b| + a.b)|c| + |a|(b.c) + |b|(c.a)).
+//   * ATAN2 fast path: with the record's normal pre-scaled by 8, the test D > |8N| selects
+//     |N/D| < 1/8, where atan(N/D) = v P(v^2), v = 8N/D, P a degree-2 Remez polynomial
 //     (atan_poly.h). Terms failing the test contribute 0 on the fast path; if any lane of the
 //     warp has such a term for the current face, a slow path adds ATAN2 via atan2f for exactly
 //     those terms (re-computed bit-identically: every operation is an explicit _rn intrinsic).
@@ -52,39 +53,37 @@ struct FwdArgs {
 // ---------------------------------------------------------------------------------------------
 // Per-pair arithmetic. Inputs are the x components of a, b, c plus the (y,z) partial sums.
 struct PairOut {
-    float N4, D;
+    float N8, D;  // 8 det(a, b, c) and D
 };
 
 __device__ __forceinline__ PairOut pair_terms(float ax, float bx, float cx, float La, float Lb, float Lc, float Pab,
-                                              float Pbc, float Pca, float Nyz, float n4x, float &la2_min) {
+                                              float Pbc, float Pca, float Nyz, float n8x, float &la2_min) {
     const float la2 = __fmaf_rn(ax, ax, La);
     const float lb2 = __fmaf_rn(bx, bx, Lb);
     const float lc2 = __fmaf_rn(cx, cx, Lc);
-    const float la = __fmul_rn(la2, rsqrt_approx(la2));
-    const float lb = __fmul_rn(lb2, rsqrt_approx(lb2));
-    const float lc = __fmul_rn(lc2, rsqrt_approx(lc2));
+    const float la = sqrt_approx(la2);
+    const float lb = sqrt_approx(lb2);
+    const float lc = sqrt_approx(lc2);
     const float ab = __fmaf_rn(ax, bx, Pab);
     const float bc = __fmaf_rn(bx, cx, Pbc);
     const float ca = __fmaf_rn(cx, ax, Pca);
     PairOut o;
-    o.N4 = __fmaf_rn(ax, n4x, Nyz);
-    float D = __fmul_rn(__fmul_rn(la, lb), lc);
-    D = __fmaf_rn(ab, lc, D);
-    D = __fmaf_rn(bc, la, D);
-    o.D = __fmaf_rn(ca, lb, D);
+    o.N8 = __fmaf_rn(ax, n8x, Nyz);
+    float D = __fmul_rn(__fmaf_rn(la, lb, ab), lc);
+    D = __fmaf_rn(la, bc, D);
+    o.D = __fmaf_rn(lb, ca, D);
     la2_min = fminf(la2, fminf(lb2, lc2));
     return o;
 }
 
-// Fast-path arctangent: contributes atan(N/D) when D > |4N|, else 0 (slow path handles it).
+// Fast-path arctangent: contributes atan(N/D) when D > |8N|, else 0 (slow path handles it).
 __device__ __forceinline__ float fast_term_fma(const PairOut &o, float acc, bool &ok) {
-    const bool p = o.D > fabsf(o.N4);
+    const bool p = o.D > fabsf(o.N8);
     ok = ok && p;
-    float v = __fmul_rn(o.N4, rcp_approx(o.D));
+    float v = __fmul_rn(o.N8, rcp_approx(o.D));
     v = p ? v : 0.0f;
     const float s = __fmul_rn(v, v);
-    float P = __fmaf_rn(DV_ATAN_C3, s, DV_ATAN_C2);
-    P = __fmaf_rn(P, s, DV_ATAN_C1);
+    float P = __fmaf_rn(DV_ATAN_C2, s, DV_ATAN_C1);
     P = __fmaf_rn(P, s, DV_ATAN_C0);
     return __fmaf_rn(v, P, acc);
 }
@@ -92,9 +91,9 @@ __device__ __forceinline__ float fast_term_fma(const PairOut &o, float acc, bool
 // Slow-path term for a pair the fast path skipped: ATAN2(N, D) per Eq. (8) (-0 treated as +0,
 // the table's y >= 0 case), and 0 when q coincides with a vertex (ATAN2(0,0)).
 __device__ __forceinline__ float slow_term(const PairOut &o, float la2_min) {
-    if (o.D > fabsf(o.N4)) return 0.0f;  // already added by the fast path
+    if (o.D > fabsf(o.N8)) return 0.0f;  // already added by the fast path
     if (!(la2_min >= 1.17549435e-38f)) return 0.0f;
-    return atan2f(__fadd_rn(o.N4, 0.0f), __fmul_rn(4.0f, o.D));
+    return atan2f(__fadd_rn(o.N8, 0.0f), __fmul_rn(kNormalScale, o.D));
 }
 
 // (y, z) partial sums of one row for one face.
