@@ -152,6 +152,31 @@ dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_ou
 dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                               const float *d_upstream, float *d_dverts, void *stream);
 
+/* No counterpart in the paper: a service of this library.
+ * Winding numbers of the voxel centres of *grid (as dv_winding with
+ * DV_PREC_FP32_KAHAN) for a mesh given directly as d_verts float32 [nv][3] and
+ * d_faces int32 [nf][3], written to d_out_w float32 [nx*ny*nz], with NO device
+ * allocation by the library: no dv_mesh is created, and no cudaMalloc, cudaFree
+ * or other allocating call is made. It is meant for callers that cannot let a
+ * library allocate: a process whose own allocator or memory budget already owns
+ * the device memory (for example a server that has divided it among requests),
+ * or a loop that cannot afford the device-wide synchronization that cudaMalloc
+ * and cudaFree may cause.
+ * The library's working memory on this path (packed face records, per-split
+ * partial sums, an error word) is one fixed 32 MiB array compiled into the
+ * library; a GPU on which the library's code is loaded keeps it until the
+ * process exits. Requests that need more (about 48 bytes per face, plus 8 bytes
+ * per query times the number of face splits for small grids) are rejected with
+ * DV_ERR_UNSUPPORTED and a message giving the sizes. The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, no allocation);
+ * make that first call before any stream capture. Every call on a device uses
+ * the same array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other; serialize them. Faces are checked on the
+ * device: an index outside [0, nv) gives DV_ERR_INVALID_MESH. The call
+ * SYNCHRONIZES `stream` once, at the end, to read that check. */
+dv_status dv_winding_grid_noalloc(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf,
+                                  const dv_grid *grid, float *d_out_w, void *stream);
+
 /* Per-kernel timing of this library's own launches, for measurement tools.
  * dv_profile_enable(1) makes every later launch (on any stream) record a CUDA
  * event pair on its own stream; dv_profile_read synchronizes on those events and

@@ -59,6 +59,8 @@ static std::mutex g_prof_mu;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+dv_status report_error(dv_status s, const char *msg) { return fail(s, "%s", msg); }
+
 void prof_begin(const char *name, cudaStream_t s) {
     if (!g_prof_on) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);

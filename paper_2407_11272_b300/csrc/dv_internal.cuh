@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "atan_poly.h"
+#include "dv_api.h"
 
 namespace dv {
 
@@ -147,6 +148,8 @@ struct LaunchCtx {
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(const char *name, cudaStream_t s);
 void count_launch();
+// Record `msg` as the calling thread's dv_last_error() text and return `s` (dv_api.cu).
+dv_status report_error(dv_status s, const char *msg);
 
 // pack.cu
 cudaError_t launch_validate(const float *verts, int64_t nv, const int32_t *faces, int64_t nf, int *d_bad,
