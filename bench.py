@@ -153,6 +153,21 @@ def _cpu_baseline(V, F, grid_n, budget_s=12.0, seed=4):
                       f"{dt:.1f} s"}
 
 
+def aggregate_ranks(local_ms: float, pairs_per_step: int, steps: int, ws: int, device=None):
+    """Whole-job throughput: every rank ran its own replica of `steps` steps; the job time is the
+    slowest rank's (max over ranks), and the value counts the pairs of all ranks.
+    Returns (job_ms, pairs_per_second). Works with any initialized process group (NCCL or gloo)."""
+    job_ms = float(local_ms)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([job_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        job_ms = float(t.item())
+    return job_ms, ws * pairs_per_step * steps / (job_ms * 1e-3)
+
+
 def run_reference(args):
     ws, rank, _ = _dist_env()
     if rank != 0:
@@ -271,15 +286,8 @@ def run_native(args):
         dv.dv_profile_enable(False)
     launches = dv.dv_launch_count() - launches0
     times_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(times_ms))
     prof = dv.dv_profile_read()
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * pairs * args.steps / (total_ms * 1e-3)
+    total_ms, value = aggregate_ranks(float(sum(times_ms)), pairs, args.steps, ws, dev)
 
     # roofline of the dominant kernel: algorithmic FP32 lane operations per launch / measured duration
     peaks, peak_src = _peaks()
