@@ -177,6 +177,18 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
 dv_status dv_winding_grid_noalloc(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf,
                                   const dv_grid *grid, float *d_out_w, void *stream);
 
+/* Algorithm 2 (Flipping Duplication, §2.3): turn an open mesh into an almost
+ * closed thin shell, Sigma^-2 = (V u V', F u F'), so that Algorithm 1 voxelizes
+ * it like a closed mesh. d_verts float32 [nv][3] must be the vertices the mesh
+ * was created or last updated with. Outputs (caller-owned, device):
+ *   d_out_verts float32 [2nv][3]: V, then V' with v' = v - eps * N_v,
+ *   d_out_faces int32  [2nf][3]: F, then F' = {(v0', v2', v1')} (reversed orientation).
+ * N_v is the normalized sum of the incident faces' (v1-v0)x(v2-v0) (area-weighted;
+ * the paper does not specify), summed in FP64 in a fixed order; a vertex with no
+ * incident face keeps v' = v. The paper suggests eps = 0.01. Stream-ordered, no sync. */
+dv_status dv_flipped_duplication(const dv_mesh *mesh, const float *d_verts, float eps, float *d_out_verts,
+                                 int32_t *d_out_faces, void *stream);
+
 /* Per-kernel timing of this library's own launches, for measurement tools.
  * dv_profile_enable(1) makes every later launch (on any stream) record a CUDA
  * event pair on its own stream; dv_profile_read synchronizes on those events and

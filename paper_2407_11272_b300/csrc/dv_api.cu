@@ -441,6 +441,20 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
     return DV_OK;
 }
 
+dv_status dv_flipped_duplication(const dv_mesh *mesh, const float *d_verts, float eps, float *d_out_verts,
+                                 int32_t *d_out_faces, void *stream) {
+    if (!mesh || !d_verts || !d_out_verts || !d_out_faces)
+        return fail(DV_ERR_INVALID_ARG, "mesh, d_verts, d_out_verts and d_out_faces must be non-NULL");
+    if (!std::isfinite(eps)) return fail(DV_ERR_INVALID_ARG, "eps must be finite");
+    if (2 * mesh->nv > (int64_t)INT32_MAX || 6 * mesh->nf > (int64_t)INT32_MAX)
+        return fail(DV_ERR_UNSUPPORTED, "duplicated mesh exceeds the 32-bit index range");
+    dv_mesh *m = const_cast<dv_mesh *>(mesh);
+    DeviceGuard dg(m->device);
+    DV_CUDA(dv::launch_flipped_duplication(d_verts, m->nv, m->faces, m->nf, m->rec64, m->vtx_ptr, m->vtx_corner,
+                                           (double)eps, d_out_verts, d_out_faces, (cudaStream_t)stream));
+    return DV_OK;
+}
+
 void dv_profile_enable(int on) { dv::g_prof_on = on != 0; }
 
 void dv_profile_reset(void) {

@@ -156,6 +156,9 @@ cudaError_t launch_validate(const float *verts, int64_t nv, const int32_t *faces
                             cudaStream_t s);
 cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, FaceRec *rec, FaceRec64 *rec64,
                         cudaStream_t s);
+cudaError_t launch_flipped_duplication(const float *verts, int64_t nv, const int32_t *faces, int64_t nf,
+                                       const FaceRec64 *rec64, const int32_t *vtx_ptr, const int32_t *vtx_corner,
+                                       double eps, float *out_verts, int32_t *out_faces, cudaStream_t s);
 cudaError_t launch_gather_dverts(const double *unused, const float *face_grad, int nsplit, int64_t nf,
                                  const int32_t *vtx_ptr, const int32_t *vtx_corner, int64_t nv, float *dverts,
                                  cudaStream_t s);

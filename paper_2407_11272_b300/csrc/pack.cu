@@ -105,3 +105,63 @@ cudaError_t launch_gather_dverts(const double *, const float *face_grad, int nsp
 }
 
 }  // namespace dv
+
+namespace dv {
+
+// Algorithm 2 (Flipping Duplication), vertex part: N_v = normalized sum over the faces incident
+// to v of (v1 - v0) x (v2 - v0) (area-weighted normal; the paper does not say how N_v is
+// computed), summed in FP64 in the adjacency's face order. Writes v (copy) and v' = v - eps N_v.
+__global__ void flipdup_verts_kernel(const float *__restrict__ verts, int64_t nv, const FaceRec64 *__restrict__ rec64,
+                                     const int32_t *__restrict__ vtx_ptr, const int32_t *__restrict__ vtx_corner,
+                                     double eps, float *__restrict__ out) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    double n0 = 0, n1 = 0, n2 = 0;
+    for (int32_t c = vtx_ptr[v]; c < vtx_ptr[v + 1]; ++c) {
+        const FaceRec64 &r = rec64[vtx_corner[c] / 3];
+        n0 += r.v[9];
+        n1 += r.v[10];
+        n2 += r.v[11];
+    }
+    const double len = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    const double inv = len > 0.0 ? 1.0 / len : 0.0;
+    const double p0 = verts[3 * v], p1 = verts[3 * v + 1], p2 = verts[3 * v + 2];
+    out[3 * v] = (float)p0;
+    out[3 * v + 1] = (float)p1;
+    out[3 * v + 2] = (float)p2;
+    out[3 * (nv + v)] = (float)(p0 - eps * n0 * inv);
+    out[3 * (nv + v) + 1] = (float)(p1 - eps * n1 * inv);
+    out[3 * (nv + v) + 2] = (float)(p2 - eps * n2 * inv);
+}
+
+// Face part: F followed by F' = {(v0', v2', v1')}: copies indexed into V', orientation reversed.
+__global__ void flipdup_faces_kernel(const int32_t *__restrict__ faces, int64_t nf, int32_t nv,
+                                     int32_t *__restrict__ out) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int32_t a = faces[3 * f], b = faces[3 * f + 1], c = faces[3 * f + 2];
+    out[3 * f] = a;
+    out[3 * f + 1] = b;
+    out[3 * f + 2] = c;
+    out[3 * (nf + f)] = a + nv;
+    out[3 * (nf + f) + 1] = c + nv;
+    out[3 * (nf + f) + 2] = b + nv;
+}
+
+cudaError_t launch_flipped_duplication(const float *verts, int64_t nv, const int32_t *faces, int64_t nf,
+                                       const FaceRec64 *rec64, const int32_t *vtx_ptr, const int32_t *vtx_corner,
+                                       double eps, float *out_verts, int32_t *out_faces, cudaStream_t s) {
+    prof_begin("flipdup_verts", s);
+    flipdup_verts_kernel<<<blocks_for(nv, 256), 256, 0, s>>>(verts, nv, rec64, vtx_ptr, vtx_corner, eps, out_verts);
+    count_launch();
+    prof_end("flipdup_verts", s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prof_begin("flipdup_faces", s);
+    flipdup_faces_kernel<<<blocks_for(nf, 256), 256, 0, s>>>(faces, nf, (int32_t)nv, out_faces);
+    count_launch();
+    prof_end("flipdup_faces", s);
+    return cudaGetLastError();
+}
+
+}  // namespace dv

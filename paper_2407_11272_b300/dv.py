@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
-    "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_flipped_duplication", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2}
@@ -103,6 +103,8 @@ def load():
     lib.dv_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, ctypes.c_int, _P]
     lib.dv_voxelize_grid.argtypes = [_P, ctypes.POINTER(_Grid), _P, _P, ctypes.c_int, ctypes.POINTER(_Report), _P]
     lib.dv_winding_backward.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P, _P]
+    lib.dv_flipped_duplication.argtypes = [_P, _P, ctypes.c_float, _P, _P, _P]
+    lib.dv_flipped_duplication.restype = ctypes.c_int
     lib.dv_profile_enable.argtypes = [ctypes.c_int]
     lib.dv_profile_enable.restype = None
     lib.dv_profile_reset.restype = None
@@ -280,6 +282,21 @@ def dv_winding_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = 
                                       ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       _stream(stream)), "dv_winding_backward")
     return out
+
+
+def dv_flipped_duplication(mesh: Mesh, verts, eps: float = 0.01, stream=None):
+    """Algorithm 2: (V u V', F u F') as new CUDA tensors [2nv,3] float32 and [2nf,3] int32."""
+    import torch
+
+    verts = _tensor(verts, torch.float32, (3,), "verts")
+    if verts.shape[0] != mesh.num_verts:
+        raise ValueError("vertex count differs from the mesh")
+    ov = torch.empty((2 * mesh.num_verts, 3), dtype=torch.float32, device=verts.device)
+    of = torch.empty((2 * mesh.num_faces, 3), dtype=torch.int32, device=verts.device)
+    _check(load().dv_flipped_duplication(mesh.handle, ctypes.c_void_p(verts.data_ptr()), float(eps),
+                                         ctypes.c_void_p(ov.data_ptr()), ctypes.c_void_p(of.data_ptr()),
+                                         _stream(stream)), "dv_flipped_duplication")
+    return ov, of
 
 
 def dv_profile_enable(on: bool = True) -> None:
