@@ -177,6 +177,20 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
 dv_status dv_winding_grid_noalloc(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf,
                                   const dv_grid *grid, float *d_out_w, void *stream);
 
+/* Eq. (4), the naive dipole discretization used by the paper for mesh morphing
+ * (§2.4: the exact winding number is almost binary, so its gradient vanishes):
+ *     W_dip(q) = (1/4pi) sum_f <n_f, (c_f - q)/|c_f - q|^3> Delta_f,
+ * c_f the face centroid, n_f its unit outward normal, Delta_f its area; a query at
+ * a centroid gets 0 from that face. Queries as in dv_winding; FP32 terms with
+ * Kahan sums across face tiles. d_out_w float32 [nq]. Stream-ordered, no sync. */
+dv_status dv_dipole_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                            float *d_out_w, void *stream);
+
+/* Adjoint of dv_dipole_winding: d_dverts float32 [nv][3] OVERWRITTEN with
+ * sum_q d_upstream[q] dW_dip(q)/dV (analytic; deterministic FP64 vertex gather). */
+dv_status dv_dipole_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                             const float *d_upstream, float *d_dverts, void *stream);
+
 /* Algorithm 2 (Flipping Duplication, §2.3): turn an open mesh into an almost
  * closed thin shell, Sigma^-2 = (V u V', F u F'), so that Algorithm 1 voxelizes
  * it like a closed mesh. d_verts float32 [nv][3] must be the vertices the mesh

@@ -441,6 +441,38 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
     return DV_OK;
 }
 
+dv_status dv_dipole_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                            float *d_out_w, void *stream) {
+    int64_t n = 0;
+    dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
+    if (st) return st;
+    if (!d_out_w) return fail(DV_ERR_INVALID_ARG, "d_out_w is NULL");
+    DeviceGuard dg(mesh->device);
+    dv::GridF gf{};
+    if (grid) gf = to_gridf(grid);
+    DV_CUDA(dv::launch_dipole_forward(mesh->rec, mesh->nf, grid ? &gf : nullptr, d_queries, n, d_out_w,
+                                      (cudaStream_t)stream));
+    return DV_OK;
+}
+
+dv_status dv_dipole_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                             const float *d_upstream, float *d_dverts, void *stream) {
+    int64_t n = 0;
+    dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
+    if (st) return st;
+    if (!d_upstream || !d_dverts) return fail(DV_ERR_INVALID_ARG, "d_upstream or d_dverts is NULL");
+    dv_mesh *m = const_cast<dv_mesh *>(mesh);
+    DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::GridF gf{};
+    if (grid) gf = to_gridf(grid);
+    const int ns = dv::dipole_bwd_splits(n, m->nf, m->num_sms);
+    if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)ns * m->nf * 9))) return st;
+    DV_CUDA(dv::launch_dipole_backward(m->rec, m->nf, grid ? &gf : nullptr, d_queries, n, d_upstream, ns, m->ws_fg, s));
+    DV_CUDA(dv::launch_gather_dverts(nullptr, m->ws_fg, ns, m->nf, m->vtx_ptr, m->vtx_corner, m->nv, d_dverts, s));
+    return DV_OK;
+}
+
 dv_status dv_flipped_duplication(const dv_mesh *mesh, const float *d_verts, float eps, float *d_out_verts,
                                  int32_t *d_out_faces, void *stream) {
     if (!mesh || !d_verts || !d_out_verts || !d_out_faces)

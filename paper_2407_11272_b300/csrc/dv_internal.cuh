@@ -188,6 +188,13 @@ cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const GridD *
                                uint8_t *occ_out, unsigned *stat_maxdiff_bits, int *stat_occ_changed, int num_sms,
                                cudaStream_t s);
 
+// dipole.cu (Eq. (4) surrogate)
+int dipole_bwd_splits(int64_t nq, int64_t nf, int num_sms);
+cudaError_t launch_dipole_forward(const FaceRec *rec, int64_t nf, const GridF *g, const float *queries, int64_t nq,
+                                  float *w_out, cudaStream_t s);
+cudaError_t launch_dipole_backward(const FaceRec *rec, int64_t nf, const GridF *g, const float *queries, int64_t nq,
+                                   const float *upstream, int nsplit, float *face_grad, cudaStream_t s);
+
 // winding_bwd.cu
 struct BwdPlan {
     int threads;

@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
-    "dv_flipped_duplication", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2}
@@ -103,6 +103,10 @@ def load():
     lib.dv_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, ctypes.c_int, _P]
     lib.dv_voxelize_grid.argtypes = [_P, ctypes.POINTER(_Grid), _P, _P, ctypes.c_int, ctypes.POINTER(_Report), _P]
     lib.dv_winding_backward.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P, _P]
+    lib.dv_dipole_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P]
+    lib.dv_dipole_winding.restype = ctypes.c_int
+    lib.dv_dipole_backward.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P, _P]
+    lib.dv_dipole_backward.restype = ctypes.c_int
     lib.dv_flipped_duplication.argtypes = [_P, _P, ctypes.c_float, _P, _P, _P]
     lib.dv_flipped_duplication.restype = ctypes.c_int
     lib.dv_profile_enable.argtypes = [ctypes.c_int]
@@ -281,6 +285,36 @@ def dv_winding_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = 
     _check(load().dv_winding_backward(mesh.handle, qp, nq_arg, ctypes.byref(g) if g is not None else None,
                                       ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       _stream(stream)), "dv_winding_backward")
+    return out
+
+
+def dv_dipole_winding(mesh: Mesh, queries=None, grid: Grid | None = None, out=None, stream=None):
+    """Eq. (4) dipole approximation of w for a query list or the voxel centres of ``grid``."""
+    import torch
+
+    qp, nq_arg, g, nq, _ = _queries_or_grid(queries, grid)
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=mesh.device)
+    out = _tensor(out, torch.float32, None, "out")
+    _check(load().dv_dipole_winding(mesh.handle, qp, nq_arg, ctypes.byref(g) if g is not None else None,
+                                    ctypes.c_void_p(out.data_ptr()), _stream(stream)), "dv_dipole_winding")
+    return out
+
+
+def dv_dipole_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = None, out=None, stream=None):
+    """dL/dV [nv,3] = sum_q upstream[q] dW_dip(q)/dV."""
+    import torch
+
+    qp, nq_arg, g, nq, _ = _queries_or_grid(queries, grid)
+    up = _tensor(upstream, torch.float32, None, "upstream")
+    if up.numel() != nq:
+        raise ValueError("upstream must have one value per query")
+    if out is None:
+        out = torch.empty((mesh.num_verts, 3), dtype=torch.float32, device=mesh.device)
+    out = _tensor(out, torch.float32, (3,), "out")
+    _check(load().dv_dipole_backward(mesh.handle, qp, nq_arg, ctypes.byref(g) if g is not None else None,
+                                     ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     _stream(stream)), "dv_dipole_backward")
     return out
 
 

@@ -1,0 +1,133 @@
+"""Mesh morphing through the differentiable voxelization (§2.4).
+
+A template mesh (icosphere) gets per-vertex offsets optimized by Adam so that its voxelization
+matches a target occupancy grid:
+
+    loss = BCE(sigmoid(s (w - 0.5)), target) + lambda * mean |L V|^2,
+
+with w the winding number on the voxel centres and L the uniform graph Laplacian of the mesh.
+``surrogate="exact"`` back-propagates through the exact winding number (Eq. (5)/(7)); for a
+closed template its gradient is zero away from the surface (the paper notes the vanishing
+gradients, §2.4), so only the Laplacian term moves the mesh. ``surrogate="dipole"`` uses the
+paper's remedy, the Eq. (4) dipole discretization, for w in the loss. Quality is always reported
+with the exact voxelization (mixed precision): IoU of occupancy against the target.
+
+    python -m paper_2407_11272_b300.morph [--steps 200] [--surrogate dipole|exact]
+
+runs the full configuration (icosphere with 40 962 vertices / 81 920 faces, radius 0.5; target a
+seeded union of 4 ellipsoids with semi-axes U[0.2, 0.5] on a 128^3 grid; lr 1e-3; sharpness 20;
+Laplacian weight 0.1) and prints one JSON line with steps/s and IoU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import dv, meshgen
+from .autograd import WindingNumber
+
+
+def ellipsoid_union_target(grid: dv.Grid, n: int = 4, seed: int = 6, axis_lo=0.2, axis_hi=0.5,
+                           centre_lo=-0.35, centre_hi=0.35) -> np.ndarray:
+    """Occupancy (float32, x fastest) of a seeded union of ellipsoids, evaluated analytically."""
+    rng = np.random.default_rng(seed)
+    ell = meshgen.random_ellipsoids(n, rng, axis_lo, axis_hi, centre_lo, centre_hi)
+    axes = [np.linspace(grid.lo[k], grid.hi[k], 2 * grid.n[k] + 1)[1::2] for k in range(3)]
+    z, y, x = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    P = np.stack([x, y, z], axis=-1).reshape(-1, 3)
+    occ = np.zeros(len(P), dtype=bool)
+    for a, c, R in ell:
+        local = (P - c) @ R  # coordinates in the ellipsoid frame (R's columns are its axes)
+        occ |= np.sum((local / a) ** 2, axis=1) <= 1.0
+    return occ.astype(np.float32)
+
+
+def uniform_laplacian_edges(faces: np.ndarray, nv: int):
+    e = np.concatenate([faces[:, [0, 1]], faces[:, [1, 2]], faces[:, [2, 0]]])
+    e = np.unique(np.sort(e, axis=1), axis=0)
+    deg = np.bincount(e.ravel(), minlength=nv).astype(np.float32)
+    return e, deg
+
+
+def laplacian(V, edges, deg):
+    """L V = (mean of neighbours) - V, per vertex."""
+    s = torch.zeros_like(V)
+    s.index_add_(0, edges[:, 0], V[edges[:, 1]])
+    s.index_add_(0, edges[:, 1], V[edges[:, 0]])
+    return s / deg[:, None].clamp_min(1.0) - V
+
+
+def iou(occ: torch.Tensor, target: torch.Tensor) -> float:
+    a = occ.bool()
+    b = target.bool()
+    return float((a & b).sum().item()) / max(float((a | b).sum().item()), 1.0)
+
+
+def morph(V0: np.ndarray, F: np.ndarray, target: np.ndarray, grid: dv.Grid, steps: int = 200, lr: float = 1e-3,
+          sharpness: float = 20.0, lap_weight: float = 0.1, surrogate: str = "dipole", device="cuda"):
+    dev = torch.device(device)
+    V0d = torch.from_numpy(V0).to(dev)
+    Fd = torch.from_numpy(F).to(dev)
+    tgt = torch.from_numpy(target).to(dev)
+    edges, deg = uniform_laplacian_edges(F, len(V0))
+    edges = torch.from_numpy(edges).long().to(dev)
+    deg = torch.from_numpy(deg).to(dev)
+    field = WindingNumber(V0d, Fd, grid=grid, kind="exact" if surrogate == "exact" else "dipole",
+                          precision="mixed")
+    judge = dv.dv_mesh_create(V0d, Fd)
+
+    def exact_iou(V):
+        dv.dv_mesh_update_verts(judge, V.detach().contiguous())
+        _, occ, _ = dv.dv_voxelize_grid(judge, grid, precision="mixed", want_w=False)
+        return iou(occ, tgt)
+
+    offsets = torch.zeros_like(V0d, requires_grad=True)
+    opt = torch.optim.Adam([offsets], lr=lr)
+    iou0 = exact_iou(V0d)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        opt.zero_grad(set_to_none=True)
+        V = V0d + offsets
+        w = field(V)
+        p = torch.sigmoid(sharpness * (w - 0.5)).clamp(1e-6, 1 - 1e-6)
+        bce = torch.nn.functional.binary_cross_entropy(p, tgt)
+        lap = laplacian(V, edges, deg).pow(2).sum(dim=1).mean()
+        loss = bce + lap_weight * lap
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    V = (V0d + offsets).detach()
+    grad_norm = float(offsets.grad.norm()) if offsets.grad is not None else 0.0
+    return {"steps": steps, "steps_per_s": steps / dt, "initial_iou": iou0, "final_iou": exact_iou(V),
+            "initial_loss": losses[0] if losses else None, "final_loss": losses[-1] if losses else None,
+            "last_grad_norm": grad_norm, "surrogate": surrogate,
+            "pairs_per_step": grid.num_queries * len(F)}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--surrogate", choices=["dipole", "exact"], default="dipole")
+    ap.add_argument("--subdiv", type=int, default=6)
+    ap.add_argument("--n", type=int, default=128)
+    a = ap.parse_args(argv)
+    V0, F = meshgen.icosphere(a.subdiv, 0.5)
+    grid = dv.Grid.cube(a.n)
+    target = ellipsoid_union_target(grid)
+    res = morph(V0, F, target, grid, steps=a.steps, lr=a.lr, surrogate=a.surrogate)
+    res.update(template=f"icosphere k={a.subdiv} ({len(V0)} V, {len(F)} F, r=0.5)", grid=a.n,
+               target="union of 4 seeded ellipsoids, semi-axes U[0.2,0.5]", lr=a.lr)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
