@@ -29,6 +29,8 @@
  *     synchronously and nothing is enqueued. Launch errors are reported as
  *     DV_ERR_CUDA. dv_last_error() gives a thread-local detail string.
  *   - There is no CPU fallback: a call either runs on the GPU or fails.
+ *   - A dv_mesh owns device memory from the stream-ordered allocator (cudaMallocAsync
+ *     on the calling stream); scratch grows on first use unless reserved.
  *   - A dv_mesh owns scratch memory. Forward calls (dv_winding, dv_voxelize_grid)
  *     on the same mesh must be ordered with each other (one stream, or events),
  *     and so must backward calls; a forward and a backward on the same mesh use
@@ -115,7 +117,8 @@ dv_status dv_mesh_update_verts(dv_mesh *mesh, const float *d_verts, void *stream
 /* Pre-size the mesh's scratch so that later forward/backward calls on `grid`
  * (may be NULL) or on query lists of up to max_list_queries points allocate
  * nothing (useful before timing or CUDA-graph capture). Without it, scratch
- * grows on first use. Synchronous (cudaMalloc). */
+ * grows on first use. Allocates on the stream of the mesh's most recent call
+ * and synchronizes that stream. */
 dv_status dv_mesh_reserve(dv_mesh *mesh, const dv_grid *grid, int64_t max_list_queries);
 
 /* Number of vertices / faces of a mesh (-1 if mesh is NULL). */
@@ -126,7 +129,10 @@ int64_t dv_mesh_num_faces(const dv_mesh *mesh);
  * of the mesh: DV_ERR_TIMEOUT if a kernel's bounded wait ran out. */
 dv_status dv_mesh_check(dv_mesh *mesh, void *stream);
 
-/* Free the mesh and its scratch. Waits for the device (cudaFree). NULL is a no-op. */
+/* Free the mesh and its scratch, in stream order on the stream of the mesh's
+ * most recent call (cudaFreeAsync: no device-wide wait). Work that uses the mesh
+ * on any other stream must be complete, or ordered before that stream, first.
+ * NULL is a no-op. */
 void dv_mesh_destroy(dv_mesh *mesh);
 
 /* Winding numbers w(q), Eq. (5), for either
@@ -176,6 +182,28 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
  * SYNCHRONIZES `stream` once, at the end, to read that check. */
 dv_status dv_winding_grid_noalloc(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf,
                                   const dv_grid *grid, float *d_out_w, void *stream);
+
+/* One request of a batch: the voxelization of a resident mesh over a grid
+ * (occupancy, optionally w) and, if d_upstream is set, its adjoint. */
+typedef struct {
+    const dv_mesh *mesh;
+    dv_grid grid;
+    float *d_out_w;          /* float32 [nx*ny*nz] or NULL */
+    uint8_t *d_out_occ;      /* uint8 [nx*ny*nz], required */
+    const float *d_upstream; /* float32 [nx*ny*nz] or NULL (no adjoint) */
+    float *d_dverts;         /* float32 [nv][3], overwritten; required with d_upstream */
+} dv_request;
+
+/* Run n independent requests (each as dv_voxelize_grid + dv_winding_backward would)
+ * as ONE CUDA graph launched on `stream`: the library captures one parallel
+ * branch per request, so the work of different requests overlaps on the GPU,
+ * then launches the graph and returns without waiting. Each request's results
+ * are identical to running it alone (same kernels, same launch plans). Used by
+ * the request server (continuous batching). Scratch is reserved on `stream`
+ * before capture; the meshes must not be used by other work until the batch is
+ * done, and a mesh may appear only once per batch. Host calls are serialized
+ * by a lock. No counterpart in the paper (serving is this library's addition). */
+dv_status dv_run_batch(const dv_request *reqs, int n, dv_precision prec, void *stream);
 
 /* Eq. (4), the naive dipole discretization used by the paper for mesh morphing
  * (§2.4: the exact winding number is almost binary, so its gradient vanishes):

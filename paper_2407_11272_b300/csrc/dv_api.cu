@@ -87,6 +87,7 @@ void prof_end(const char *name, cudaStream_t s) {
 // Mesh
 struct dv_mesh {
     int device = 0;
+    cudaStream_t last_stream = nullptr;  // stream of the most recent call (frees are ordered on it)
     int num_sms = 148;
     int64_t nv = 0, nf = 0;
     int32_t *faces = nullptr;       // device copy [nf][3]
@@ -121,34 +122,37 @@ struct DeviceGuard {
     }
 };
 
+// All device memory of a mesh comes from the stream-ordered allocator (cudaMallocAsync /
+// cudaFreeAsync on the calling stream): growing or releasing scratch never waits for the
+// whole device, so meshes can come and go while other work runs (the request server).
 template <typename T>
-dv_status grow(T *&p, int64_t &cap, int64_t need) {
+dv_status grow(T *&p, int64_t &cap, int64_t need, cudaStream_t s) {
     if (need <= cap) return DV_OK;
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     cap = 0;
-    cudaError_t e = cudaMalloc((void **)&p, (size_t)need * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void **)&p, (size_t)need * sizeof(T), s);
     if (e != cudaSuccess) {
         p = nullptr;
-        return fail(DV_ERR_OOM, "cudaMalloc(%lld bytes) failed: %s", (long long)(need * (int64_t)sizeof(T)),
+        return fail(DV_ERR_OOM, "cudaMallocAsync(%lld bytes) failed: %s", (long long)(need * (int64_t)sizeof(T)),
                     cudaGetErrorString(e));
     }
     cap = need;
     return DV_OK;
 }
 
-dv_status reserve_queries(dv_mesh *m, int64_t nq) {
+dv_status reserve_queries(dv_mesh *m, int64_t nq, cudaStream_t s) {
     if (nq <= m->cap_q) return DV_OK;
-    cudaFree(m->ws_w);
-    cudaFree(m->ws_near);
-    cudaFree(m->ws_list);
+    if (m->ws_w) cudaFreeAsync(m->ws_w, s);
+    if (m->ws_near) cudaFreeAsync(m->ws_near, s);
+    if (m->ws_list) cudaFreeAsync(m->ws_list, s);
     m->ws_w = nullptr;
     m->ws_near = nullptr;
     m->ws_list = nullptr;
     m->cap_q = 0;
-    cudaError_t e = cudaMalloc((void **)&m->ws_w, (size_t)nq * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&m->ws_near, (size_t)nq);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&m->ws_list, (size_t)nq * sizeof(int));
+    cudaError_t e = cudaMallocAsync((void **)&m->ws_w, (size_t)nq * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&m->ws_near, (size_t)nq, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&m->ws_list, (size_t)nq * sizeof(int), s);
     if (e != cudaSuccess) return fail(DV_ERR_OOM, "scratch for %lld queries: %s", (long long)nq, cudaGetErrorString(e));
     m->cap_q = nq;
     return DV_OK;
@@ -213,8 +217,9 @@ dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_gri
     const dv::FwdPlan plan = dv::plan_forward(nq, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
     const bool mixed = prec == DV_PREC_MIXED;
     dv_status st;
-    if (plan.nsplit > 1 && (st = grow(m->ws_partial, m->cap_partial, (int64_t)plan.nsplit * nq))) return st;
-    if ((mixed || w == nullptr) && (st = reserve_queries(m, nq))) return st;
+    m->last_stream = s;
+    if (plan.nsplit > 1 && (st = grow(m->ws_partial, m->cap_partial, (int64_t)plan.nsplit * nq, s))) return st;
+    if ((mixed || w == nullptr) && (st = reserve_queries(m, nq, s))) return st;
     if (w == nullptr) w = m->ws_w;
     const dv::LaunchCtx ctx{s, m->err};
     if (mixed) {
@@ -275,17 +280,10 @@ const char *dv_last_error(void) { return g_last_error.c_str(); }
 void dv_mesh_destroy(dv_mesh *m) {
     if (!m) return;
     DeviceGuard dg(m->device);
-    cudaFree(m->faces);
-    cudaFree(m->rec);
-    cudaFree(m->rec64);
-    cudaFree(m->vtx_ptr);
-    cudaFree(m->vtx_corner);
-    cudaFree(m->err);
-    cudaFree(m->ws_w);
-    cudaFree(m->ws_near);
-    cudaFree(m->ws_list);
-    cudaFree(m->ws_partial);
-    cudaFree(m->ws_fg);
+    void *bufs[] = {m->faces, m->rec,  m->rec64,   m->vtx_ptr,    m->vtx_corner, m->err,
+                    m->ws_w,  m->ws_near, m->ws_list, m->ws_partial, m->ws_fg};
+    for (void *b : bufs)
+        if (b) cudaFreeAsync(b, m->last_stream);
     delete m;
 }
 
@@ -310,12 +308,13 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
         return st;
     };
     cudaError_t e = cudaSuccess;
-    e = cudaMalloc((void **)&m->faces, (size_t)nf * 3 * sizeof(int32_t));
-    if (!e) e = cudaMalloc((void **)&m->rec, (size_t)nf * sizeof(dv::FaceRec));
-    if (!e) e = cudaMalloc((void **)&m->rec64, (size_t)nf * sizeof(dv::FaceRec64));
-    if (!e) e = cudaMalloc((void **)&m->vtx_ptr, (size_t)(nv + 1) * sizeof(int32_t));
-    if (!e) e = cudaMalloc((void **)&m->vtx_corner, (size_t)nf * 3 * sizeof(int32_t));
-    if (!e) e = cudaMalloc((void **)&m->err, 4 * sizeof(int));
+    m->last_stream = s;
+    e = cudaMallocAsync((void **)&m->faces, (size_t)nf * 3 * sizeof(int32_t), s);
+    if (!e) e = cudaMallocAsync((void **)&m->rec, (size_t)nf * sizeof(dv::FaceRec), s);
+    if (!e) e = cudaMallocAsync((void **)&m->rec64, (size_t)nf * sizeof(dv::FaceRec64), s);
+    if (!e) e = cudaMallocAsync((void **)&m->vtx_ptr, (size_t)(nv + 1) * sizeof(int32_t), s);
+    if (!e) e = cudaMallocAsync((void **)&m->vtx_corner, (size_t)nf * 3 * sizeof(int32_t), s);
+    if (!e) e = cudaMallocAsync((void **)&m->err, 4 * sizeof(int), s);
     if (e) return bail(fail(DV_ERR_OOM, "mesh storage: %s", cudaGetErrorString(e)));
     if ((e = cudaMemsetAsync(m->err, 0, 4 * sizeof(int), s))) return bail(fail(DV_ERR_CUDA, "%s", cudaGetErrorString(e)));
     if ((e = dv::launch_validate(d_verts, nv, d_faces, nf, m->err, s)))
@@ -350,6 +349,7 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
 dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
     if (!m || !d_verts) return fail(DV_ERR_INVALID_ARG, "mesh or vertex pointer is NULL");
     DeviceGuard dg(m->device);
+    m->last_stream = (cudaStream_t)stream;
     DV_CUDA(dv::launch_pack(d_verts, m->faces, m->nf, m->rec, m->rec64, (cudaStream_t)stream));
     return DV_OK;
 }
@@ -375,9 +375,11 @@ dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_quer
         part = std::max(part, fp.nsplit > 1 ? (int64_t)fp.nsplit * gq : (int64_t)0);
         fg = std::max(fg, (int64_t)bp.nsplit * m->nf * 9);
     }
-    if ((st = reserve_queries(m, nq))) return st;
-    if (part > 0 && (st = grow(m->ws_partial, m->cap_partial, part))) return st;
-    if (fg > 0 && (st = grow(m->ws_fg, m->cap_fg, fg))) return st;
+    cudaStream_t s = m->last_stream;
+    if ((st = reserve_queries(m, nq, s))) return st;
+    if (part > 0 && (st = grow(m->ws_partial, m->cap_partial, part, s))) return st;
+    if (fg > 0 && (st = grow(m->ws_fg, m->cap_fg, fg, s))) return st;
+    DV_CUDA(cudaStreamSynchronize(s));
     return DV_OK;
 }
 
@@ -433,11 +435,151 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
     const dv::BwdPlan plan = dv::plan_backward(n, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
-    if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)plan.nsplit * m->nf * 9))) return st;
+    m->last_stream = s;
+    if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)plan.nsplit * m->nf * 9, s))) return st;
     const dv::LaunchCtx ctx{s, m->err};
     DV_CUDA(dv::launch_backward(plan, m->rec, m->nf, grid ? &gf : nullptr, d_queries, n, d_upstream, m->ws_fg, ctx));
     DV_CUDA(dv::launch_gather_dverts(nullptr, m->ws_fg, plan.nsplit, m->nf, m->vtx_ptr, m->vtx_corner, m->nv, d_dverts,
                                      s));
+    return DV_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batches of independent requests as one CUDA graph (request server).
+namespace {
+
+constexpr int kBranches = 16;
+struct BatchRes {
+    bool ready = false;
+    cudaStream_t branch[kBranches];
+    cudaEvent_t fork, join[kBranches];
+    std::vector<std::pair<cudaEvent_t, cudaGraphExec_t>> pending;  // launched graphs, freed once done
+};
+std::mutex g_batch_mu;
+BatchRes g_batch[64];
+
+cudaError_t batch_resources(int dev, BatchRes **out) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    BatchRes &r = g_batch[dev];
+    if (!r.ready) {
+        cudaError_t e = cudaEventCreateWithFlags(&r.fork, cudaEventDisableTiming);
+        for (int i = 0; i < kBranches && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&r.branch[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.join[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return e;
+        r.ready = true;
+    }
+    // release the executable graphs of batches that have finished
+    for (auto it = r.pending.begin(); it != r.pending.end();) {
+        if (cudaEventQuery(it->first) == cudaSuccess) {
+            cudaGraphExecDestroy(it->second);
+            cudaEventDestroy(it->first);
+            it = r.pending.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    *out = &r;
+    return cudaSuccess;
+}
+
+// Scratch a forward / adjoint of this request will use, allocated in stream order on s.
+dv_status reserve_request(dv_mesh *m, const dv_request &r, dv_precision prec, cudaStream_t s) {
+    const int64_t nq = (int64_t)r.grid.n[0] * r.grid.n[1] * r.grid.n[2];
+    const dv::GridF gf = to_gridf(&r.grid);
+    const dv::FwdPlan fp = dv::plan_forward(nq, m->nf, true, &gf, m->num_sms);
+    dv_status st;
+    m->last_stream = s;
+    if (fp.nsplit > 1 && (st = grow(m->ws_partial, m->cap_partial, (int64_t)fp.nsplit * nq, s))) return st;
+    if ((prec == DV_PREC_MIXED || r.d_out_w == nullptr) && (st = reserve_queries(m, nq, s))) return st;
+    if (r.d_upstream) {
+        const dv::BwdPlan bp = dv::plan_backward(nq, m->nf, true, &gf, m->num_sms);
+        if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)bp.nsplit * m->nf * 9, s))) return st;
+    }
+    return DV_OK;
+}
+
+dv_status backward_on(dv_mesh *m, const dv_grid *grid, int64_t nq, const float *up, float *dverts, cudaStream_t s) {
+    const dv::GridF gf = to_gridf(grid);
+    const dv::BwdPlan plan = dv::plan_backward(nq, m->nf, true, &gf, m->num_sms);
+    dv_status st;
+    if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)plan.nsplit * m->nf * 9, s))) return st;
+    const dv::LaunchCtx ctx{s, m->err};
+    DV_CUDA(dv::launch_backward(plan, m->rec, m->nf, &gf, nullptr, nq, up, m->ws_fg, ctx));
+    DV_CUDA(dv::launch_gather_dverts(nullptr, m->ws_fg, plan.nsplit, m->nf, m->vtx_ptr, m->vtx_corner, m->nv, dverts,
+                                     s));
+    return DV_OK;
+}
+
+}  // namespace
+
+dv_status dv_run_batch(const dv_request *reqs, int n, dv_precision prec, void *stream) {
+    if (n < 0 || (n > 0 && !reqs)) return fail(DV_ERR_INVALID_ARG, "bad request array");
+    if (n == 0) return DV_OK;
+    if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED)
+        return fail(DV_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    int dev = -1;
+    for (int i = 0; i < n; ++i) {
+        const dv_request &r = reqs[i];
+        if (!r.mesh || !r.d_out_occ) return fail(DV_ERR_INVALID_ARG, "request %d: mesh and d_out_occ are required", i);
+        if (r.d_upstream && !r.d_dverts) return fail(DV_ERR_INVALID_ARG, "request %d: d_dverts is required", i);
+        dv_status st = check_grid(&r.grid);
+        if (st) return st;
+        if (dev < 0) dev = r.mesh->device;
+        if (r.mesh->device != dev) return fail(DV_ERR_INVALID_ARG, "all meshes of a batch must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (reqs[j].mesh == r.mesh) return fail(DV_ERR_INVALID_ARG, "a mesh appears twice in one batch");
+    }
+    DeviceGuard dg(dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchRes *br = nullptr;
+    DV_CUDA(batch_resources(dev, &br));
+    for (int i = 0; i < n; ++i) {
+        dv_status st = reserve_request(const_cast<dv_mesh *>(reqs[i].mesh), reqs[i], prec, s);
+        if (st) return st;
+    }
+    // Capture: fork one branch per request (round-robin over the branch streams), join all.
+    DV_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    dv_status st = DV_OK;
+    cudaError_t e = cudaEventRecord(br->fork, s);
+    const int nb = n < kBranches ? n : kBranches;
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaStreamWaitEvent(br->branch[b], br->fork, 0);
+    for (int i = 0; i < n && e == cudaSuccess && st == DV_OK; ++i) {
+        const dv_request &r = reqs[i];
+        dv_mesh *m = const_cast<dv_mesh *>(r.mesh);
+        cudaStream_t b = br->branch[i % nb];
+        const int64_t nq = (int64_t)r.grid.n[0] * r.grid.n[1] * r.grid.n[2];
+        st = run_forward(m, nullptr, nq, &r.grid, r.d_out_w, r.d_out_occ, prec, nullptr, b);
+        if (st == DV_OK && r.d_upstream) st = backward_on(m, &r.grid, nq, r.d_upstream, r.d_dverts, b);
+    }
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        e = cudaEventRecord(br->join[b], br->branch[b]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, br->join[b], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (st != DV_OK || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (st != DV_OK) return st;
+        return fail(DV_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(DV_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    e = cudaGraphLaunch(exec, s);
+    if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return fail(DV_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    }
+    cudaEvent_t done;
+    DV_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    DV_CUDA(cudaEventRecord(done, s));
+    br->pending.emplace_back(done, exec);
+    for (int i = 0; i < n; ++i) const_cast<dv_mesh *>(reqs[i].mesh)->last_stream = s;
     return DV_OK;
 }
 
@@ -448,6 +590,7 @@ dv_status dv_dipole_winding(const dv_mesh *mesh, const float *d_queries, int64_t
     if (st) return st;
     if (!d_out_w) return fail(DV_ERR_INVALID_ARG, "d_out_w is NULL");
     DeviceGuard dg(mesh->device);
+    const_cast<dv_mesh *>(mesh)->last_stream = (cudaStream_t)stream;
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
     DV_CUDA(dv::launch_dipole_forward(mesh->rec, mesh->nf, grid ? &gf : nullptr, d_queries, n, d_out_w,
@@ -467,7 +610,8 @@ dv_status dv_dipole_backward(const dv_mesh *mesh, const float *d_queries, int64_
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
     const int ns = dv::dipole_bwd_splits(n, m->nf, m->num_sms);
-    if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)ns * m->nf * 9))) return st;
+    m->last_stream = s;
+    if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)ns * m->nf * 9, s))) return st;
     DV_CUDA(dv::launch_dipole_backward(m->rec, m->nf, grid ? &gf : nullptr, d_queries, n, d_upstream, ns, m->ws_fg, s));
     DV_CUDA(dv::launch_gather_dverts(nullptr, m->ws_fg, ns, m->nf, m->vtx_ptr, m->vtx_corner, m->nv, d_dverts, s));
     return DV_OK;
@@ -482,6 +626,7 @@ dv_status dv_flipped_duplication(const dv_mesh *mesh, const float *d_verts, floa
         return fail(DV_ERR_UNSUPPORTED, "duplicated mesh exceeds the 32-bit index range");
     dv_mesh *m = const_cast<dv_mesh *>(mesh);
     DeviceGuard dg(m->device);
+    m->last_stream = (cudaStream_t)stream;
     DV_CUDA(dv::launch_flipped_duplication(d_verts, m->nv, m->faces, m->nf, m->rec64, m->vtx_ptr, m->vtx_corner,
                                            (double)eps, d_out_verts, d_out_faces, (cudaStream_t)stream));
     return DV_OK;

@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
-    "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2}
@@ -32,6 +32,11 @@ class DvError(RuntimeError):
 
 class _Grid(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("n", ctypes.c_int32 * 3)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("mesh", ctypes.c_void_p), ("grid", _Grid), ("d_out_w", ctypes.c_void_p),
+                ("d_out_occ", ctypes.c_void_p), ("d_upstream", ctypes.c_void_p), ("d_dverts", ctypes.c_void_p)]
 
 
 class _Report(ctypes.Structure):
@@ -103,6 +108,8 @@ def load():
     lib.dv_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, ctypes.c_int, _P]
     lib.dv_voxelize_grid.argtypes = [_P, ctypes.POINTER(_Grid), _P, _P, ctypes.c_int, ctypes.POINTER(_Report), _P]
     lib.dv_winding_backward.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P, _P]
+    lib.dv_run_batch.argtypes = [ctypes.POINTER(_Request), ctypes.c_int, ctypes.c_int, _P]
+    lib.dv_run_batch.restype = ctypes.c_int
     lib.dv_dipole_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P]
     lib.dv_dipole_winding.restype = ctypes.c_int
     lib.dv_dipole_backward.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P, _P]
@@ -286,6 +293,34 @@ def dv_winding_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = 
                                       ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       _stream(stream)), "dv_winding_backward")
     return out
+
+
+def dv_run_batch(requests, precision: str = "mixed", stream=None) -> None:
+    """Launch independent requests as one CUDA graph (one branch per request) on ``stream``.
+
+    ``requests``: iterable of dicts with keys mesh (Mesh), grid (Grid), occ (uint8 CUDA tensor),
+    and optionally w (float32), upstream (float32) and dverts (float32 [nv,3]). Returns at once."""
+    import torch
+
+    reqs = list(requests)
+    arr = (_Request * max(1, len(reqs)))()
+    for i, r in enumerate(reqs):
+        mesh, grid = r["mesh"], r["grid"]
+        arr[i].mesh = mesh.handle
+        arr[i].grid = grid._c()
+        occ = _tensor(r["occ"], torch.uint8, None, "occ")
+        if occ.numel() != grid.num_queries:
+            raise ValueError("occ has the wrong size")
+        arr[i].d_out_occ = occ.data_ptr()
+        w = r.get("w")
+        arr[i].d_out_w = _tensor(w, torch.float32, None, "w").data_ptr() if w is not None else None
+        up = r.get("upstream")
+        if up is not None:
+            _tensor(up, torch.float32, None, "upstream")
+            dV = _tensor(r["dverts"], torch.float32, (3,), "dverts")
+            arr[i].d_upstream = up.data_ptr()
+            arr[i].d_dverts = dV.data_ptr()
+    _check(load().dv_run_batch(arr, len(reqs), PRECISION[precision], _stream(stream)), "dv_run_batch")
 
 
 def dv_dipole_winding(mesh: Mesh, queries=None, grid: Grid | None = None, out=None, stream=None):

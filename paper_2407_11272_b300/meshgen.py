@@ -20,6 +20,7 @@ available here:
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -94,38 +95,53 @@ def icosphere(subdivisions: int, radius: float = 1.0, centre=(0.0, 0.0, 0.0)):
     return vv.astype(np.float32), faces.astype(np.int32)
 
 
+@functools.lru_cache(maxsize=128)
+def _unit_geodesic(freq: int):
+    v, f = icosahedron()
+    n = int(freq)
+    I, J = [], []
+    for i in range(n + 1):
+        for j in range(n + 1 - i):
+            I.append(i)
+            J.append(j)
+    I = np.asarray(I, dtype=np.int64)
+    J = np.asarray(J, dtype=np.int64)
+    P = len(I)
+    pid = lambda i, j: i * (n + 1) - (i * (i - 1)) // 2 + j  # noqa: E731  (index of (i, j) in I, J)
+    # Key of every point of every face: its (icosahedron vertex, integer weight) pairs, zero weights
+    # dropped, sorted by vertex; points shared along edges and corners get equal keys.
+    W = np.stack([np.broadcast_to(n - I - J, (20, P)), np.broadcast_to(I, (20, P)), np.broadcast_to(J, (20, P))],
+                 axis=-1)
+    Vid = np.broadcast_to(f[:, None, :], (20, P, 3)).copy()
+    Vid[W == 0] = -1
+    order = np.argsort(Vid, axis=-1)
+    key = np.concatenate([np.take_along_axis(Vid, order, -1), np.take_along_axis(W, order, -1)], axis=-1)
+    key = key.reshape(20 * P, 6)
+    uniq, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    inv = inv.reshape(20, P)
+    Wf = W.reshape(20 * P, 3)[first].astype(np.float64)
+    Vf = np.broadcast_to(f[:, None, :], (20, P, 3)).reshape(20 * P, 3)[first]
+    pos = (Wf[:, :1] * v[Vf[:, 0]] + Wf[:, 1:2] * v[Vf[:, 1]] + Wf[:, 2:] * v[Vf[:, 2]]) / n
+    pos /= np.linalg.norm(pos, axis=1, keepdims=True)
+    tris = []
+    for i in range(n):
+        for j in range(n - i):
+            tris.append((pid(i, j), pid(i + 1, j), pid(i, j + 1)))
+            if i + j < n - 1:
+                tris.append((pid(i + 1, j), pid(i + 1, j + 1), pid(i, j + 1)))
+    tris = np.asarray(tris, dtype=np.int64)
+    faces = inv[:, tris].reshape(-1, 3)
+    return pos, faces
+
+
 def geodesic_sphere(freq: int, radius: float = 1.0):
     """Class-I geodesic sphere: each icosahedron face split into ``freq**2`` triangles.
 
     ``freq=101`` gives 102 012 vertices and 20 * 101**2 = 204 020 faces.
     Points are shared between faces by their exact barycentric key.
     """
-    v, f = icosahedron()
-    n = int(freq)
-    keys: dict[tuple, int] = {}
-    pos: list[np.ndarray] = []
-    out_faces = []
-    for a, b, c in f:
-        A, B, C = v[a], v[b], v[c]
-        idx = {}
-        for i in range(n + 1):
-            for j in range(n + 1 - i):
-                wa, wb, wc = n - i - j, i, j
-                key = tuple(sorted((vid, w) for vid, w in ((a, wa), (b, wb), (c, wc)) if w > 0))
-                k = keys.get(key)
-                if k is None:
-                    p = (wa * A + wb * B + wc * C) / n
-                    k = len(pos)
-                    pos.append(p / np.linalg.norm(p))
-                    keys[key] = k
-                idx[(i, j)] = k
-        for i in range(n):
-            for j in range(n - i):
-                out_faces.append((idx[(i, j)], idx[(i + 1, j)], idx[(i, j + 1)]))
-                if i + j < n - 1:
-                    out_faces.append((idx[(i + 1, j)], idx[(i + 1, j + 1)], idx[(i, j + 1)]))
-    vv = np.asarray(pos, dtype=np.float64) * radius
-    return vv.astype(np.float32), np.asarray(out_faces, dtype=np.int32)
+    pos, faces = _unit_geodesic(int(freq))
+    return (pos * radius).astype(np.float32), faces.astype(np.int32)
 
 
 def _real_sh(lmax: int, theta: np.ndarray, phi: np.ndarray) -> np.ndarray:
