@@ -250,12 +250,12 @@ def run_native(args):
     def step():
         dv.dv_mesh_update_verts(mesh, Vd, stream=stream)
         if args.streams == 1:
-            dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision="mixed", stream=stream)
+            dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision=args.precision, stream=stream)
             dv.dv_winding_backward(mesh, g, grid=grid, out=dV, stream=stream)
             return
         s_fwd.wait_stream(stream)
         s_bwd.wait_stream(stream)
-        dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision="mixed", stream=s_fwd)
+        dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision=args.precision, stream=s_fwd)
         dv.dv_winding_backward(mesh, g, grid=grid, out=dV, stream=s_bwd)
         stream.wait_stream(s_fwd)
         stream.wait_stream(s_bwd)
@@ -265,7 +265,7 @@ def run_native(args):
         step()
     torch.cuda.synchronize()
     # one report outside the timed region: how many queries the FP64 pass re-evaluates
-    _, _, rep = dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision="mixed", report=True)
+    _, _, rep = dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision=args.precision, report=True)
 
     if ws > 1:
         import torch.distributed as dist
@@ -296,7 +296,8 @@ def run_native(args):
     fp32_peak = sms * 128 * sm_mhz * 1e6  # lane-ops/s, FMA counted once
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
     dname, (dms, dn) = dom
-    ops = {"fwd_grid_kahan": OPS_FWD, "fwd_grid": OPS_FWD, "bwd_grid": OPS_BWD}.get(dname, OPS_FWD)
+    ops = {"fwd_grid_kahan": OPS_FWD, "fwd_grid": OPS_FWD, "fwd_grid_fp16": OPS_FWD, "bwd_grid": OPS_BWD}.get(dname,
+                                                                                                      OPS_FWD)
     avg_s = dms / max(dn, 1) * 1e-3
     achieved = ops * pairs / avg_s if avg_s > 0 else 0.0
     roof = {"bound": "alu", "kernel": dname, "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
@@ -318,6 +319,7 @@ def run_native(args):
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "faces": nf,
                        "queries": nq, "pairs_per_step": pairs, "parallelism": f"replicas{ws}",
                        "l2": "flushed between timed steps (256 MB write)", "streams": args.streams,
+                       "precision": args.precision,
                        "fp64_reevaluated_queries": rep["n_flagged"]},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
@@ -356,7 +358,7 @@ def _e2e(args, V, F, grid, dev):
         Fd = hF.to(dev, non_blocking=True)
         gd = hg.to(dev, non_blocking=True)
         mesh = dv.dv_mesh_create(Vd, Fd)
-        w, occ, _ = dv.dv_voxelize_grid(mesh, grid, precision="mixed")
+        w, occ, _ = dv.dv_voxelize_grid(mesh, grid, precision=args.precision)
         dV = dv.dv_winding_backward(mesh, gd, grid=grid)
         hw.copy_(w, non_blocking=True)
         ho.copy_(occ, non_blocking=True)
@@ -383,6 +385,8 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="torus_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=["mixed", "kahan", "fp32", "fp16"], default="mixed",
+                    help="forward arithmetic (mixed = Kahan FP32 + FP64 re-evaluation, the default)")
     ap.add_argument("--streams", type=int, choices=[1, 2], default=1,
                     help="1: one stream (default); 2: forward and adjoint on two streams")
     args = ap.parse_args(argv)

@@ -66,8 +66,11 @@ typedef enum {
  *   DV_PREC_MIXED       DV_PREC_FP32_KAHAN, then every query with |w - 0.5| < 1e-3 or
  *                       within 1e-3 (Euclidean) of a triangle is re-evaluated over all
  *                       faces in FP64 on the GPU and its w / occupancy overwritten.
- * The paper ran half precision (§3.1); these modes are this library's choice. */
-typedef enum { DV_PREC_FP32 = 0, DV_PREC_FP32_KAHAN = 1, DV_PREC_MIXED = 2 } dv_precision;
+ *   DV_PREC_FP16        ablation of the paper's half precision (§3.1): per-pair terms in
+ *                       packed FP16 arithmetic (offsets and their partial sums in FP32),
+ *                       FP32 Kahan sums; grid queries only; NOT accurate to 1e-4.
+ * The paper ran half precision (§3.1); the other modes are this library's choice. */
+typedef enum { DV_PREC_FP32 = 0, DV_PREC_FP32_KAHAN = 1, DV_PREC_MIXED = 2, DV_PREC_FP16 = 3 } dv_precision;
 
 /* Cell-centred voxel grid over the box [lo, hi] (§3: meshes normalized to [-1,1],
  * resolutions 32..256; any n >= 1 per axis is accepted). */

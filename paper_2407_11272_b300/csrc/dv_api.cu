@@ -210,8 +210,10 @@ dv_status check_queries(const dv_mesh *m, const float *q, int64_t nq, const dv_g
 
 dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_grid *grid, float *w, uint8_t *occ,
                       dv_precision prec, dv_report *report, cudaStream_t s) {
-    if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED)
+    if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED && prec != DV_PREC_FP16)
         return fail(DV_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (prec == DV_PREC_FP16 && queries)
+        return fail(DV_ERR_UNSUPPORTED, "the FP16 ablation is implemented for grid queries only");
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
     const dv::FwdPlan plan = dv::plan_forward(nq, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
@@ -230,7 +232,8 @@ dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_gri
     int *list = mixed ? m->ws_list : nullptr;
     int *count = mixed ? m->err + 1 : nullptr;
     const uint8_t *nearf = mixed ? m->ws_near : nullptr;
-    DV_CUDA(dv::launch_forward(plan, m->rec, m->nf, grid ? &gf : nullptr, queries, nq, prec != DV_PREC_FP32,
+    const int arith = prec == DV_PREC_FP16 ? dv::kArithFP16 : (prec == DV_PREC_FP32 ? dv::kArithFP32 : dv::kArithKahan);
+    DV_CUDA(dv::launch_forward(plan, m->rec, m->nf, grid ? &gf : nullptr, queries, nq, arith,
                                m->ws_partial, w, occ, nearf, list, count, ctx));
     if (plan.nsplit > 1)
         DV_CUDA(dv::launch_split_reduce(plan, m->ws_partial, nq, w, occ, nearf, list, count, s));
@@ -517,7 +520,7 @@ dv_status backward_on(dv_mesh *m, const dv_grid *grid, int64_t nq, const float *
 dv_status dv_run_batch(const dv_request *reqs, int n, dv_precision prec, void *stream) {
     if (n < 0 || (n > 0 && !reqs)) return fail(DV_ERR_INVALID_ARG, "bad request array");
     if (n == 0) return DV_OK;
-    if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED)
+    if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED && prec != DV_PREC_FP16)
         return fail(DV_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     int dev = -1;
     for (int i = 0; i < n; ++i) {

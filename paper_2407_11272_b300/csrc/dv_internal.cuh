@@ -172,8 +172,11 @@ struct FwdPlan {
     int64_t faces_per_split;
 };
 FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms);
+// Per-pair arithmetic of the forward: FP32 with a plain sum, FP32 with Kahan across face tiles,
+// or the FP16 ablation (half2 per-pair terms, FP32 Kahan sums; grid queries only).
+constexpr int kArithFP32 = 0, kArithKahan = 1, kArithFP16 = 2;
 cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
-                           int64_t nq, bool kahan, float2 *partial, float *w_out, uint8_t *occ_out,
+                           int64_t nq, int arith, float2 *partial, float *w_out, uint8_t *occ_out,
                            const uint8_t *near_flag, int *flag_list, int *flag_count, const LaunchCtx &ctx);
 cudaError_t launch_split_reduce(const FwdPlan &p, const float2 *partial, int64_t nq, float *w_out, uint8_t *occ_out,
                                 const uint8_t *near_flag, int *flag_list, int *flag_count, cudaStream_t s);

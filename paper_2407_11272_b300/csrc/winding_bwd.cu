@@ -77,7 +77,7 @@ __device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx
         lc2 = fmaxf(lc2, 1e-30f);
     }
     const float ia = rsqrt_approx(la2), ib = rsqrt_approx(lb2), ic = rsqrt_approx(lc2);
-    const float la = sqrt_approx(la2), lb = sqrt_approx(lb2), lc = sqrt_approx(lc2);
+    const float la = la2 * ia, lb = lb2 * ib, lc = lc2 * ic;  // multiply, not a second MUFU op per vertex
     const float ab = fmaf(ax, bx, R.Pab), bc = fmaf(bx, cx, R.Pbc), ca = fmaf(cx, ax, R.Pca);
     const float N = fmaf(ax, F.nx, R.Nyz);
     const float tc = fmaf(la, lb, ab);  // |a||b| + a.b, also the numerator of alpha_c
@@ -107,6 +107,55 @@ __device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx
     X[4] = fmaf(alA, ax, X[4]);
     X[5] = fmaf(alB, ax, X[5]);
     X[6] = fmaf(alC, ax, X[6]);
+}
+
+// The same arithmetic as bwd_pair<false> for two queries of one row at once, every FP32 operation
+// a packed FP32x2 instruction (Blackwell FFMA2/FADD2/FMUL2: one issue slot for both queries);
+// only the MUFU reciprocal square roots and reciprocals stay scalar. The even and odd queries of
+// the row accumulate in the two halves of S2/X2.
+struct FaceF2 {
+    float2 v0x, v1x, v2x, nx;
+};
+struct RowB2 {
+    float2 La, Lb, Lc, Pab, Pbc, Pca, Nyz;
+};
+
+__device__ __forceinline__ void bwd_pair2(const FaceF2 &F, const RowB2 &R, float2 nqx, float2 g, float2 (&S)[7],
+                                          float2 (&X)[7]) {
+    const float2 ax = __fadd2_rn(F.v0x, nqx), bx = __fadd2_rn(F.v1x, nqx), cx = __fadd2_rn(F.v2x, nqx);
+    const float2 la2 = __ffma2_rn(ax, ax, R.La), lb2 = __ffma2_rn(bx, bx, R.Lb), lc2 = __ffma2_rn(cx, cx, R.Lc);
+    const float2 ia = make_float2(rsqrt_approx(la2.x), rsqrt_approx(la2.y));
+    const float2 ib = make_float2(rsqrt_approx(lb2.x), rsqrt_approx(lb2.y));
+    const float2 ic = make_float2(rsqrt_approx(lc2.x), rsqrt_approx(lc2.y));
+    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
+    const float2 ab = __ffma2_rn(ax, bx, R.Pab), bc = __ffma2_rn(bx, cx, R.Pbc), ca = __ffma2_rn(cx, ax, R.Pca);
+    const float2 N = __ffma2_rn(ax, F.nx, R.Nyz);
+    const float2 tc = __ffma2_rn(la, lb, ab);
+    float2 D = __fmul2_rn(tc, lc);
+    D = __ffma2_rn(la, bc, D);
+    D = __ffma2_rn(lb, ca, D);
+    const float2 den = __ffma2_rn(N, N, __fmul2_rn(D, D));
+    const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
+    const float2 gr = __fmul2_rn(g, r);
+    const float2 cD = __fmul2_rn(gr, D), cN = __fmul2_rn(gr, N);
+    const float2 P = __fmul2_rn(cN, la), Qb = __fmul2_rn(cN, lb), Rc = __fmul2_rn(cN, lc);
+    const float2 alA = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lb, lc, bc), ia));
+    const float2 alB = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lc, la, ca), ib));
+    const float2 alC = __fmul2_rn(cN, __fmul2_rn(tc, ic));
+    S[0] = __fadd2_rn(S[0], cD);
+    S[1] = __fadd2_rn(S[1], P);
+    S[2] = __fadd2_rn(S[2], Qb);
+    S[3] = __fadd2_rn(S[3], Rc);
+    S[4] = __fadd2_rn(S[4], alA);
+    S[5] = __fadd2_rn(S[5], alB);
+    S[6] = __fadd2_rn(S[6], alC);
+    X[0] = __ffma2_rn(cD, ax, X[0]);
+    X[1] = __ffma2_rn(P, ax, X[1]);
+    X[2] = __ffma2_rn(Qb, ax, X[2]);
+    X[3] = __ffma2_rn(Rc, ax, X[3]);
+    X[4] = __ffma2_rn(alA, ax, X[4]);
+    X[5] = __ffma2_rn(alB, ax, X[5]);
+    X[6] = __ffma2_rn(alC, ax, X[6]);
 }
 
 struct Kahan {
@@ -190,19 +239,31 @@ __device__ __forceinline__ bool all_finite(const float (&S)[7], const float (&X)
     return isfinite(t);
 }
 
+// Staged queries of a window, in pairs: for query i (pair p = i/2, k = i%2) the window holds
+// -x_i at wf[4p + k] and the upstream g_i at wf[4p + 2 + k], so one 16-byte load gives the
+// packed (-x, -x') and (g, g') operands of two consecutive queries.
+__device__ __forceinline__ float win_nqx(const float *wf, int64_t i) { return wf[4 * (i >> 1) + (i & 1)]; }
+__device__ __forceinline__ float win_g(const float *wf, int64_t i) { return wf[4 * (i >> 1) + 2 + (i & 1)]; }
+
 __global__ void __launch_bounds__(kBwdThreads) bwd_grid_kernel(const BwdArgs a) {
-    __shared__ float2 win[kBwdWin];  // (upstream g, query x) of the staged queries
+    __shared__ __align__(16) float wf[2 * kBwdWin];
     const int64_t f = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     const FaceF F = load_face(a.rec, f < a.nf ? f : a.nf - 1);
+    FaceF2 F2;
+    F2.v0x = make_float2(F.v0x, F.v0x);
+    F2.v1x = make_float2(F.v1x, F.v1x);
+    F2.v2x = make_float2(F.v2x, F.v2x);
+    F2.nx = make_float2(F.nx, F.nx);
     const int nx = a.g.n[0], ny = a.g.n[1];
     const int64_t nrows = (int64_t)a.g.n[1] * a.g.n[2];
     const int64_t r0 = (int64_t)blockIdx.y * a.rows_per_split;
     const int64_t r1 = r0 + a.rows_per_split < nrows ? r0 + a.rows_per_split : nrows;
     FaceSums fs;
     fs.zero();
-    // Rows are processed in windows of whole rows when a row fits the window; otherwise in
-    // pieces, always through the guarded path.
+    // Rows are processed in windows of whole rows when a row fits the window (packed pairs of
+    // queries when the row length is even); longer rows go in pieces through the guarded path.
     const bool whole = nx <= kBwdWin;
+    const bool packed = whole && (nx % 2 == 0);
     const int rows_per_win = whole ? kBwdWin / nx : 1;
     for (int64_t rw = r0; rw < r1; rw += rows_per_win) {
         const int64_t rend = rw + rows_per_win < r1 ? rw + rows_per_win : r1;
@@ -213,7 +274,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_grid_kernel(const BwdArgs a) 
             __syncthreads();
             for (int64_t i = threadIdx.x; i < len; i += kBwdThreads) {
                 const int ix = whole ? (int)(i % nx) : x0 + (int)i;
-                win[i] = make_float2(a.upstream[base + i], __fmaf_rn((float)ix + 0.5f, a.g.h[0], a.g.lo[0]));
+                wf[4 * (i >> 1) + (i & 1)] = -__fmaf_rn((float)ix + 0.5f, a.g.h[0], a.g.lo[0]);
+                wf[4 * (i >> 1) + 2 + (i & 1)] = a.upstream[base + i];
             }
             __syncthreads();
             const int64_t nr = whole ? rend - rw : 1;
@@ -223,29 +285,45 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_grid_kernel(const BwdArgs a) 
                 const float qy = __fmaf_rn((float)iy + 0.5f, a.g.h[1], a.g.lo[1]);
                 const float qz = __fmaf_rn((float)iz + 0.5f, a.g.h[2], a.g.lo[2]);
                 const RowB R = row_b(F, qy, qz);
-                const float2 *wrow = win + rr * (whole ? nx : 0);
+                const int64_t i0 = whole ? rr * nx : 0;  // first window index of this row
                 float S[7], X[7];
 #pragma unroll
                 for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-                if (whole) {
-#pragma unroll 2
-                    for (int ix = 0; ix < nx; ++ix) {
-                        const float2 gq = wrow[ix];
-                        bwd_pair<false>(F, R, gq.y, gq.x, S, X);
-                    }
-                    if (!all_finite(S, X)) {
+                if (packed) {
+                    RowB2 R2;
+                    R2.La = make_float2(R.La, R.La);
+                    R2.Lb = make_float2(R.Lb, R.Lb);
+                    R2.Lc = make_float2(R.Lc, R.Lc);
+                    R2.Pab = make_float2(R.Pab, R.Pab);
+                    R2.Pbc = make_float2(R.Pbc, R.Pbc);
+                    R2.Pca = make_float2(R.Pca, R.Pca);
+                    R2.Nyz = make_float2(R.Nyz, R.Nyz);
+                    float2 S2[7], X2[7];
 #pragma unroll
-                        for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-                        for (int ix = 0; ix < nx; ++ix) {
-                            const float2 gq = wrow[ix];
-                            bwd_pair<true>(F, R, gq.y, gq.x, S, X);
-                        }
+                    for (int k = 0; k < 7; ++k) S2[k] = X2[k] = make_float2(0.f, 0.f);
+                    const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
+#pragma unroll 2
+                    for (int p = 0; p < nx / 2; ++p) {
+                        const float4 q = wp[p];
+                        bwd_pair2(F2, R2, make_float2(q.x, q.y), make_float2(q.z, q.w), S2, X2);
                     }
-                } else {
-                    for (int ix = 0; ix < xlen; ++ix) {
-                        const float2 gq = wrow[ix];
-                        bwd_pair<true>(F, R, gq.y, gq.x, S, X);
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) {
+                        S[k] = S2[k].x + S2[k].y;
+                        X[k] = X2[k].x + X2[k].y;
                     }
+                } else if (whole) {
+#pragma unroll 4
+                    for (int ix = 0; ix < nx; ++ix)
+                        bwd_pair<false>(F, R, -win_nqx(wf, i0 + ix), win_g(wf, i0 + ix), S, X);
+                }
+                if (!whole || !all_finite(S, X)) {
+                    // pieces of long rows, and rows whose unguarded sums are not finite (a query on a
+                    // vertex or on an edge line): the guarded scalar path
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
+                    for (int ix = 0; ix < xlen; ++ix)
+                        bwd_pair<true>(F, R, -win_nqx(wf, i0 + ix), win_g(wf, i0 + ix), S, X);
                 }
                 fs.fold(S, X, R.ay, R.az);
             }

@@ -23,7 +23,9 @@
 //   * Compensated summation: plain FP32 over a tile of 64 faces, Kahan across tiles.
 //   * Split over faces (grid.y) for small query counts; partial sums (sum, -compensation) go
 //     to a scratch buffer and are reduced in FP64, in fixed order, by split_reduce_kernel.
+#include <cuda_fp16.h>
 #include <math.h>
+#include <string.h>
 
 #include "dv_internal.cuh"
 
@@ -115,10 +117,103 @@ __device__ __forceinline__ RowPart row_part(const FaceRec &r, float qy, float La
     return p;
 }
 
-// One face against the thread's QY x QX grid queries. Returns true if every pair took the fast path.
+// One face against the thread's QY x QX grid queries, x-adjacent queries paired: every FP32
+// operation of the fast path is one packed FP32x2 instruction (Blackwell FFMA2/FADD2/FMUL2) for
+// two queries; MUFU square roots and reciprocals stay scalar. nqx holds the negated query x
+// coordinates in pairs. Returns true if every pair took the fast path. The SLOW variant adds
+// ATAN2 for exactly the pairs the fast path skipped, recomputing N and D with scalar _rn
+// operations in the same order (bit-identical to the packed ones).
 template <int QX, int QY, bool SLOW>
-__device__ __forceinline__ bool face_grid(const FaceRec &r, const float (&qx)[QX], const float (&qy)[QY], float qz,
-                                          float (&acc)[QY][QX]) {
+__device__ __forceinline__ bool face_grid(const FaceRec &r, const float2 (&nqx)[QX / 2], const float (&qy)[QY],
+                                          float qz, float2 (&acc)[QY][QX / 2]) {
+    static_assert(QX % 2 == 0, "queries are paired along x");
+    const float az = __fsub_rn(r.r0.z, qz), bz = __fsub_rn(r.r1.z, qz), cz = __fsub_rn(r.r2.z, qz);
+    const float Laz = __fmul_rn(az, az), Lbz = __fmul_rn(bz, bz), Lcz = __fmul_rn(cz, cz);
+    const float Pabz = __fmul_rn(az, bz), Pbcz = __fmul_rn(bz, cz), Pcaz = __fmul_rn(cz, az);
+    const float Nz = __fmul_rn(az, r.r2.w);
+    const float2 v0x = make_float2(r.r0.x, r.r0.x), v1x = make_float2(r.r1.x, r.r1.x), v2x = make_float2(r.r2.x, r.r2.x);
+    float2 ax[QX / 2], bx[QX / 2], cx[QX / 2];
+#pragma unroll
+    for (int j = 0; j < QX / 2; ++j) {
+        ax[j] = __fadd2_rn(v0x, nqx[j]);
+        bx[j] = __fadd2_rn(v1x, nqx[j]);
+        cx[j] = __fadd2_rn(v2x, nqx[j]);
+    }
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < QY; ++i) {
+        const RowPart p = row_part(r, qy[i], Laz, Lbz, Lcz, Pabz, Pbcz, Pcaz, Nz);
+        if (!SLOW) {
+            const float2 La = make_float2(p.La, p.La), Lb = make_float2(p.Lb, p.Lb), Lc = make_float2(p.Lc, p.Lc);
+            const float2 Pab = make_float2(p.Pab, p.Pab), Pbc = make_float2(p.Pbc, p.Pbc);
+            const float2 Pca = make_float2(p.Pca, p.Pca), Nyz = make_float2(p.Nyz, p.Nyz);
+            const float2 n8x = make_float2(r.r0.w, r.r0.w);
+            const float2 C0 = make_float2(DV_ATAN_C0, DV_ATAN_C0), C1 = make_float2(DV_ATAN_C1, DV_ATAN_C1);
+            const float2 C2 = make_float2(DV_ATAN_C2, DV_ATAN_C2);
+#pragma unroll
+            for (int j = 0; j < QX / 2; ++j) {
+                const float2 la2 = __ffma2_rn(ax[j], ax[j], La);
+                const float2 lb2 = __ffma2_rn(bx[j], bx[j], Lb);
+                const float2 lc2 = __ffma2_rn(cx[j], cx[j], Lc);
+                const float2 la = make_float2(sqrt_approx(la2.x), sqrt_approx(la2.y));
+                const float2 lb = make_float2(sqrt_approx(lb2.x), sqrt_approx(lb2.y));
+                const float2 lc = make_float2(sqrt_approx(lc2.x), sqrt_approx(lc2.y));
+                const float2 ab = __ffma2_rn(ax[j], bx[j], Pab);
+                const float2 bc = __ffma2_rn(bx[j], cx[j], Pbc);
+                const float2 ca = __ffma2_rn(cx[j], ax[j], Pca);
+                const float2 N8 = __ffma2_rn(ax[j], n8x, Nyz);
+                float2 D = __fmul2_rn(__ffma2_rn(la, lb, ab), lc);
+                D = __ffma2_rn(la, bc, D);
+                D = __ffma2_rn(lb, ca, D);
+                const bool p0 = D.x > fabsf(N8.x), p1 = D.y > fabsf(N8.y);
+                ok = ok && p0 && p1;
+                float2 v = __fmul2_rn(N8, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
+                v.x = p0 ? v.x : 0.0f;
+                v.y = p1 ? v.y : 0.0f;
+                const float2 sq = __fmul2_rn(v, v);
+                const float2 P = __ffma2_rn(__ffma2_rn(C2, sq, C1), sq, C0);
+                acc[i][j] = __ffma2_rn(v, P, acc[i][j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < QX / 2; ++j) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const float axs = k ? ax[j].y : ax[j].x, bxs = k ? bx[j].y : bx[j].x, cxs = k ? cx[j].y : cx[j].x;
+                    float m;
+                    const PairOut o = pair_terms(axs, bxs, cxs, p.La, p.Lb, p.Lc, p.Pab, p.Pbc, p.Pca, p.Nyz, r.r0.w, m);
+                    const float t = slow_term(o, m);
+                    if (k)
+                        acc[i][j].y = __fadd_rn(acc[i][j].y, t);
+                    else
+                        acc[i][j].x = __fadd_rn(acc[i][j].x, t);
+                }
+            }
+        }
+    }
+    return ok;
+}
+
+// FP16 ablation of face_grid (the paper computed in half precision, §3.1): offsets and their
+// (y,z) partial sums in FP32 as above, then every per-pair operation in packed half2 arithmetic
+// (two x-adjacent queries per instruction), the fast-path arctangent in half, and the term
+// accumulated in FP32. Pairs failing the half fast-path test are added by the SLOW variant
+// through the FP32 formula and atan2f. Quantifies half precision; not an accurate mode.
+__device__ __forceinline__ unsigned h2_bits(__half2 v) {
+    unsigned u;
+    memcpy(&u, &v, sizeof(u));
+    return u;
+}
+__device__ __forceinline__ __half2 bits_h2(unsigned u) {
+    __half2 v;
+    memcpy(&v, &u, sizeof(u));
+    return v;
+}
+
+template <int QX, int QY, bool SLOW>
+__device__ __forceinline__ bool face_grid_h(const FaceRec &r, const float (&qx)[QX], const float (&qy)[QY], float qz,
+                                            float (&acc)[QY][QX]) {
+    static_assert(QX % 2 == 0, "half2 path pairs x-adjacent queries");
     const float az = __fsub_rn(r.r0.z, qz), bz = __fsub_rn(r.r1.z, qz), cz = __fsub_rn(r.r2.z, qz);
     const float Laz = __fmul_rn(az, az), Lbz = __fmul_rn(bz, bz), Lcz = __fmul_rn(cz, cz);
     const float Pabz = __fmul_rn(az, bz), Pbcz = __fmul_rn(bz, cz), Pcaz = __fmul_rn(cz, az);
@@ -130,18 +225,57 @@ __device__ __forceinline__ bool face_grid(const FaceRec &r, const float (&qx)[QX
         bx[j] = __fsub_rn(r.r1.x, qx[j]);
         cx[j] = __fsub_rn(r.r2.x, qx[j]);
     }
+    __half2 ax2[QX / 2], bx2[QX / 2], cx2[QX / 2];
+#pragma unroll
+    for (int j = 0; j < QX / 2; ++j) {
+        ax2[j] = __floats2half2_rn(ax[2 * j], ax[2 * j + 1]);
+        bx2[j] = __floats2half2_rn(bx[2 * j], bx[2 * j + 1]);
+        cx2[j] = __floats2half2_rn(cx[2 * j], cx[2 * j + 1]);
+    }
+    const __half2 n8x = __float2half2_rn(r.r0.w);
+    const __half2 Dmin = __float2half2_rn(6.103515625e-05f);
+    const __half2 C0 = __float2half2_rn(DV_ATAN_C0), C1 = __float2half2_rn(DV_ATAN_C1),
+                  C2 = __float2half2_rn(DV_ATAN_C2);
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < QY; ++i) {
         const RowPart p = row_part(r, qy[i], Laz, Lbz, Lcz, Pabz, Pbcz, Pcaz, Nz);
+        const __half2 La = __float2half2_rn(p.La), Lb = __float2half2_rn(p.Lb), Lc = __float2half2_rn(p.Lc);
+        const __half2 Pab = __float2half2_rn(p.Pab), Pbc = __float2half2_rn(p.Pbc), Pca = __float2half2_rn(p.Pca);
+        const __half2 Nyz = __float2half2_rn(p.Nyz);
 #pragma unroll
-        for (int j = 0; j < QX; ++j) {
-            float m;
-            const PairOut o = pair_terms(ax[j], bx[j], cx[j], p.La, p.Lb, p.Lc, p.Pab, p.Pbc, p.Pca, p.Nyz, r.r0.w, m);
-            if (SLOW)
-                acc[i][j] = __fadd_rn(acc[i][j], slow_term(o, m));
-            else
-                acc[i][j] = fast_term_fma(o, acc[i][j], ok);
+        for (int j = 0; j < QX / 2; ++j) {
+            const __half2 la = h2sqrt(__hfma2(ax2[j], ax2[j], La));
+            const __half2 lb = h2sqrt(__hfma2(bx2[j], bx2[j], Lb));
+            const __half2 lc = h2sqrt(__hfma2(cx2[j], cx2[j], Lc));
+            const __half2 ab = __hfma2(ax2[j], bx2[j], Pab);
+            const __half2 bc = __hfma2(bx2[j], cx2[j], Pbc);
+            const __half2 ca = __hfma2(cx2[j], ax2[j], Pca);
+            const __half2 N8 = __hfma2(ax2[j], n8x, Nyz);
+            __half2 D = __hmul2(__hfma2(la, lb, ab), lc);
+            D = __hfma2(la, bc, D);
+            D = __hfma2(lb, ca, D);
+            // fast path needs D > |8N| and D > 2^-14, so that 1/D stays finite in half precision
+            const unsigned m = __hgt2_mask(D, __hmax2(__habs2(N8), Dmin));
+            if (!SLOW) {
+                ok = ok && m == 0xffffffffu;
+                const __half2 v = bits_h2(h2_bits(__hmul2(N8, h2rcp(D))) & m);
+                const __half2 sq = __hmul2(v, v);
+                const __half2 t = __hmul2(v, __hfma2(__hfma2(C2, sq, C1), sq, C0));
+                acc[i][2 * j] = __fadd_rn(acc[i][2 * j], __low2float(t));
+                acc[i][2 * j + 1] = __fadd_rn(acc[i][2 * j + 1], __high2float(t));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if ((m >> (16 * k)) & 0xffffu) continue;  // taken by the half fast path
+                    float mn;
+                    const PairOut o = pair_terms(ax[2 * j + k], bx[2 * j + k], cx[2 * j + k], p.La, p.Lb, p.Lc, p.Pab,
+                                                 p.Pbc, p.Pca, p.Nyz, r.r0.w, mn);
+                    if (mn >= 1.17549435e-38f)
+                        acc[i][2 * j + k] = __fadd_rn(acc[i][2 * j + k], atan2f(__fadd_rn(o.N8, 0.0f),
+                                                                                __fmul_rn(kNormalScale, o.D)));
+                }
+            }
         }
     }
     return ok;
@@ -246,7 +380,7 @@ __device__ __forceinline__ bool run_face_tiles(TilePipe &pp, int *err, Body &&bo
 }
 
 // ---------------------------------------------------------------------------------------------
-template <int QX, int QY, bool KAHAN>
+template <int QX, int QY, bool KAHAN, bool HALF>
 __global__ void __launch_bounds__(kFwdThreads, 2) fwd_grid_kernel(const FwdArgs a) {
     __shared__ __align__(128) FaceRec sm[kStages][kTileFaces];
     __shared__ __align__(8) uint64_t full[kStages];
@@ -267,16 +401,22 @@ __global__ void __launch_bounds__(kFwdThreads, 2) fwd_grid_kernel(const FwdArgs 
     float qx[QX], qy[QY];
 #pragma unroll
     for (int j = 0; j < QX; ++j) qx[j] = __fmaf_rn((float)(tx * QX + j) + 0.5f, a.g.h[0], a.g.lo[0]);
+    float2 nqx[QX / 2];
+#pragma unroll
+    for (int j = 0; j < QX / 2; ++j) nqx[j] = make_float2(-qx[2 * j], -qx[2 * j + 1]);
 #pragma unroll
     for (int i = 0; i < QY; ++i) qy[i] = __fmaf_rn((float)(ty * QY + i) + 0.5f, a.g.h[1], a.g.lo[1]);
     const float qz = __fmaf_rn((float)z + 0.5f, a.g.h[2], a.g.lo[2]);
 
+    // acc2: packed per pair of x-adjacent queries (FP32 path); acc: per query (FP16 path)
+    float2 acc2[QY][QX / 2];
     float acc[QY][QX];
 #pragma unroll
     for (int i = 0; i < QY; ++i)
 #pragma unroll
         for (int j = 0; j < QX; ++j) {
             acc[i][j] = 0.0f;
+            if (j % 2 == 0) acc2[i][j / 2] = make_float2(0.0f, 0.0f);
             if (KAHAN) kst[i * QX + j][threadIdx.x] = make_float2(0.0f, 0.0f);
         }
 
@@ -295,8 +435,13 @@ __global__ void __launch_bounds__(kFwdThreads, 2) fwd_grid_kernel(const FwdArgs 
 #pragma unroll 1
             for (int k = 0; k < cnt; ++k) {
                 const FaceRec r = tilep[k];
-                const bool ok = face_grid<QX, QY, false>(r, qx, qy, qz, acc);
-                if (__any_sync(kFull, !ok)) face_grid<QX, QY, true>(r, qx, qy, qz, acc);
+                if (HALF) {
+                    const bool ok = face_grid_h<QX, QY, false>(r, qx, qy, qz, acc);
+                    if (__any_sync(kFull, !ok)) face_grid_h<QX, QY, true>(r, qx, qy, qz, acc);
+                } else {
+                    const bool ok = face_grid<QX, QY, false>(r, nqx, qy, qz, acc2);
+                    if (__any_sync(kFull, !ok)) face_grid<QX, QY, true>(r, nqx, qy, qz, acc2);
+                }
             }
         },
         [&]() {
@@ -306,9 +451,11 @@ __global__ void __launch_bounds__(kFwdThreads, 2) fwd_grid_kernel(const FwdArgs 
 #pragma unroll
                     for (int j = 0; j < QX; ++j) {
                         float2 k = kst[i * QX + j][threadIdx.x];
-                        kahan_add(k.x, k.y, acc[i][j]);
+                        const float t = HALF ? acc[i][j] : (j % 2 ? acc2[i][j / 2].y : acc2[i][j / 2].x);
+                        kahan_add(k.x, k.y, t);
                         kst[i * QX + j][threadIdx.x] = k;
                         acc[i][j] = 0.0f;
+                        if (j % 2) acc2[i][j / 2] = make_float2(0.0f, 0.0f);
                     }
             }
         });
@@ -323,7 +470,8 @@ __global__ void __launch_bounds__(kFwdThreads, 2) fwd_grid_kernel(const FwdArgs 
             const int ix = tx * QX + j;
             if (ix >= nx) continue;
             const int64_t idx = ((int64_t)z * ny + iy) * nx + ix;
-            const float2 k = KAHAN ? kst[i * QX + j][threadIdx.x] : make_float2(acc[i][j], 0.0f);
+            const float plain = HALF ? acc[i][j] : (j % 2 ? acc2[i][j / 2].y : acc2[i][j / 2].x);
+            const float2 k = KAHAN ? kst[i * QX + j][threadIdx.x] : make_float2(plain, 0.0f);
             const float s = k.x, c = k.y;
             if (a.nsplit > 1)
                 a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(s, -c);
@@ -447,7 +595,7 @@ FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_
 }
 
 cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
-                           int64_t nq, bool kahan, float2 *partial, float *w_out, uint8_t *occ_out,
+                           int64_t nq, int arith, float2 *partial, float *w_out, uint8_t *occ_out,
                            const uint8_t *near_flag, int *flag_list, int *flag_count, const LaunchCtx &ctx) {
     FwdArgs a{};
     a.rec = rec;
@@ -465,7 +613,10 @@ cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, con
     a.flag_count = flag_count;
     a.err = ctx.d_err;
     dim3 grid((unsigned)p.qblocks, (unsigned)p.nsplit);
-    const char *name = queries ? (kahan ? "fwd_list_kahan" : "fwd_list") : (kahan ? "fwd_grid_kahan" : "fwd_grid");
+    const bool kahan = arith != kArithFP32;
+    if (arith == kArithFP16 && queries) return cudaErrorNotSupported;
+    const char *name = queries ? (kahan ? "fwd_list_kahan" : "fwd_list")
+                               : (arith == kArithFP16 ? "fwd_grid_fp16" : (kahan ? "fwd_grid_kahan" : "fwd_grid"));
     prof_begin(name, ctx.stream);
     if (queries) {
         if (kahan)
@@ -473,10 +624,12 @@ cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, con
         else
             fwd_list_kernel<kListQ, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
     } else {
-        if (kahan)
-            fwd_grid_kernel<kGridQX, kGridQY, true><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
+        if (arith == kArithFP16)
+            fwd_grid_kernel<kGridQX, kGridQY, true, true><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
+        else if (kahan)
+            fwd_grid_kernel<kGridQX, kGridQY, true, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
         else
-            fwd_grid_kernel<kGridQX, kGridQY, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
+            fwd_grid_kernel<kGridQX, kGridQY, false, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
     }
     count_launch();
     prof_end(name, ctx.stream);

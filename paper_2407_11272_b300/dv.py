@@ -19,7 +19,7 @@ __all__ = [
     "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
-PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2}
+PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2, "fp16": 3}
 STATUS = {0: "DV_OK", 1: "DV_ERR_INVALID_ARG", 2: "DV_ERR_INVALID_MESH", 3: "DV_ERR_OOM", 4: "DV_ERR_CUDA",
           5: "DV_ERR_TIMEOUT", 6: "DV_ERR_UNSUPPORTED"}
 
