@@ -46,6 +46,8 @@ WORKLOADS = {
                       n=128),
     "shsphere_256": dict(desc="SH-displaced geodesic sphere r=0.7 (204020 faces), 256^3 grid on [-1,1]^3, "
                               "fwd(mixed) + bwd", n=256),
+    "torus_64": dict(desc="the torus_128 mesh (36000 faces) on a 64^3 grid on [-1,1]^3, fwd(mixed) + bwd; "
+                          "the small case for profiler captures", n=64),
     "icosphere_32": dict(desc="icosphere k=3 r=0.8 (1280 faces), 32^3 grid on [-1,1]^3, fwd(mixed) + bwd", n=32),
 }
 
@@ -53,7 +55,7 @@ WORKLOADS = {
 def _mesh_for(name):
     from paper_2407_11272_b300 import meshgen
 
-    if name == "torus_128":
+    if name in ("torus_128", "torus_64"):
         return meshgen.jittered_torus()
     if name == "shsphere_256":
         return meshgen.sh_sphere()

@@ -381,7 +381,7 @@ __device__ __forceinline__ bool run_face_tiles(TilePipe &pp, int *err, Body &&bo
 
 // ---------------------------------------------------------------------------------------------
 template <int QX, int QY, bool KAHAN, bool HALF>
-__global__ void __launch_bounds__(kFwdThreads, 2) fwd_grid_kernel(const FwdArgs a) {
+__global__ void __launch_bounds__(kFwdThreads, 3) fwd_grid_kernel(const FwdArgs a) {
     __shared__ __align__(128) FaceRec sm[kStages][kTileFaces];
     __shared__ __align__(8) uint64_t full[kStages];
     // Kahan state (sum, compensation) of every query of every thread, touched once per tile:
@@ -558,7 +558,7 @@ __global__ void split_reduce_kernel(const float2 *__restrict__ partial, int nspl
 
 // ---------------------------------------------------------------------------------------------
 // Host side.
-constexpr int kGridQX = 8, kGridQY = 2;  // 16 queries per thread on the grid path
+constexpr int kGridQX = 4, kGridQY = 2;  // 8 queries per thread on the grid path (3 CTAs per SM)
 constexpr int kListQ = 8;                // 8 queries per thread on the list path
 
 FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms) {
@@ -575,9 +575,10 @@ FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_
         p.qy = 1;
         p.qblocks = (nq + (int64_t)kFwdThreads * kListQ - 1) / ((int64_t)kFwdThreads * kListQ);
     }
-    // Two CTAs fit per SM. Split the face loop when the query CTAs alone would leave the GPU
-    // under-filled (fewer than ~4 waves), keeping at least 2 tiles of faces per split.
-    const int64_t slots = 2LL * num_sms;
+    // Three grid CTAs (two list CTAs) fit per SM. Split the face loop when the query CTAs alone
+    // would leave the GPU under-filled (fewer than ~4 waves), keeping at least 2 tiles of faces
+    // per split.
+    const int64_t slots = (grid ? 3LL : 2LL) * num_sms;
     int nsplit = 1;
     if (p.qblocks < 4 * slots) {
         const int64_t want = (4 * slots + p.qblocks - 1) / p.qblocks;
