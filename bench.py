@@ -298,8 +298,8 @@ def run_native(args):
     fp32_peak = sms * 128 * sm_mhz * 1e6  # lane-ops/s, FMA counted once
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
     dname, (dms, dn) = dom
-    ops = {"fwd_grid_kahan": OPS_FWD, "fwd_grid": OPS_FWD, "fwd_grid_fp16": OPS_FWD, "bwd_grid": OPS_BWD}.get(dname,
-                                                                                                      OPS_FWD)
+    ops = {"fwd_grid_kahan": OPS_FWD, "fwd_grid": OPS_FWD, "fwd_grid_fp16": OPS_FWD, "fwd_strip_kahan": OPS_FWD,
+           "fwd_strip": OPS_FWD, "bwd_grid": OPS_BWD}.get(dname, OPS_FWD)
     avg_s = dms / max(dn, 1) * 1e-3
     achieved = ops * pairs / avg_s if avg_s > 0 else 0.0
     roof = {"bound": "alu", "kernel": dname, "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,

@@ -96,6 +96,21 @@ typedef struct {
 /* Version of this ABI (DV_ABI_VERSION). */
 int dv_abi_version(void);
 
+/* Strip order of a mesh's faces, the visiting order of the forward passes
+ * (the sum of Eq. (5) is order-free; this order lets consecutive faces share
+ * the per-vertex |v - q| and per-edge dot terms of Eq. (7)). HOST function, no
+ * GPU needed. faces int32 [nf][3] (host), indices in [0, nv). Output, host,
+ * caller-owned: events ev_vert[k] (a vertex index) and ev_face[k] (the face
+ * completed by this event and the two events before it, or -1 for the first
+ * two events of each strip). Every face appears exactly once; the vertex set
+ * {ev_vert[k-2], ev_vert[k-1], ev_vert[k]} of an event with ev_face[k] >= 0
+ * equals that face's vertex set. nf <= n_events <= 3 nf. With ev_vert or
+ * ev_face NULL only *n_events is set (size query); DV_ERR_INVALID_ARG if
+ * capacity < *n_events. No counterpart in the paper (an evaluation order of
+ * this library). */
+dv_status dv_build_strips(const int32_t *faces, int64_t nf, int64_t nv, int32_t *ev_vert, int32_t *ev_face,
+                          int64_t capacity, int64_t *n_events);
+
 /* Human-readable name of a status code. Never NULL. */
 const char *dv_status_string(dv_status s);
 
@@ -104,8 +119,10 @@ const char *dv_last_error(void);
 
 /* Algorithm 1 input "Mesh (V, F)": validate the faces (every index in [0, nv))
  * and vertices (finite), then pack each face f into a per-face record
- * (v0, v1, v2 and the face normal (v1-v0)x(v2-v0), FP32 and FP64 copies) and
- * build the vertex-to-face adjacency. d_verts float32 [nv][3], d_faces int32 [nf][3]
+ * (v0, v1, v2 and the face normal (v1-v0)x(v2-v0), FP32 and FP64 copies),
+ * build the vertex-to-face adjacency and the strip order of the faces
+ * (dv_build_strips) with its per-event records, used by the grid forward
+ * and the FP64 re-evaluation. d_verts float32 [nv][3], d_faces int32 [nf][3]
  * are read only during this call (the mesh keeps its own copies).
  * SYNCHRONIZES `stream` once (validation result). nv >= 3, nf >= 1.
  * On success *out receives a new handle; release it with dv_mesh_destroy. */

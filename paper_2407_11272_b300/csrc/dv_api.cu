@@ -95,6 +95,11 @@ struct dv_mesh {
     dv::FaceRec64 *rec64 = nullptr; // [nf]
     int32_t *vtx_ptr = nullptr;     // [nv+1]
     int32_t *vtx_corner = nullptr;  // [3 nf]
+    int64_t ne = 0;                       // strip events (strips.cu)
+    int32_t *ev_vert = nullptr;           // [ne]
+    int32_t *ev_face = nullptr;           // [ne], -1 for a strip's first two events
+    dv::StripRec *srec = nullptr;         // [ne]
+    dv::StripRec64 *srec64 = nullptr;     // [ne]
     int *err = nullptr;             // sticky error word + small counters: [0]=err [1]=flag_count [2]=occ_changed [3]=maxdiff bits
     // scratch, grown on demand
     int64_t cap_q = 0;
@@ -216,7 +221,8 @@ dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_gri
         return fail(DV_ERR_UNSUPPORTED, "the FP16 ablation is implemented for grid queries only");
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
-    const dv::FwdPlan plan = dv::plan_forward(nq, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
+    const int64_t nev = (grid && prec != DV_PREC_FP16) ? m->ne : 0;  // strip order on the grid path
+    const dv::FwdPlan plan = dv::plan_forward(nq, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms, nev);
     const bool mixed = prec == DV_PREC_MIXED;
     dv_status st;
     m->last_stream = s;
@@ -233,14 +239,15 @@ dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_gri
     int *count = mixed ? m->err + 1 : nullptr;
     const uint8_t *nearf = mixed ? m->ws_near : nullptr;
     const int arith = prec == DV_PREC_FP16 ? dv::kArithFP16 : (prec == DV_PREC_FP32 ? dv::kArithFP32 : dv::kArithKahan);
-    DV_CUDA(dv::launch_forward(plan, m->rec, m->nf, grid ? &gf : nullptr, queries, nq, arith,
+    DV_CUDA(dv::launch_forward(plan, m->rec, m->nf, m->srec, m->ne, grid ? &gf : nullptr, queries, nq, arith,
                                m->ws_partial, w, occ, nearf, list, count, ctx));
     if (plan.nsplit > 1)
         DV_CUDA(dv::launch_split_reduce(plan, m->ws_partial, nq, w, occ, nearf, list, count, s));
     if (mixed) {
         dv::GridD gd{};
         if (grid) gd = to_gridd(grid);
-        DV_CUDA(dv::launch_reeval_fp64(m->rec64, m->nf, grid ? &gd : nullptr, queries, list, count, nq, w, occ,
+        DV_CUDA(dv::launch_reeval_fp64(m->rec64, m->nf, m->srec64, m->ne, grid ? &gd : nullptr, queries, list, count,
+                                       nq, w, occ,
                                        (unsigned *)(m->err + 3), m->err + 2, m->num_sms, s));
     }
     if (report) {
@@ -283,8 +290,9 @@ const char *dv_last_error(void) { return g_last_error.c_str(); }
 void dv_mesh_destroy(dv_mesh *m) {
     if (!m) return;
     DeviceGuard dg(m->device);
-    void *bufs[] = {m->faces, m->rec,  m->rec64,   m->vtx_ptr,    m->vtx_corner, m->err,
-                    m->ws_w,  m->ws_near, m->ws_list, m->ws_partial, m->ws_fg};
+    void *bufs[] = {m->faces,   m->rec,     m->rec64, m->vtx_ptr, m->vtx_corner, m->ev_vert,    m->ev_face,
+                    m->srec,    m->srec64,  m->err,   m->ws_w,    m->ws_near,    m->ws_list,    m->ws_partial,
+                    m->ws_fg};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, m->last_stream);
     delete m;
@@ -336,12 +344,26 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
     for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
     std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
     for (int64_t i = 0; i < 3 * nf; ++i) corner[(size_t)fill[hf[i]]++] = (int32_t)i;
+    // vertex-sharing strip order of the faces for the forward passes
+    std::vector<int32_t> ev_vert, ev_face;
+    dv::build_strips(hf.data(), nf, nv, ev_vert, ev_face);
+    m->ne = (int64_t)ev_vert.size();
+    e = cudaMallocAsync((void **)&m->ev_vert, (size_t)m->ne * sizeof(int32_t), s);
+    if (!e) e = cudaMallocAsync((void **)&m->ev_face, (size_t)m->ne * sizeof(int32_t), s);
+    if (!e) e = cudaMallocAsync((void **)&m->srec, (size_t)m->ne * sizeof(dv::StripRec), s);
+    if (!e) e = cudaMallocAsync((void **)&m->srec64, (size_t)m->ne * sizeof(dv::StripRec64), s);
+    if (e) return bail(fail(DV_ERR_OOM, "strip storage: %s", cudaGetErrorString(e)));
     if ((e = cudaMemcpyAsync(m->vtx_ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(m->vtx_corner, corner.data(), corner.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                              s)) ||
+        (e = cudaMemcpyAsync(m->ev_vert, ev_vert.data(), ev_vert.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             s)) ||
+        (e = cudaMemcpyAsync(m->ev_face, ev_face.data(), ev_face.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             s)) ||
         (e = cudaMemcpyAsync(m->faces, d_faces, (size_t)nf * 3 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)))
         return bail(fail(DV_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e)));
-    if ((e = dv::launch_pack(d_verts, m->faces, nf, m->rec, m->rec64, s)))
+    if ((e = dv::launch_pack(d_verts, m->faces, nf, m->rec, m->rec64, s)) ||
+        (e = dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64, s)))
         return bail(fail(DV_ERR_CUDA, "pack: %s", cudaGetErrorString(e)));
     // the host vectors above must outlive the async uploads
     if ((e = cudaStreamSynchronize(s))) return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
@@ -354,6 +376,8 @@ dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
     DeviceGuard dg(m->device);
     m->last_stream = (cudaStream_t)stream;
     DV_CUDA(dv::launch_pack(d_verts, m->faces, m->nf, m->rec, m->rec64, (cudaStream_t)stream));
+    DV_CUDA(dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64,
+                                   (cudaStream_t)stream));
     return DV_OK;
 }
 
@@ -372,10 +396,13 @@ dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_quer
         if ((st = check_grid(grid))) return st;
         const dv::GridF gf = to_gridf(grid);
         const int64_t gq = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
-        const dv::FwdPlan fp = dv::plan_forward(gq, m->nf, true, &gf, m->num_sms);
+        // the strip plan (FP32 / Kahan / mixed) and the face plan (FP16 ablation)
+        const dv::FwdPlan fp = dv::plan_forward(gq, m->nf, true, &gf, m->num_sms, m->ne);
+        const dv::FwdPlan fp16 = dv::plan_forward(gq, m->nf, true, &gf, m->num_sms);
         const dv::BwdPlan bp = dv::plan_backward(gq, m->nf, true, &gf, m->num_sms);
         nq = std::max(nq, gq);
         part = std::max(part, fp.nsplit > 1 ? (int64_t)fp.nsplit * gq : (int64_t)0);
+        part = std::max(part, fp16.nsplit > 1 ? (int64_t)fp16.nsplit * gq : (int64_t)0);
         fg = std::max(fg, (int64_t)bp.nsplit * m->nf * 9);
     }
     cudaStream_t s = m->last_stream;
@@ -491,7 +518,7 @@ cudaError_t batch_resources(int dev, BatchRes **out) {
 dv_status reserve_request(dv_mesh *m, const dv_request &r, dv_precision prec, cudaStream_t s) {
     const int64_t nq = (int64_t)r.grid.n[0] * r.grid.n[1] * r.grid.n[2];
     const dv::GridF gf = to_gridf(&r.grid);
-    const dv::FwdPlan fp = dv::plan_forward(nq, m->nf, true, &gf, m->num_sms);
+    const dv::FwdPlan fp = dv::plan_forward(nq, m->nf, true, &gf, m->num_sms, prec != DV_PREC_FP16 ? m->ne : 0);
     dv_status st;
     m->last_stream = s;
     if (fp.nsplit > 1 && (st = grow(m->ws_partial, m->cap_partial, (int64_t)fp.nsplit * nq, s))) return st;

@@ -4,7 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "atan_poly.h"
+
 #include "dv_api.h"
 
 namespace dv {
@@ -29,6 +32,23 @@ static_assert(sizeof(FaceRec) == 48, "face record must be 48 bytes (TMA bulk cop
 // Per-face FP64 record for the re-evaluation pass: v0, v1, v2, n (12 doubles, 96 bytes).
 struct FaceRec64 {
     double v[12];
+};
+
+// One event of the vertex-sharing strip order (strips.cu), FP32: the event's vertex and, if the
+// event completes a face, that face's normal n_f pre-scaled by kNormalScale and flag = 1 (else
+// n = 0, flag = 0). 32 bytes: TMA bulk copies of any run of events stay 16-byte aligned.
+struct StripRec {
+    float4 p;  // vx, vy, vz, 8 n.x
+    float4 q;  // 8 n.y, 8 n.z, flag, 0
+};
+static_assert(sizeof(StripRec) == 32, "strip record must be 32 bytes");
+
+// FP64 strip event for the re-evaluation pass: vertex, unscaled normal, flag (64 bytes).
+struct StripRec64 {
+    double v[3];
+    double n[3];
+    double flag;
+    double pad;
 };
 
 // Cell-centred grid, FP32 form used by the FP32 kernels: x = lo + (i + 0.5) * h.
@@ -156,6 +176,15 @@ cudaError_t launch_validate(const float *verts, int64_t nv, const int32_t *faces
                             cudaStream_t s);
 cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, FaceRec *rec, FaceRec64 *rec64,
                         cudaStream_t s);
+// Strip events from the vertices and the packed face records (normals copied from rec/rec64, so
+// both orders see the same n_f). Runs after launch_pack on the same stream.
+cudaError_t launch_pack_strips(const float *verts, const int32_t *ev_vert, const int32_t *ev_face, int64_t ne,
+                               const FaceRec *rec, const FaceRec64 *rec64, StripRec *srec, StripRec64 *srec64,
+                               cudaStream_t s);
+
+// strips.cu: vertex-sharing strip order of the faces (host, once per mesh).
+void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int32_t> &ev_vert,
+                  std::vector<int32_t> &ev_face);
 cudaError_t launch_flipped_duplication(const float *verts, int64_t nv, const int32_t *faces, int64_t nf,
                                        const FaceRec64 *rec64, const int32_t *vtx_ptr, const int32_t *vtx_corner,
                                        double eps, float *out_verts, int32_t *out_faces, cudaStream_t s);
@@ -169,15 +198,18 @@ struct FwdPlan {
     int threads;         // CTA size
     int64_t qblocks;     // CTAs over queries
     int nsplit;          // face splits (grid dimension y); 1 = no split
-    int64_t faces_per_split;
+    int64_t faces_per_split;  // faces, or strip events when strips is set
+    bool strips;         // grid path over the strip events (FP32 / Kahan arithmetic)
 };
-FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms);
+// n_events > 0 selects the strip-order grid kernel (grid queries, FP32 or Kahan arithmetic).
+FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms, int64_t n_events = 0);
 // Per-pair arithmetic of the forward: FP32 with a plain sum, FP32 with Kahan across face tiles,
 // or the FP16 ablation (half2 per-pair terms, FP32 Kahan sums; grid queries only).
 constexpr int kArithFP32 = 0, kArithKahan = 1, kArithFP16 = 2;
-cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
-                           int64_t nq, int arith, float2 *partial, float *w_out, uint8_t *occ_out,
-                           const uint8_t *near_flag, int *flag_list, int *flag_count, const LaunchCtx &ctx);
+cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const StripRec *srec, int64_t ne,
+                           const GridF *g, const float *queries, int64_t nq, int arith, float2 *partial, float *w_out,
+                           uint8_t *occ_out, const uint8_t *near_flag, int *flag_list, int *flag_count,
+                           const LaunchCtx &ctx);
 cudaError_t launch_split_reduce(const FwdPlan &p, const float2 *partial, int64_t nq, float *w_out, uint8_t *occ_out,
                                 const uint8_t *near_flag, int *flag_list, int *flag_count, cudaStream_t s);
 
@@ -186,10 +218,12 @@ cudaError_t launch_near_surface(const FaceRec *rec, int64_t nf, const GridF *g, 
                                 uint8_t *near_flag, cudaStream_t s);
 
 // winding_fp64.cu
-cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const GridD *g, const float *queries,
-                               const int *flag_list, const int *flag_count, int64_t max_flagged, float *w_out,
-                               uint8_t *occ_out, unsigned *stat_maxdiff_bits, int *stat_occ_changed, int num_sms,
-                               cudaStream_t s);
+// FP64 re-evaluation of the flagged queries; over the strip events when srec64 is given
+// (ne > 0), else over the face records.
+cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const StripRec64 *srec64, int64_t ne,
+                               const GridD *g, const float *queries, const int *flag_list, const int *flag_count,
+                               int64_t max_flagged, float *w_out, uint8_t *occ_out, unsigned *stat_maxdiff_bits,
+                               int *stat_occ_changed, int num_sms, cudaStream_t s);
 
 // dipole.cu (Eq. (4) surrogate)
 int dipole_bwd_splits(int64_t nq, int64_t nf, int num_sms);

@@ -136,8 +136,8 @@ extern "C" dv_status dv_winding_grid_noalloc(const float *d_verts, int64_t nv, c
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail("pack launch", e);
     const LaunchCtx ctx{s, err};
-    if ((e = launch_forward(plan, rec, nf, &gf, nullptr, nq, true, partial, d_out_w, nullptr, nullptr, nullptr,
-                            nullptr, ctx)) != cudaSuccess)
+    if ((e = launch_forward(plan, rec, nf, nullptr, 0, &gf, nullptr, nq, kArithKahan, partial, d_out_w, nullptr,
+                            nullptr, nullptr, nullptr, ctx)) != cudaSuccess)
         return cuda_fail("forward launch", e);
     if (plan.nsplit > 1 &&
         (e = launch_split_reduce(plan, partial, nq, d_out_w, nullptr, nullptr, nullptr, nullptr, s)) != cudaSuccess)

@@ -18,13 +18,11 @@ __global__ void validate_kernel(const float *__restrict__ verts, int64_t nv, con
     }
 }
 
-// One thread per face: gather the three vertices, compute n = (v1 - v0) x (v2 - v0) in FP64
-// (products of FP32 values are exact in FP64), and store the FP32 record (normal scaled by 8)
-// and the FP64 record used by the re-evaluation pass.
-__global__ void pack_kernel(const float *__restrict__ verts, const int32_t *__restrict__ faces, int64_t nf,
-                            FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
-    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf) return;
+// Per face: gather the three vertices, compute n = (v1 - v0) x (v2 - v0) in FP64 (products of
+// FP32 values are exact in FP64), and store the FP32 record (normal scaled by 8) and the FP64
+// record used by the re-evaluation pass.
+__device__ __forceinline__ void pack_one(const float *__restrict__ verts, const int32_t *__restrict__ faces, int64_t f,
+                                         FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
     double v[3][3];
     for (int k = 0; k < 3; ++k) {
         int64_t id = faces[3 * f + k];
@@ -43,6 +41,12 @@ __global__ void pack_kernel(const float *__restrict__ verts, const int32_t *__re
         for (int c = 0; c < 3; ++c) r64.v[3 * k + c] = v[k][c];
     for (int c = 0; c < 3; ++c) r64.v[9 + c] = n[c];
     rec64[f] = r64;
+}
+
+__global__ void pack_kernel(const float *__restrict__ verts, const int32_t *__restrict__ faces, int64_t nf,
+                            FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x)
+        pack_one(verts, faces, f, rec, rec64);
 }
 
 // dverts[v] = sum over the faces f incident to v (corner k) and over the query splits s of
@@ -91,6 +95,56 @@ cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, Fa
     pack_kernel<<<blocks_for(nf, 256), 256, 0, s>>>(verts, faces, nf, rec, rec64);
     count_launch();
     prof_end("pack_faces", s);
+    return cudaGetLastError();
+}
+
+// One strip event: the vertex (FP32 as given, and widened to FP64) and, for an event that
+// completes a face, that face's normal taken from the packed face records.
+__device__ __forceinline__ void pack_strip_one(const float *__restrict__ verts, const int32_t *__restrict__ ev_vert,
+                                               const int32_t *__restrict__ ev_face, int64_t e,
+                                               const FaceRec *__restrict__ rec, const FaceRec64 *__restrict__ rec64,
+                                               StripRec *__restrict__ srec, StripRec64 *__restrict__ srec64) {
+    const int64_t v = ev_vert[e];
+    const int32_t f = ev_face[e];
+    const float x = verts[3 * v], y = verts[3 * v + 1], z = verts[3 * v + 2];
+    StripRec r;
+    StripRec64 r64;
+    r64.v[0] = x;
+    r64.v[1] = y;
+    r64.v[2] = z;
+    r64.pad = 0.0;
+    if (f >= 0) {
+        const FaceRec fr = rec[f];
+        r.p = make_float4(x, y, z, fr.r0.w);
+        r.q = make_float4(fr.r1.w, fr.r2.w, 1.0f, 0.0f);
+        for (int c = 0; c < 3; ++c) r64.n[c] = rec64[f].v[9 + c];
+        r64.flag = 1.0;
+    } else {
+        r.p = make_float4(x, y, z, 0.0f);
+        r.q = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int c = 0; c < 3; ++c) r64.n[c] = 0.0;
+        r64.flag = 0.0;
+    }
+    srec[e] = r;
+    srec64[e] = r64;
+}
+
+__global__ void pack_strips_kernel(const float *__restrict__ verts, const int32_t *__restrict__ ev_vert,
+                                   const int32_t *__restrict__ ev_face, int64_t ne, const FaceRec *__restrict__ rec,
+                                   const FaceRec64 *__restrict__ rec64, StripRec *__restrict__ srec,
+                                   StripRec64 *__restrict__ srec64) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
+        pack_strip_one(verts, ev_vert, ev_face, e, rec, rec64, srec, srec64);
+}
+
+cudaError_t launch_pack_strips(const float *verts, const int32_t *ev_vert, const int32_t *ev_face, int64_t ne,
+                               const FaceRec *rec, const FaceRec64 *rec64, StripRec *srec, StripRec64 *srec64,
+                               cudaStream_t s) {
+    if (ne == 0) return cudaSuccess;
+    prof_begin("pack_strips", s);
+    pack_strips_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(verts, ev_vert, ev_face, ne, rec, rec64, srec, srec64);
+    count_launch();
+    prof_end("pack_strips", s);
     return cudaGetLastError();
 }
 

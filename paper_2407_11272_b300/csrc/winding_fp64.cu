@@ -102,18 +102,147 @@ __global__ void __launch_bounds__(kReThreads) reeval_fp64_kernel(const FaceRec64
     }
 }
 
-cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const GridD *g, const float *queries,
-                               const int *flag_list, const int *flag_count, int64_t max_flagged, float *w_out,
-                               uint8_t *occ_out, unsigned *stat_maxdiff_bits, int *stat_occ_changed, int num_sms,
-                               cudaStream_t s) {
+// ---------------------------------------------------------------------------------------------
+// The same re-evaluation over the strip order of the faces (strips.cu): every thread walks a
+// contiguous run of events and keeps, per query of the batch, the offset, |P - q| and the dot
+// with the previous vertex of the two most recent vertices; a face then costs one FP64 square
+// root and two dots instead of three of each (D and N as in the FP32 strip kernel). A thread's
+// run starts with up to two warm-up events (vertex part only). The FP64 pipe bounds this
+// kernel, not instruction issue, so the state is simply shifted after each event.
+constexpr int kRsQB = 2;
+
+struct Slot64 {
+    double ax[kRsQB], ay[kRsQB], az[kRsQB], l[kRsQB], e[kRsQB];
+};
+
+// ATAN2(N, D) of one strip face in FP64 with the fast path of half_angle64; a query on one of
+// the face's vertices (a distance of exactly 0, where N and D vanish) contributes 0.
+__device__ __forceinline__ double strip_half_angle64(double N, double D, double lV, double l1, double l2) {
+    if (D > 8.0 * fabs(N)) {
+        const double u = N / D;
+        const double s = u * u;
+        double P = DV_ATAN64_C6;
+        P = fma(P, s, DV_ATAN64_C5);
+        P = fma(P, s, DV_ATAN64_C4);
+        P = fma(P, s, DV_ATAN64_C3);
+        P = fma(P, s, DV_ATAN64_C2);
+        P = fma(P, s, DV_ATAN64_C1);
+        P = fma(P, s, DV_ATAN64_C0);
+        return u * P;
+    }
+    if (lV == 0.0 || l1 == 0.0 || l2 == 0.0) return 0.0;
+    if (N == 0.0 && D == 0.0) return 0.0;
+    return atan2(N + 0.0, D);
+}
+
+__global__ void __launch_bounds__(kReThreads, 2)
+    reeval_strip_kernel(const StripRec64 *__restrict__ srec, int64_t ne, GridD g, const float *__restrict__ queries,
+                        const int *__restrict__ list, const int *__restrict__ count, float *w_out, uint8_t *occ_out,
+                        unsigned *maxdiff_bits, int *occ_changed) {
+    __shared__ double red[kReThreads / 32][kRsQB];
+    const int M = *count;
+    const int nb = (M + kRsQB - 1) / kRsQB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t chunk = (ne + kReThreads - 1) / kReThreads;
+    const int64_t eb = (int64_t)threadIdx.x * chunk;
+    const int64_t ee = eb + chunk < ne ? eb + chunk : ne;
+    const int64_t es = eb < 2 ? 0 : eb - 2;  // warm-up start
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        double qx[kRsQB], qy[kRsQB], qz[kRsQB], sum[kRsQB];
+        int ids[kRsQB];
+#pragma unroll
+        for (int j = 0; j < kRsQB; ++j) {
+            const int k = b * kRsQB + j < M ? b * kRsQB + j : M - 1;
+            const int idx = list[k];
+            ids[j] = idx;
+            if (queries) {
+                qx[j] = (double)queries[3 * (int64_t)idx];
+                qy[j] = (double)queries[3 * (int64_t)idx + 1];
+                qz[j] = (double)queries[3 * (int64_t)idx + 2];
+            } else {
+                const int ix = idx % g.n[0], iy = (idx / g.n[0]) % g.n[1], iz = idx / (g.n[0] * g.n[1]);
+                qx[j] = g.lo[0] + ((double)ix + 0.5) * g.h[0];
+                qy[j] = g.lo[1] + ((double)iy + 0.5) * g.h[1];
+                qz[j] = g.lo[2] + ((double)iz + 0.5) * g.h[2];
+            }
+            sum[j] = 0.0;
+        }
+        Slot64 P1, P2;
+#pragma unroll
+        for (int j = 0; j < kRsQB; ++j) {
+            P1.ax[j] = P1.ay[j] = P1.az[j] = P1.l[j] = P1.e[j] = 0.0;
+            P2.ax[j] = P2.ay[j] = P2.az[j] = P2.l[j] = P2.e[j] = 0.0;
+        }
+        for (int64_t ev = es; ev < ee; ++ev) {
+            const StripRec64 r = srec[ev];
+            const bool face = r.flag != 0.0 && ev >= eb;
+            Slot64 V;
+#pragma unroll
+            for (int j = 0; j < kRsQB; ++j) {
+                V.ax[j] = r.v[0] - qx[j];
+                V.ay[j] = r.v[1] - qy[j];
+                V.az[j] = r.v[2] - qz[j];
+                V.l[j] = sqrt(V.ax[j] * V.ax[j] + V.ay[j] * V.ay[j] + V.az[j] * V.az[j]);
+                V.e[j] = V.ax[j] * P1.ax[j] + V.ay[j] * P1.ay[j] + V.az[j] * P1.az[j];
+            }
+            if (face) {
+#pragma unroll
+                for (int j = 0; j < kRsQB; ++j) {
+                    const double d2 = V.ax[j] * P2.ax[j] + V.ay[j] * P2.ay[j] + V.az[j] * P2.az[j];
+                    const double N = V.ax[j] * r.n[0] + V.ay[j] * r.n[1] + V.az[j] * r.n[2];
+                    const double D = (V.l[j] * P1.l[j] + V.e[j]) * P2.l[j] + V.l[j] * P1.e[j] + P1.l[j] * d2;
+                    sum[j] += strip_half_angle64(N, D, V.l[j], P1.l[j], P2.l[j]);
+                }
+            }
+            P2 = P1;
+            P1 = V;
+        }
+#pragma unroll
+        for (int j = 0; j < kRsQB; ++j) {
+            double v = sum[j];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+            if (lane == 0) red[warp][j] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kRsQB && b * kRsQB + (int)threadIdx.x < M) {
+            const int j = threadIdx.x;
+            double t = 0.0;
+            for (int w = 0; w < kReThreads / 32; ++w) t += red[w][j];
+            const double w64 = t * kInv2PiD;
+            const int idx = ids[j];
+            const float w32 = w_out[idx];
+            const float wn = (float)w64;
+            w_out[idx] = wn;
+            const uint8_t o_new = w64 > 0.5 ? 1 : 0;
+            if (occ_out) occ_out[idx] = o_new;
+            const float diff = fabsf(w32 - wn);
+            atomicMax(maxdiff_bits, __float_as_uint(isfinite(diff) ? diff : 3.0e38f));
+            if ((w32 > 0.5f ? 1 : 0) != o_new) atomicAdd(occ_changed, 1);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const StripRec64 *srec64, int64_t ne,
+                               const GridD *g, const float *queries, const int *flag_list, const int *flag_count,
+                               int64_t max_flagged, float *w_out, uint8_t *occ_out, unsigned *stat_maxdiff_bits,
+                               int *stat_occ_changed, int num_sms, cudaStream_t s) {
     GridD gd{};
     if (g) gd = *g;
+    const bool strips = srec64 != nullptr && ne > 0;
+    const int qb = strips ? kRsQB : kReQB;
     int64_t blocks = 4LL * num_sms;
-    const int64_t need = (max_flagged + kReQB - 1) / kReQB;
+    const int64_t need = (max_flagged + qb - 1) / qb;
     if (need < blocks) blocks = need > 0 ? need : 1;
     prof_begin("reeval_fp64", s);
-    reeval_fp64_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(rec64, nf, gd, queries, flag_list, flag_count, w_out,
-                                                               occ_out, stat_maxdiff_bits, stat_occ_changed);
+    if (strips)
+        reeval_strip_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(srec64, ne, gd, queries, flag_list, flag_count,
+                                                                    w_out, occ_out, stat_maxdiff_bits,
+                                                                    stat_occ_changed);
+    else
+        reeval_fp64_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(rec64, nf, gd, queries, flag_list, flag_count,
+                                                                   w_out, occ_out, stat_maxdiff_bits,
+                                                                   stat_occ_changed);
     count_launch();
     prof_end("reeval_fp64", s);
     return cudaGetLastError();

@@ -38,6 +38,8 @@ constexpr int kStages = 4;
 struct FwdArgs {
     const FaceRec *rec;
     int64_t nf;
+    const StripRec *srec;  // strip events (grid FP32 path); null: face order
+    int64_t ne;
     GridF g;
     const float *queries;  // list path: [nq][3]; grid path: null
     int64_t nq;
@@ -323,29 +325,31 @@ __device__ __forceinline__ void epilogue(const FwdArgs &a, int64_t idx, float w)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Shared TMA face-tile pipeline. `Body` processes one tile: body(const FaceRec* tile, int count).
+// Shared TMA tile pipeline over an array of 16-byte-multiple records (faces or strip events).
+// `Body` processes one tile: body(const Rec* tile, int count).
+template <typename Rec, int kT = kTileFaces>
 struct TilePipe {
-    FaceRec (*sm)[kTileFaces];
+    Rec (*sm)[kT];
     uint64_t *full;
-    const FaceRec *src;
+    const Rec *src;
     int64_t f0;
     int64_t nfaces;
     int ntiles;
 
     __device__ __forceinline__ int tile_count(int t) const {
-        const int64_t left = nfaces - (int64_t)t * kTileFaces;
-        return left < kTileFaces ? (int)left : kTileFaces;
+        const int64_t left = nfaces - (int64_t)t * kT;
+        return left < kT ? (int)left : kT;
     }
     __device__ __forceinline__ void issue(int t) const {
         const int s = t % kStages;
-        const uint32_t bytes = (uint32_t)tile_count(t) * (uint32_t)sizeof(FaceRec);
+        const uint32_t bytes = (uint32_t)tile_count(t) * (uint32_t)sizeof(Rec);
         mbar_arrive_expect_tx(&full[s], bytes);
-        tma_load_1d(&sm[s][0], src + f0 + (int64_t)t * kTileFaces, bytes, &full[s]);
+        tma_load_1d(&sm[s][0], src + f0 + (int64_t)t * kT, bytes, &full[s]);
     }
 };
 
-template <typename Body, typename TileEnd>
-__device__ __forceinline__ bool run_face_tiles(TilePipe &pp, int *err, Body &&body, TileEnd &&tile_end) {
+template <typename Rec, int kT, typename Body, typename TileEnd>
+__device__ __forceinline__ bool run_face_tiles(TilePipe<Rec, kT> &pp, int *err, Body &&body, TileEnd &&tile_end) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&pp.full[s], 1);
         fence_mbar_init();
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) fwd_grid_kernel(const FwdArgs 
             if (KAHAN) kst[i * QX + j][threadIdx.x] = make_float2(0.0f, 0.0f);
         }
 
-    TilePipe pp;
+    TilePipe<FaceRec> pp;
     pp.sm = sm;
     pp.full = full;
     pp.src = a.rec;
@@ -481,6 +485,227 @@ __global__ void __launch_bounds__(kFwdThreads, 3) fwd_grid_kernel(const FwdArgs 
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Grid forward over the vertex-sharing strip order (strips.cu). Each event brings a vertex V; an
+// event flagged as a face completes the face {P2, P1, V} of the two vertices before it. Per
+// thread and query the state carried from event to event is, for P1 and P2, the offset from the
+// query, the distance |P - q| and the dot (P - q).(P' - q) with the vertex before it, so a face
+// costs one MUFU square root, two dots and D:
+//   D = (|V||P1| + V.P1)|P2| + |V|(P1.P2) + |P1|(V.P2)      (offsets relative to q)
+//   N = (V - q) . n_f                                       (any vertex of the face gives det)
+// then the ATAN2 fast path / slow path of face_grid. (y, z) parts are shared per row as before.
+// Three state slots rotate through the roles (P2, P1, V), so the event loop is unrolled by
+// three and no state is copied; strip tiles hold a multiple of three events.
+constexpr int kStripThreads = 128;
+constexpr int kTileEvents = 96;
+
+template <int QX, int QY>
+struct StripSlot {
+    float2 ax[QX / 2];     // vertex x - query x, pairs of x-adjacent queries
+    float ay[QY], az;      // vertex y - query y per row, vertex z - query z
+    float2 l[QY][QX / 2];  // |vertex - query|
+    float2 e[QY][QX / 2];  // (vertex - query).(previous vertex - query)
+};
+
+// Slow-path term for a strip face (same conventions as slow_term): 0 if the fast path took it,
+// 0 when q coincides with one of the face's vertices (a distance that is 0 after the flush to
+// zero of a subnormal |.|^2), else ATAN2(N, D) per Eq. (8).
+__device__ __forceinline__ float strip_slow_term(float N8, float D, float lmin) {
+    if (D > fabsf(N8)) return 0.0f;
+    if (!(lmin > 0.0f)) return 0.0f;
+    return atan2f(__fadd_rn(N8, 0.0f), __fmul_rn(kNormalScale, D));
+}
+
+template <int QX, int QY, bool FACE>
+__device__ __forceinline__ void strip_event(const StripRec &r, const float2 (&nqx)[QX / 2], const float (&qy)[QY],
+                                            float qz, const StripSlot<QX, QY> &P2, const StripSlot<QX, QY> &P1,
+                                            StripSlot<QX, QY> &V, float2 (&acc)[QY][QX / 2]) {
+    V.az = __fsub_rn(r.p.z, qz);
+    const float2 vx = make_float2(r.p.x, r.p.x);
+#pragma unroll
+    for (int j = 0; j < QX / 2; ++j) V.ax[j] = __fadd2_rn(vx, nqx[j]);
+    const float azz = __fmul_rn(V.az, V.az), az1 = __fmul_rn(V.az, P1.az);
+    const float2 n8x = make_float2(r.p.w, r.p.w);
+    const float2 C0 = make_float2(DV_ATAN_C0, DV_ATAN_C0), C1 = make_float2(DV_ATAN_C1, DV_ATAN_C1);
+    const float2 C2 = make_float2(DV_ATAN_C2, DV_ATAN_C2);
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < QY; ++i) {
+        V.ay[i] = __fsub_rn(r.p.y, qy[i]);
+        const float Lyz = __fmaf_rn(V.ay[i], V.ay[i], azz);
+        const float d1yz = __fmaf_rn(V.ay[i], P1.ay[i], az1);
+        const float d2yz = FACE ? __fmaf_rn(V.ay[i], P2.ay[i], __fmul_rn(V.az, P2.az)) : 0.0f;
+        const float Nyz = FACE ? __fmaf_rn(V.ay[i], r.q.x, __fmul_rn(V.az, r.q.y)) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < QX / 2; ++j) {
+            const float2 l2 = __ffma2_rn(V.ax[j], V.ax[j], make_float2(Lyz, Lyz));
+            V.l[i][j] = make_float2(sqrt_approx(l2.x), sqrt_approx(l2.y));
+            V.e[i][j] = __ffma2_rn(V.ax[j], P1.ax[j], make_float2(d1yz, d1yz));  // (V - q).(P1 - q)
+            if (FACE) {
+                const float2 d2 = __ffma2_rn(V.ax[j], P2.ax[j], make_float2(d2yz, d2yz));  // (V - q).(P2 - q)
+                const float2 N8 = __ffma2_rn(V.ax[j], n8x, make_float2(Nyz, Nyz));
+                float2 D = __fmul2_rn(__ffma2_rn(V.l[i][j], P1.l[i][j], V.e[i][j]), P2.l[i][j]);
+                D = __ffma2_rn(V.l[i][j], P1.e[i][j], D);
+                D = __ffma2_rn(P1.l[i][j], d2, D);
+                const bool p0 = D.x > fabsf(N8.x), p1 = D.y > fabsf(N8.y);
+                ok = ok && p0 && p1;
+                float2 v = __fmul2_rn(N8, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
+                v.x = p0 ? v.x : 0.0f;
+                v.y = p1 ? v.y : 0.0f;
+                const float2 sq = __fmul2_rn(v, v);
+                const float2 P = __ffma2_rn(__ffma2_rn(C2, sq, C1), sq, C0);
+                acc[i][j] = __ffma2_rn(v, P, acc[i][j]);
+            }
+        }
+    }
+    if (FACE && __any_sync(kFull, !ok)) {
+        // rare: recompute N and D of this face (same operations, same results) for ATAN2
+#pragma unroll
+        for (int i = 0; i < QY; ++i) {
+            const float d2yz = __fmaf_rn(V.ay[i], P2.ay[i], __fmul_rn(V.az, P2.az));
+            const float Nyz = __fmaf_rn(V.ay[i], r.q.x, __fmul_rn(V.az, r.q.y));
+#pragma unroll
+            for (int j = 0; j < QX / 2; ++j) {
+                const float2 d2 = __ffma2_rn(V.ax[j], P2.ax[j], make_float2(d2yz, d2yz));
+                const float2 N8 = __ffma2_rn(V.ax[j], n8x, make_float2(Nyz, Nyz));
+                float2 D = __fmul2_rn(__ffma2_rn(V.l[i][j], P1.l[i][j], V.e[i][j]), P2.l[i][j]);
+                D = __ffma2_rn(V.l[i][j], P1.e[i][j], D);
+                D = __ffma2_rn(P1.l[i][j], d2, D);
+                const float lx = fminf(V.l[i][j].x, fminf(P1.l[i][j].x, P2.l[i][j].x));
+                const float ly = fminf(V.l[i][j].y, fminf(P1.l[i][j].y, P2.l[i][j].y));
+                acc[i][j].x = __fadd_rn(acc[i][j].x, strip_slow_term(N8.x, D.x, lx));
+                acc[i][j].y = __fadd_rn(acc[i][j].y, strip_slow_term(N8.y, D.y, ly));
+            }
+        }
+    }
+}
+
+// One event into slot V given the two before it; `face` is warp-uniform (same record for all).
+template <int QX, int QY>
+__device__ __forceinline__ void strip_step(const StripRec &r, bool face, const float2 (&nqx)[QX / 2],
+                                           const float (&qy)[QY], float qz, const StripSlot<QX, QY> &P2,
+                                           const StripSlot<QX, QY> &P1, StripSlot<QX, QY> &V,
+                                           float2 (&acc)[QY][QX / 2]) {
+    if (face)
+        strip_event<QX, QY, true>(r, nqx, qy, qz, P2, P1, V, acc);
+    else
+        strip_event<QX, QY, false>(r, nqx, qy, qz, P2, P1, V, acc);
+}
+
+template <int QX, int QY, bool KAHAN>
+__global__ void __launch_bounds__(kStripThreads, 4) fwd_grid_strip_kernel(const FwdArgs a) {
+    __shared__ __align__(128) StripRec sm[kStages][kTileEvents];
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ float2 kst[KAHAN ? QX * QY : 1][kStripThreads];
+
+    const int nx = a.g.n[0], ny = a.g.n[1], nz = a.g.n[2];
+    const int tiles_x = (nx + QX - 1) / QX, tiles_y = (ny + QY - 1) / QY;
+    const int64_t tile = (int64_t)blockIdx.x * kStripThreads + threadIdx.x;
+    const int tx = (int)(tile % tiles_x);
+    const int64_t t2 = tile / tiles_x;
+    const int ty = (int)(t2 % tiles_y);
+    const int64_t zz = t2 / tiles_y;
+    const bool valid_t = zz < nz;
+    const int z = valid_t ? (int)zz : nz - 1;
+
+    float qy[QY];
+    float2 nqx[QX / 2];
+#pragma unroll
+    for (int j = 0; j < QX / 2; ++j)
+        nqx[j] = make_float2(-__fmaf_rn((float)(tx * QX + 2 * j) + 0.5f, a.g.h[0], a.g.lo[0]),
+                             -__fmaf_rn((float)(tx * QX + 2 * j + 1) + 0.5f, a.g.h[0], a.g.lo[0]));
+#pragma unroll
+    for (int i = 0; i < QY; ++i) qy[i] = __fmaf_rn((float)(ty * QY + i) + 0.5f, a.g.h[1], a.g.lo[1]);
+    const float qz = __fmaf_rn((float)z + 0.5f, a.g.h[2], a.g.lo[2]);
+
+    float2 acc[QY][QX / 2];
+    StripSlot<QX, QY> S0, S1, S2;
+#pragma unroll
+    for (int i = 0; i < QY; ++i) {
+        S0.ay[i] = S1.ay[i] = S2.ay[i] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < QX / 2; ++j) {
+            acc[i][j] = make_float2(0.0f, 0.0f);
+            S0.l[i][j] = S1.l[i][j] = S2.l[i][j] = S0.e[i][j] = S1.e[i][j] = S2.e[i][j] = make_float2(0.0f, 0.0f);
+            if (KAHAN) {
+                kst[i * QX + 2 * j][threadIdx.x] = make_float2(0.0f, 0.0f);
+                kst[i * QX + 2 * j + 1][threadIdx.x] = make_float2(0.0f, 0.0f);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < QX / 2; ++j) S0.ax[j] = S1.ax[j] = S2.ax[j] = make_float2(0.0f, 0.0f);
+    S0.az = S1.az = S2.az = 0.0f;
+
+    // Events [e0, e1) of this split, preceded by up to two warm-up events (vertex part only)
+    // that supply the first faces' earlier vertices. Splits hold whole tiles of events.
+    const int64_t e0 = (int64_t)blockIdx.y * a.faces_per_split;
+    const int64_t e1 = e0 + a.faces_per_split < a.ne ? e0 + a.faces_per_split : a.ne;
+    const int warm = (int)(e0 < 2 ? e0 : 2);
+    TilePipe<StripRec, kTileEvents> pp;
+    pp.sm = sm;
+    pp.full = full;
+    pp.src = a.srec;
+    pp.f0 = e0 - warm;
+    pp.nfaces = e1 - pp.f0;
+    pp.ntiles = (int)((pp.nfaces + kTileEvents - 1) / kTileEvents);
+
+    int first = warm;  // leading events of the current tile that are warm-up only
+    run_face_tiles(
+        pp, a.err,
+        [&](const StripRec *tilep, int cnt) {
+            // roles on entry: S1 = P2, S2 = P1 (the two most recent vertices)
+#pragma unroll 1
+            for (int k = 0; k < cnt; k += 3) {
+                {
+                    const StripRec r = tilep[k];
+                    strip_step<QX, QY>(r, r.q.z != 0.0f && k >= first, nqx, qy, qz, S1, S2, S0, acc);
+                }
+                if (k + 1 < cnt) {
+                    const StripRec r = tilep[k + 1];
+                    strip_step<QX, QY>(r, r.q.z != 0.0f && k + 1 >= first, nqx, qy, qz, S2, S0, S1, acc);
+                }
+                if (k + 2 < cnt) {
+                    const StripRec r = tilep[k + 2];
+                    strip_step<QX, QY>(r, r.q.z != 0.0f, nqx, qy, qz, S0, S1, S2, acc);
+                }
+            }
+            first = 0;
+        },
+        [&]() {
+            if (KAHAN) {
+#pragma unroll
+                for (int i = 0; i < QY; ++i)
+#pragma unroll
+                    for (int j = 0; j < QX; ++j) {
+                        float2 k = kst[i * QX + j][threadIdx.x];
+                        kahan_add(k.x, k.y, j % 2 ? acc[i][j / 2].y : acc[i][j / 2].x);
+                        kst[i * QX + j][threadIdx.x] = k;
+                        if (j % 2) acc[i][j / 2] = make_float2(0.0f, 0.0f);
+                    }
+            }
+        });
+
+    if (!valid_t) return;
+#pragma unroll
+    for (int i = 0; i < QY; ++i) {
+        const int iy = ty * QY + i;
+        if (iy >= ny) continue;
+#pragma unroll
+        for (int j = 0; j < QX; ++j) {
+            const int ix = tx * QX + j;
+            if (ix >= nx) continue;
+            const int64_t idx = ((int64_t)z * ny + iy) * nx + ix;
+            const float plain = j % 2 ? acc[i][j / 2].y : acc[i][j / 2].x;
+            const float2 k = KAHAN ? kst[i * QX + j][threadIdx.x] : make_float2(plain, 0.0f);
+            if (a.nsplit > 1)
+                a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(k.x, -k.y);
+            else
+                epilogue(a, idx, __fmul_rn(__fsub_rn(k.x, k.y), kInv2Pi));
+        }
+    }
+}
+
 template <int QL, bool KAHAN>
 __global__ void __launch_bounds__(kFwdThreads, 2) fwd_list_kernel(const FwdArgs a) {
     __shared__ __align__(128) FaceRec sm[kStages][kTileFaces];
@@ -500,7 +725,7 @@ __global__ void __launch_bounds__(kFwdThreads, 2) fwd_list_kernel(const FwdArgs 
 #pragma unroll
     for (int j = 0; j < QL; ++j) acc[j] = ks[j] = kc[j] = 0.0f;
 
-    TilePipe pp;
+    TilePipe<FaceRec> pp;
     pp.sm = sm;
     pp.full = full;
     pp.src = a.rec;
@@ -560,47 +785,57 @@ __global__ void split_reduce_kernel(const float2 *__restrict__ partial, int nspl
 // Host side.
 constexpr int kGridQX = 4, kGridQY = 2;  // 8 queries per thread on the grid path (3 CTAs per SM)
 constexpr int kListQ = 8;                // 8 queries per thread on the list path
+constexpr int kStripQX = 4, kStripQY = 2;  // 8 queries per thread on the strip grid path
 
-FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms) {
+FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms, int64_t n_events) {
     FwdPlan p{};
-    p.threads = kFwdThreads;
-    if (grid) {
-        p.qx = kGridQX;
-        p.qy = kGridQY;
-        const int64_t tiles = (int64_t)((g->n[0] + kGridQX - 1) / kGridQX) * ((g->n[1] + kGridQY - 1) / kGridQY) *
-                              g->n[2];
-        p.qblocks = (tiles + kFwdThreads - 1) / kFwdThreads;
+    p.strips = grid && n_events > 0;
+    int64_t nrec = nf, tile = kTileFaces, per_sm = grid ? 3 : 2;
+    if (p.strips) {
+        p.threads = kStripThreads;
+        p.qx = kStripQX;
+        p.qy = kStripQY;
+        nrec = n_events;
+        tile = kTileEvents;
+        per_sm = 5;
     } else {
-        p.qx = kListQ;
-        p.qy = 1;
-        p.qblocks = (nq + (int64_t)kFwdThreads * kListQ - 1) / ((int64_t)kFwdThreads * kListQ);
+        p.threads = kFwdThreads;
+        p.qx = grid ? kGridQX : kListQ;
+        p.qy = grid ? kGridQY : 1;
     }
-    // Three grid CTAs (two list CTAs) fit per SM. Split the face loop when the query CTAs alone
-    // would leave the GPU under-filled (fewer than ~4 waves), keeping at least 2 tiles of faces
-    // per split.
-    const int64_t slots = (grid ? 3LL : 2LL) * num_sms;
+    if (grid) {
+        const int64_t tiles = (int64_t)((g->n[0] + p.qx - 1) / p.qx) * ((g->n[1] + p.qy - 1) / p.qy) * g->n[2];
+        p.qblocks = (tiles + p.threads - 1) / p.threads;
+    } else {
+        p.qblocks = (nq + (int64_t)p.threads * kListQ - 1) / ((int64_t)p.threads * kListQ);
+    }
+    // per_sm CTAs fit on an SM. Split the face (event) loop when the query CTAs alone would leave
+    // the GPU under-filled (fewer than ~4 waves), keeping at least 2 tiles per split.
+    const int64_t slots = per_sm * num_sms;
     int nsplit = 1;
     if (p.qblocks < 4 * slots) {
         const int64_t want = (4 * slots + p.qblocks - 1) / p.qblocks;
-        const int64_t maxs = (nf + 2 * kTileFaces - 1) / (2 * kTileFaces);
+        const int64_t maxs = (nrec + 2 * tile - 1) / (2 * tile);
         nsplit = (int)(want < maxs ? want : maxs);
         if (nsplit < 1) nsplit = 1;
         if (nsplit > 65535) nsplit = 65535;
     }
-    p.nsplit = nsplit;
-    int64_t fps = (nf + nsplit - 1) / nsplit;
-    fps = ((fps + kTileFaces - 1) / kTileFaces) * kTileFaces;  // whole tiles per split
+    int64_t fps = (nrec + nsplit - 1) / nsplit;
+    fps = ((fps + tile - 1) / tile) * tile;  // whole tiles per split
     p.faces_per_split = fps;
-    p.nsplit = (int)((nf + fps - 1) / fps);
+    p.nsplit = (int)((nrec + fps - 1) / fps);
     return p;
 }
 
-cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
-                           int64_t nq, int arith, float2 *partial, float *w_out, uint8_t *occ_out,
-                           const uint8_t *near_flag, int *flag_list, int *flag_count, const LaunchCtx &ctx) {
+cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, const StripRec *srec, int64_t ne,
+                           const GridF *g, const float *queries, int64_t nq, int arith, float2 *partial, float *w_out,
+                           uint8_t *occ_out, const uint8_t *near_flag, int *flag_list, int *flag_count,
+                           const LaunchCtx &ctx) {
     FwdArgs a{};
     a.rec = rec;
     a.nf = nf;
+    a.srec = srec;
+    a.ne = ne;
     if (g) a.g = *g;
     a.queries = queries;
     a.nq = nq;
@@ -616,8 +851,10 @@ cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, con
     dim3 grid((unsigned)p.qblocks, (unsigned)p.nsplit);
     const bool kahan = arith != kArithFP32;
     if (arith == kArithFP16 && queries) return cudaErrorNotSupported;
-    const char *name = queries ? (kahan ? "fwd_list_kahan" : "fwd_list")
-                               : (arith == kArithFP16 ? "fwd_grid_fp16" : (kahan ? "fwd_grid_kahan" : "fwd_grid"));
+    if (p.strips && (queries || arith == kArithFP16 || !srec || ne < 1)) return cudaErrorInvalidValue;
+    const char *name = queries    ? (kahan ? "fwd_list_kahan" : "fwd_list")
+                       : p.strips ? (kahan ? "fwd_strip_kahan" : "fwd_strip")
+                                  : (arith == kArithFP16 ? "fwd_grid_fp16" : (kahan ? "fwd_grid_kahan" : "fwd_grid"));
     prof_begin(name, ctx.stream);
     if (queries) {
         if (kahan)
@@ -625,7 +862,12 @@ cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, con
         else
             fwd_list_kernel<kListQ, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
     } else {
-        if (arith == kArithFP16)
+        if (p.strips) {
+            if (kahan)
+                fwd_grid_strip_kernel<kStripQX, kStripQY, true><<<grid, kStripThreads, 0, ctx.stream>>>(a);
+            else
+                fwd_grid_strip_kernel<kStripQX, kStripQY, false><<<grid, kStripThreads, 0, ctx.stream>>>(a);
+        } else if (arith == kArithFP16)
             fwd_grid_kernel<kGridQX, kGridQY, true, true><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
         else if (kahan)
             fwd_grid_kernel<kGridQX, kGridQY, true, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);

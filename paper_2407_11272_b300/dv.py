@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
-    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2, "fp16": 3}
@@ -116,6 +116,8 @@ def load():
     lib.dv_dipole_backward.restype = ctypes.c_int
     lib.dv_flipped_duplication.argtypes = [_P, _P, ctypes.c_float, _P, _P, _P]
     lib.dv_flipped_duplication.restype = ctypes.c_int
+    lib.dv_build_strips.argtypes = [_P, _I64, _I64, _P, _P, _I64, ctypes.POINTER(_I64)]
+    lib.dv_build_strips.restype = ctypes.c_int
     lib.dv_profile_enable.argtypes = [ctypes.c_int]
     lib.dv_profile_enable.restype = None
     lib.dv_profile_reset.restype = None
@@ -351,6 +353,23 @@ def dv_dipole_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = N
                                      ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                      _stream(stream)), "dv_dipole_backward")
     return out
+
+
+def dv_build_strips(faces, nv: int):
+    """Strip order of the faces (host call, no GPU): returns (ev_vert, ev_face) int32 numpy arrays."""
+    import numpy as np
+
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    nf = f.shape[0]
+    lib = load()
+    n = _I64(0)
+    ptr = ctypes.c_void_p(f.ctypes.data)
+    _check(lib.dv_build_strips(ptr, nf, int(nv), None, None, 0, ctypes.byref(n)), "dv_build_strips")
+    ev_vert = np.empty(n.value, dtype=np.int32)
+    ev_face = np.empty(n.value, dtype=np.int32)
+    _check(lib.dv_build_strips(ptr, nf, int(nv), ctypes.c_void_p(ev_vert.ctypes.data),
+                               ctypes.c_void_p(ev_face.ctypes.data), n.value, ctypes.byref(n)), "dv_build_strips")
+    return ev_vert, ev_face
 
 
 def dv_flipped_duplication(mesh: Mesh, verts, eps: float = 0.01, stream=None):

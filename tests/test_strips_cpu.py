@@ -1,0 +1,73 @@
+"""Strip order of the faces (dv_build_strips, a host function of the library; no GPU).
+
+The forward passes visit faces in this order and take |v - q| of a face's older vertices and
+the dot of its older edge from the events before it, so the order must (1) contain every face
+exactly once, (2) give each face event the face's own vertex set as its last three vertices,
+and (3) actually share vertices (events per face well below 3) on the benchmark meshes."""
+import numpy as np
+import pytest
+
+from paper_2407_11272_b300 import dv, meshgen
+
+
+def _check_order(F, ev_vert, ev_face):
+    nf = len(F)
+    assert ev_vert.shape == ev_face.shape
+    assert nf <= len(ev_vert) <= 3 * nf
+    faces_seen = ev_face[ev_face >= 0]
+    assert np.array_equal(np.sort(faces_seen), np.arange(nf)), "every face exactly once"
+    k = 0
+    n = len(ev_vert)
+    while k < n:
+        # a strip: two vertex-only events, then at least one face event
+        assert k + 2 < n and ev_face[k] == -1 and ev_face[k + 1] == -1 and ev_face[k + 2] >= 0, k
+        k += 2
+        while k < n and ev_face[k] >= 0:
+            f = ev_face[k]
+            assert sorted(ev_vert[k - 2:k + 1].tolist()) == sorted(F[f].tolist()), (k, f)
+            k += 1
+
+
+@pytest.mark.parametrize("kind", ["torus", "icosphere", "sh_sphere", "open_sheet"])
+def test_strip_order_valid(kind):
+    if kind == "torus":
+        V, F = meshgen.jittered_torus()
+    elif kind == "icosphere":
+        V, F = meshgen.icosphere(3, 0.8)
+    elif kind == "sh_sphere":
+        V, F = meshgen.sh_sphere(freq=20)
+    else:
+        V, F = meshgen.jittered_torus(nu=12, nv=7, sigma=0.0, delete_frac=0.4, seed=3)
+    ev_vert, ev_face = dv.dv_build_strips(F, len(V))
+    _check_order(F, ev_vert, ev_face)
+    per_face = len(ev_vert) / len(F)
+    if kind == "torus":
+        assert per_face < 1.3, per_face  # 10 % faces deleted: strips break at the holes
+    if kind in ("icosphere", "sh_sphere"):
+        assert per_face < 1.1, per_face
+
+
+def test_strip_order_odd_inputs():
+    # non-manifold edge (three faces on edge 0-1), a degenerate face, an isolated face, and
+    # two faces with opposite orientations across an edge
+    F = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4], [5, 5, 6], [7, 8, 9], [2, 1, 10], [2, 10, 11]], dtype=np.int32)
+    ev_vert, ev_face = dv.dv_build_strips(F, 12)
+    _check_order(F, ev_vert, ev_face)
+    one = np.array([[0, 1, 2]], dtype=np.int32)
+    ev_vert, ev_face = dv.dv_build_strips(one, 3)
+    assert sorted(ev_vert.tolist()) == [0, 1, 2] and ev_face.tolist() == [-1, -1, 0]
+
+
+def test_strip_order_errors():
+    F = np.array([[0, 1, 2], [0, 2, 5]], dtype=np.int32)
+    with pytest.raises(dv.DvError):
+        dv.dv_build_strips(F, 5)  # index 5 outside [0, 5)
+    with pytest.raises(dv.DvError):
+        dv.dv_build_strips(np.array([[0, -1, 2]], dtype=np.int32), 3)
+
+
+def test_strip_order_deterministic():
+    V, F = meshgen.jittered_torus(nu=40, nv=20, sigma=0.01, delete_frac=0.1, seed=2)
+    a = dv.dv_build_strips(F, len(V))
+    b = dv.dv_build_strips(F, len(V))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
