@@ -40,6 +40,15 @@ UNIT = "pairs/s"
 OPS_FWD = 59
 OPS_BWD = 120
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# the dominant kernel on the full workload, keyed by (workload, kernel). Each entry records the
+# SHA-256 of the kernel's source file at capture time: if that file has changed since, the
+# counters no longer describe the kernel and the bench line reports traffic as null.
+TRAFFIC = {
+    ("torus_128", "bwd_grid"): (10764032, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                "b25552125709d6eceaec60899c383ca0e21dd30ce4384959128a5a17905ca7d3"),
+}
+
 WORKLOADS = {
     "torus_128": dict(desc="jittered open torus R=0.6 r=0.25 200x100, 10% faces deleted (36000 faces), "
                            "128^3 grid on [-1,1]^3, fwd(mixed: Kahan FP32 + FP64 re-eval) + bwd",
@@ -62,6 +71,24 @@ def _mesh_for(name):
     if name == "icosphere_32":
         return meshgen.icosphere(3, 0.8)
     raise SystemExit(f"unknown workload {name}")
+
+
+def _traffic(workload, kernel):
+    """Captured DRAM bytes per launch of `kernel` on `workload`, or None if not captured or if the
+    kernel's source changed after the capture."""
+    import hashlib
+
+    ent = TRAFFIC.get((workload, kernel))
+    if not ent:
+        return None
+    nbytes, src, digest = ent
+    path = os.path.join(ROOT, src)
+    if not os.path.exists(path):
+        return None
+    with open(path, "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != digest:
+            return None
+    return nbytes
 
 
 def _dist_env():
@@ -302,9 +329,10 @@ def run_native(args):
            "fwd_strip": OPS_FWD, "bwd_grid": OPS_BWD}.get(dname, OPS_FWD)
     avg_s = dms / max(dn, 1) * 1e-3
     achieved = ops * pairs / avg_s if avg_s > 0 else 0.0
+    traffic = _traffic(args.workload, dname)
     roof = {"bound": "alu", "kernel": dname, "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
             "unit": "Tlane-op/s (FP32, FMA=1)", "frac": achieved / fp32_peak if fp32_peak else None,
-            "traffic": None, "ops_per_pair": ops,
+            "traffic": traffic, "ops_per_pair": ops,
             "peak_note": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_src} sm_max_mhz)"}
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}

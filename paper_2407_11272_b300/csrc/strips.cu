@@ -10,8 +10,9 @@
 // (a, b, c) and N is taken from the face's own normal n_f (orientation of the input face), so
 // the strip's vertex order does not have to follow the face's orientation.
 //
-// Strips are grown greedily: start at the unused face with the fewest unused neighbours (the
-// classic heuristic that keeps isolated faces from being left as singletons), try its three
+// Strips are grown greedily: start at an unused face with the fewest unused neighbours (the
+// classic heuristic that keeps isolated faces from being left as singletons; a bucket queue,
+// most recently touched first), try its three
 // rotations, extend each forward across the edge formed by the last two vertices and then
 // backward from the first edge, keep the longest. Two faces are neighbours across an edge only
 // if exactly those two faces contain it (boundary and non-manifold edges end a strip); faces
@@ -22,7 +23,6 @@
 // with face index >= 0 completes the face formed with the two vertices before it.
 #include <algorithm>
 #include <cstdint>
-#include <queue>
 #include <utility>
 #include <vector>
 
@@ -31,12 +31,6 @@
 namespace dv {
 
 namespace {
-
-struct Edge {
-    uint64_t key;
-    int32_t face;
-    int32_t local;  // edge k joins corners k and (k+1) % 3
-};
 
 bool degenerate(const int32_t *t) { return t[0] == t[1] || t[1] == t[2] || t[2] == t[0]; }
 
@@ -48,40 +42,41 @@ void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int3
     ev_face.clear();
     ev_vert.reserve((size_t)nf * 3 / 2 + 16);
     ev_face.reserve((size_t)nf * 3 / 2 + 16);
-    // neighbour across each local edge (-1: none)
-    std::vector<int32_t> nb((size_t)nf * 3, -1);
+    // vertex -> incident faces (CSR), then the neighbour across each local edge (-1: none)
+    std::vector<int32_t> vptr((size_t)nv + 1, 0), vfaces((size_t)nf * 3);
+    for (int64_t i = 0; i < 3 * nf; ++i) vptr[(size_t)faces[i] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
     {
-        std::vector<Edge> e;
-        e.reserve((size_t)nf * 3);
-        for (int64_t f = 0; f < nf; ++f) {
-            const int32_t *t = faces + 3 * f;
-            if (degenerate(t)) continue;
-            for (int k = 0; k < 3; ++k) {
-                const uint64_t u = (uint32_t)t[k], v = (uint32_t)t[(k + 1) % 3];
-                const uint64_t key = u < v ? (u * (uint64_t)nv + v) : (v * (uint64_t)nv + u);
-                e.push_back({key, (int32_t)f, k});
+        std::vector<int32_t> fill(vptr.begin(), vptr.end() - 1);
+        for (int64_t i = 0; i < 3 * nf; ++i) vfaces[(size_t)fill[faces[i]]++] = (int32_t)(i / 3);
+    }
+    std::vector<int32_t> nb((size_t)nf * 3, -1);
+    for (int64_t f = 0; f < nf; ++f) {
+        const int32_t *t = faces + 3 * f;
+        if (degenerate(t)) continue;
+        for (int k = 0; k < 3; ++k) {
+            const int32_t u = t[k], v = t[(k + 1) % 3];
+            int32_t g = -1, n_other = 0;
+            for (int32_t c = vptr[u]; c < vptr[u + 1]; ++c) {
+                const int32_t h = vfaces[c];
+                if (h == f) continue;
+                const int32_t *th = faces + 3 * (int64_t)h;
+                if (th[0] == v || th[1] == v || th[2] == v) {  // h also has the edge {u, v}
+                    if (h != g) ++n_other;  // (a face listed twice under u counts once)
+                    g = h;
+                }
             }
-        }
-        std::sort(e.begin(), e.end(), [](const Edge &x, const Edge &y) {
-            return x.key != y.key ? x.key < y.key : (x.face != y.face ? x.face < y.face : x.local < y.local);
-        });
-        for (size_t i = 0; i < e.size();) {
-            size_t j = i;
-            while (j < e.size() && e[j].key == e[i].key) ++j;
-            if (j - i == 2 && e[i].face != e[i + 1].face) {
-                nb[(size_t)e[i].face * 3 + e[i].local] = e[i + 1].face;
-                nb[(size_t)e[i + 1].face * 3 + e[i + 1].local] = e[i].face;
-            }
-            i = j;
+            if (n_other == 1 && !degenerate(faces + 3 * (int64_t)g)) nb[(size_t)f * 3 + k] = g;
         }
     }
     std::vector<uint8_t> used((size_t)nf, 0);
     std::vector<int32_t> deg((size_t)nf, 0), stamp((size_t)nf, 0);
-    for (int64_t f = 0; f < nf; ++f)
+    // bucket queue on the number of unused neighbours (0..3), stale entries skipped on pop
+    std::vector<int32_t> bucket[4];
+    for (int64_t f = nf - 1; f >= 0; --f) {
         for (int k = 0; k < 3; ++k) deg[f] += nb[(size_t)f * 3 + k] >= 0;
-    using Item = std::pair<int32_t, int32_t>;  // (unused neighbours, face)
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
-    for (int64_t f = 0; f < nf; ++f) heap.push({deg[f], (int32_t)f});
+        bucket[deg[f]].push_back((int32_t)f);
+    }
     int32_t cur_stamp = 0;
 
     // Grow (seq, fs) across the edge (seq[-2], seq[-1]) while the face there is free.
@@ -107,11 +102,19 @@ void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int3
     };
 
     std::vector<int32_t> seq, fs, best_seq, best_fs;
-    while (!heap.empty()) {
-        const Item it = heap.top();
-        heap.pop();
-        const int32_t f = it.second;
-        if (used[f] || it.first != deg[f]) continue;
+    for (;;) {
+        int32_t f = -1;
+        for (int d = 0; d < 4 && f < 0; ++d) {
+            while (!bucket[d].empty()) {
+                const int32_t h = bucket[d].back();
+                bucket[d].pop_back();
+                if (!used[h] && deg[h] == d) {
+                    f = h;
+                    break;
+                }
+            }
+        }
+        if (f < 0) break;
         best_seq.clear();
         best_fs.clear();
         const int32_t *t = faces + 3 * (int64_t)f;
@@ -144,7 +147,7 @@ void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int3
         for (const int32_t g : best_fs)
             for (int k = 0; k < 3; ++k) {
                 const int32_t h = nb[(size_t)g * 3 + k];
-                if (h >= 0 && !used[h]) heap.push({--deg[h], h});
+                if (h >= 0 && !used[h]) bucket[--deg[h]].push_back(h);
             }
     }
 }

@@ -510,8 +510,8 @@ struct StripSlot {
 // Slow-path term for a strip face (same conventions as slow_term): 0 if the fast path took it,
 // 0 when q coincides with one of the face's vertices (a distance that is 0 after the flush to
 // zero of a subnormal |.|^2), else ATAN2(N, D) per Eq. (8).
-__device__ __forceinline__ float strip_slow_term(float N8, float D, float lmin) {
-    if (D > fabsf(N8)) return 0.0f;
+__device__ __forceinline__ float strip_slow_term(float N8, float D, float lmin, bool real) {
+    if (!real || D > fabsf(N8)) return 0.0f;
     if (!(lmin > 0.0f)) return 0.0f;
     return atan2f(__fadd_rn(N8, 0.0f), __fmul_rn(kNormalScale, D));
 }
@@ -519,7 +519,7 @@ __device__ __forceinline__ float strip_slow_term(float N8, float D, float lmin) 
 template <int QX, int QY, bool FACE>
 __device__ __forceinline__ void strip_event(const StripRec &r, const float2 (&nqx)[QX / 2], const float (&qy)[QY],
                                             float qz, const StripSlot<QX, QY> &P2, const StripSlot<QX, QY> &P1,
-                                            StripSlot<QX, QY> &V, float2 (&acc)[QY][QX / 2]) {
+                                            StripSlot<QX, QY> &V, float2 (&acc)[QY][QX / 2], bool real) {
     V.az = __fsub_rn(r.p.z, qz);
     const float2 vx = make_float2(r.p.x, r.p.x);
 #pragma unroll
@@ -573,8 +573,8 @@ __device__ __forceinline__ void strip_event(const StripRec &r, const float2 (&nq
                 D = __ffma2_rn(P1.l[i][j], d2, D);
                 const float lx = fminf(V.l[i][j].x, fminf(P1.l[i][j].x, P2.l[i][j].x));
                 const float ly = fminf(V.l[i][j].y, fminf(P1.l[i][j].y, P2.l[i][j].y));
-                acc[i][j].x = __fadd_rn(acc[i][j].x, strip_slow_term(N8.x, D.x, lx));
-                acc[i][j].y = __fadd_rn(acc[i][j].y, strip_slow_term(N8.y, D.y, ly));
+                acc[i][j].x = __fadd_rn(acc[i][j].x, strip_slow_term(N8.x, D.x, lx, real));
+                acc[i][j].y = __fadd_rn(acc[i][j].y, strip_slow_term(N8.y, D.y, ly, real));
             }
         }
     }
@@ -587,9 +587,9 @@ __device__ __forceinline__ void strip_step(const StripRec &r, bool face, const f
                                            const StripSlot<QX, QY> &P1, StripSlot<QX, QY> &V,
                                            float2 (&acc)[QY][QX / 2]) {
     if (face)
-        strip_event<QX, QY, true>(r, nqx, qy, qz, P2, P1, V, acc);
+        strip_event<QX, QY, true>(r, nqx, qy, qz, P2, P1, V, acc, true);
     else
-        strip_event<QX, QY, false>(r, nqx, qy, qz, P2, P1, V, acc);
+        strip_event<QX, QY, false>(r, nqx, qy, qz, P2, P1, V, acc, false);
 }
 
 template <int QX, int QY, bool KAHAN>
