@@ -28,7 +28,7 @@
 namespace dv {
 
 constexpr int kBwdThreads = 128;
-constexpr int kBwdWin = 4096;  // queries staged per window
+constexpr int kBwdWin = 2048;  // queries staged per window
 
 struct BwdArgs {
     const FaceRec *rec;
@@ -168,6 +168,40 @@ struct Kahan {
     }
 };
 
+// Per-face sums of the grid kernel, kept in shared memory (touched once per row of queries, so
+// the registers of the pair loop stay free): slot k of thread t is ks[k][t] = (sum, compensation),
+// k = 0..5 for T_cD, T_P, T_Q, T_R, T_ab, T_ac and 6 + 3i + j for U_i component j
+// (U_cD, U_a, U_b, U_c).
+constexpr int kFaceSlots = 18;
+
+__device__ __forceinline__ void kahan_sm(float2 *slot, float x) {
+    float2 k = *slot;
+    const float y = __fsub_rn(x, k.y);
+    const float t = __fadd_rn(k.x, y);
+    k.y = __fsub_rn(__fsub_rn(t, k.x), y);
+    k.x = t;
+    *slot = k;
+}
+
+__device__ __forceinline__ void fold_sm(float2 (*ks)[kBwdThreads], const float (&S)[7], const float (&X)[7], float ay,
+                                        float az) {
+    const int t = threadIdx.x;
+    kahan_sm(&ks[0][t], S[0]);
+    kahan_sm(&ks[1][t], S[1]);
+    kahan_sm(&ks[2][t], S[2]);
+    kahan_sm(&ks[3][t], S[3]);
+    kahan_sm(&ks[4][t], S[5]);
+    kahan_sm(&ks[5][t], S[6]);
+    const float ws[4] = {S[0], S[4] + S[3] + S[2], S[5] + S[1] + S[3], S[6] + S[2] + S[1]};
+    const float wx[4] = {X[0], X[4] + X[3] + X[2], X[5] + X[1] + X[3], X[6] + X[2] + X[1]};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        kahan_sm(&ks[6 + 3 * i][t], wx[i]);
+        kahan_sm(&ks[7 + 3 * i][t], ay * ws[i]);
+        kahan_sm(&ks[8 + 3 * i][t], az * ws[i]);
+    }
+}
+
 // Per-face sums: T[0..5] = T_cD, T_P, T_Q, T_R, T_ab, T_ac; U[0..3][3] = U_cD, U_a, U_b, U_c.
 struct FaceSums {
     Kahan T[6];
@@ -208,12 +242,10 @@ __device__ __forceinline__ FaceF load_face(const FaceRec *rec, int64_t f) {
     return F;
 }
 
-// Combine the face sums into the 9 gradient components (FP64 arithmetic) and store them.
-__device__ __forceinline__ void write_face_grad(const FaceF &F, const FaceSums &fs, float *out) {
-    double T[6], U[4][3];
-    for (int i = 0; i < 6; ++i) T[i] = (double)fs.T[i].s - (double)fs.T[i].c;
-    for (int i = 0; i < 4; ++i)
-        for (int k = 0; k < 3; ++k) U[i][k] = (double)fs.U[i][k].s - (double)fs.U[i][k].c;
+// Combine the face sums (T, U as compensated FP64 values) into the 9 gradient components (FP64
+// arithmetic) and store them.
+__device__ __forceinline__ void write_face_grad_d(const FaceF &F, const double (&T)[6], const double (&U)[4][3],
+                                                  float *out) {
     const double e1[3] = {(double)F.v1x - F.v0x, (double)F.v1y - F.v0y, (double)F.v1z - F.v0z};
     const double e2[3] = {(double)F.v2x - F.v0x, (double)F.v2y - F.v0y, (double)F.v2z - F.v0z};
     const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -232,6 +264,23 @@ __device__ __forceinline__ void write_face_grad(const FaceF &F, const FaceSums &
     }
 }
 
+__device__ __forceinline__ void write_face_grad(const FaceF &F, const FaceSums &fs, float *out) {
+    double T[6], U[4][3];
+    for (int i = 0; i < 6; ++i) T[i] = (double)fs.T[i].s - (double)fs.T[i].c;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) U[i][k] = (double)fs.U[i][k].s - (double)fs.U[i][k].c;
+    write_face_grad_d(F, T, U, out);
+}
+
+__device__ __forceinline__ void write_face_grad_sm(const FaceF &F, float2 (*ks)[kBwdThreads], float *out) {
+    const int t = threadIdx.x;
+    double T[6], U[4][3];
+    for (int i = 0; i < 6; ++i) T[i] = (double)ks[i][t].x - (double)ks[i][t].y;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) U[i][k] = (double)ks[6 + 3 * i + k][t].x - (double)ks[6 + 3 * i + k][t].y;
+    write_face_grad_d(F, T, U, out);
+}
+
 __device__ __forceinline__ bool all_finite(const float (&S)[7], const float (&X)[7]) {
     float t = 0.f;
 #pragma unroll
@@ -245,8 +294,9 @@ __device__ __forceinline__ bool all_finite(const float (&S)[7], const float (&X)
 __device__ __forceinline__ float win_nqx(const float *wf, int64_t i) { return wf[4 * (i >> 1) + (i & 1)]; }
 __device__ __forceinline__ float win_g(const float *wf, int64_t i) { return wf[4 * (i >> 1) + 2 + (i & 1)]; }
 
-__global__ void __launch_bounds__(kBwdThreads) bwd_grid_kernel(const BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 4) bwd_grid_kernel(const BwdArgs a) {
     __shared__ __align__(16) float wf[2 * kBwdWin];
+    __shared__ float2 ks[kFaceSlots][kBwdThreads];
     const int64_t f = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     const FaceF F = load_face(a.rec, f < a.nf ? f : a.nf - 1);
     FaceF2 F2;
@@ -258,8 +308,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_grid_kernel(const BwdArgs a) 
     const int64_t nrows = (int64_t)a.g.n[1] * a.g.n[2];
     const int64_t r0 = (int64_t)blockIdx.y * a.rows_per_split;
     const int64_t r1 = r0 + a.rows_per_split < nrows ? r0 + a.rows_per_split : nrows;
-    FaceSums fs;
-    fs.zero();
+#pragma unroll
+    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
     // Rows are processed in windows of whole rows when a row fits the window (packed pairs of
     // queries when the row length is even); longer rows go in pieces through the guarded path.
     const bool whole = nx <= kBwdWin;
@@ -325,12 +375,12 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_grid_kernel(const BwdArgs a) 
                     for (int ix = 0; ix < xlen; ++ix)
                         bwd_pair<true>(F, R, -win_nqx(wf, i0 + ix), win_g(wf, i0 + ix), S, X);
                 }
-                fs.fold(S, X, R.ay, R.az);
+                fold_sm(ks, S, X, R.ay, R.az);
             }
             if (whole) break;
         }
     }
-    if (f < a.nf) write_face_grad(F, fs, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+    if (f < a.nf) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
 // List path: arbitrary queries, no shared row parts; each query is its own "row".

@@ -510,86 +510,104 @@ struct StripSlot {
 // Slow-path term for a strip face (same conventions as slow_term): 0 if the fast path took it,
 // 0 when q coincides with one of the face's vertices (a distance that is 0 after the flush to
 // zero of a subnormal |.|^2), else ATAN2(N, D) per Eq. (8).
-__device__ __forceinline__ float strip_slow_term(float N8, float D, float lmin, bool real) {
-    if (!real || D > fabsf(N8)) return 0.0f;
+__device__ __forceinline__ float strip_slow_term(float N8, float D, float lmin) {
+    if (D > fabsf(N8)) return 0.0f;
     if (!(lmin > 0.0f)) return 0.0f;
     return atan2f(__fadd_rn(N8, 0.0f), __fmul_rn(kNormalScale, D));
 }
 
-template <int QX, int QY, bool FACE>
-__device__ __forceinline__ void strip_event(const StripRec &r, const float2 (&nqx)[QX / 2], const float (&qy)[QY],
-                                            float qz, const StripSlot<QX, QY> &P2, const StripSlot<QX, QY> &P1,
-                                            StripSlot<QX, QY> &V, float2 (&acc)[QY][QX / 2], bool real) {
+// Vertex part of a strip event: offsets of the event's vertex V from the thread's queries,
+// |V - q| (MUFU square root) and the dot with the previous vertex P1.
+template <int QX, int QY>
+__device__ __forceinline__ void strip_vertex(const StripRec &r, const float2 (&nqx)[QX / 2], const float (&qy)[QY],
+                                             float qz, const StripSlot<QX, QY> &P1, StripSlot<QX, QY> &V) {
     V.az = __fsub_rn(r.p.z, qz);
     const float2 vx = make_float2(r.p.x, r.p.x);
 #pragma unroll
     for (int j = 0; j < QX / 2; ++j) V.ax[j] = __fadd2_rn(vx, nqx[j]);
     const float azz = __fmul_rn(V.az, V.az), az1 = __fmul_rn(V.az, P1.az);
-    const float2 n8x = make_float2(r.p.w, r.p.w);
-    const float2 C0 = make_float2(DV_ATAN_C0, DV_ATAN_C0), C1 = make_float2(DV_ATAN_C1, DV_ATAN_C1);
-    const float2 C2 = make_float2(DV_ATAN_C2, DV_ATAN_C2);
-    bool ok = true;
 #pragma unroll
     for (int i = 0; i < QY; ++i) {
         V.ay[i] = __fsub_rn(r.p.y, qy[i]);
         const float Lyz = __fmaf_rn(V.ay[i], V.ay[i], azz);
         const float d1yz = __fmaf_rn(V.ay[i], P1.ay[i], az1);
-        const float d2yz = FACE ? __fmaf_rn(V.ay[i], P2.ay[i], __fmul_rn(V.az, P2.az)) : 0.0f;
-        const float Nyz = FACE ? __fmaf_rn(V.ay[i], r.q.x, __fmul_rn(V.az, r.q.y)) : 0.0f;
 #pragma unroll
         for (int j = 0; j < QX / 2; ++j) {
             const float2 l2 = __ffma2_rn(V.ax[j], V.ax[j], make_float2(Lyz, Lyz));
             V.l[i][j] = make_float2(sqrt_approx(l2.x), sqrt_approx(l2.y));
             V.e[i][j] = __ffma2_rn(V.ax[j], P1.ax[j], make_float2(d1yz, d1yz));  // (V - q).(P1 - q)
-            if (FACE) {
-                const float2 d2 = __ffma2_rn(V.ax[j], P2.ax[j], make_float2(d2yz, d2yz));  // (V - q).(P2 - q)
-                const float2 N8 = __ffma2_rn(V.ax[j], n8x, make_float2(Nyz, Nyz));
-                float2 D = __fmul2_rn(__ffma2_rn(V.l[i][j], P1.l[i][j], V.e[i][j]), P2.l[i][j]);
-                D = __ffma2_rn(V.l[i][j], P1.e[i][j], D);
-                D = __ffma2_rn(P1.l[i][j], d2, D);
-                const bool p0 = D.x > fabsf(N8.x), p1 = D.y > fabsf(N8.y);
-                ok = ok && p0 && p1;
-                float2 v = __fmul2_rn(N8, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
-                v.x = p0 ? v.x : 0.0f;
-                v.y = p1 ? v.y : 0.0f;
-                const float2 sq = __fmul2_rn(v, v);
-                const float2 P = __ffma2_rn(__ffma2_rn(C2, sq, C1), sq, C0);
-                acc[i][j] = __ffma2_rn(v, P, acc[i][j]);
-            }
-        }
-    }
-    if (FACE && __any_sync(kFull, !ok)) {
-        // rare: recompute N and D of this face (same operations, same results) for ATAN2
-#pragma unroll
-        for (int i = 0; i < QY; ++i) {
-            const float d2yz = __fmaf_rn(V.ay[i], P2.ay[i], __fmul_rn(V.az, P2.az));
-            const float Nyz = __fmaf_rn(V.ay[i], r.q.x, __fmul_rn(V.az, r.q.y));
-#pragma unroll
-            for (int j = 0; j < QX / 2; ++j) {
-                const float2 d2 = __ffma2_rn(V.ax[j], P2.ax[j], make_float2(d2yz, d2yz));
-                const float2 N8 = __ffma2_rn(V.ax[j], n8x, make_float2(Nyz, Nyz));
-                float2 D = __fmul2_rn(__ffma2_rn(V.l[i][j], P1.l[i][j], V.e[i][j]), P2.l[i][j]);
-                D = __ffma2_rn(V.l[i][j], P1.e[i][j], D);
-                D = __ffma2_rn(P1.l[i][j], d2, D);
-                const float lx = fminf(V.l[i][j].x, fminf(P1.l[i][j].x, P2.l[i][j].x));
-                const float ly = fminf(V.l[i][j].y, fminf(P1.l[i][j].y, P2.l[i][j].y));
-                acc[i][j].x = __fadd_rn(acc[i][j].x, strip_slow_term(N8.x, D.x, lx, real));
-                acc[i][j].y = __fadd_rn(acc[i][j].y, strip_slow_term(N8.y, D.y, ly, real));
-            }
         }
     }
 }
 
-// One event into slot V given the two before it; `face` is warp-uniform (same record for all).
+// N and D of the face {P2, P1, V} for pair (i, j) of the thread's queries.
 template <int QX, int QY>
-__device__ __forceinline__ void strip_step(const StripRec &r, bool face, const float2 (&nqx)[QX / 2],
-                                           const float (&qy)[QY], float qz, const StripSlot<QX, QY> &P2,
-                                           const StripSlot<QX, QY> &P1, StripSlot<QX, QY> &V,
+__device__ __forceinline__ void strip_nd(const StripRec &r, const StripSlot<QX, QY> &P2, const StripSlot<QX, QY> &P1,
+                                         const StripSlot<QX, QY> &V, int i, int j, float2 &N8, float2 &D) {
+    const float d2yz = __fmaf_rn(V.ay[i], P2.ay[i], __fmul_rn(V.az, P2.az));
+    const float Nyz = __fmaf_rn(V.ay[i], r.q.x, __fmul_rn(V.az, r.q.y));
+    const float2 d2 = __ffma2_rn(V.ax[j], P2.ax[j], make_float2(d2yz, d2yz));  // (V - q).(P2 - q)
+    N8 = __ffma2_rn(V.ax[j], make_float2(r.p.w, r.p.w), make_float2(Nyz, Nyz));
+    D = __fmul2_rn(__ffma2_rn(V.l[i][j], P1.l[i][j], V.e[i][j]), P2.l[i][j]);
+    D = __ffma2_rn(V.l[i][j], P1.e[i][j], D);
+    D = __ffma2_rn(P1.l[i][j], d2, D);
+}
+
+// Face part of a strip event: the ATAN2 fast path for the thread's queries; if any lane of the
+// warp has a pair outside it, the slow path recomputes N and D (same operations, same values)
+// and adds ATAN2 for exactly those pairs.
+template <int QX, int QY>
+__device__ __forceinline__ void strip_face(const StripRec &r, const StripSlot<QX, QY> &P2,
+                                           const StripSlot<QX, QY> &P1, const StripSlot<QX, QY> &V,
                                            float2 (&acc)[QY][QX / 2]) {
-    if (face)
-        strip_event<QX, QY, true>(r, nqx, qy, qz, P2, P1, V, acc, true);
-    else
-        strip_event<QX, QY, false>(r, nqx, qy, qz, P2, P1, V, acc, false);
+    const float2 C0 = make_float2(DV_ATAN_C0, DV_ATAN_C0), C1 = make_float2(DV_ATAN_C1, DV_ATAN_C1);
+    const float2 C2 = make_float2(DV_ATAN_C2, DV_ATAN_C2);
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < QY; ++i)
+#pragma unroll
+        for (int j = 0; j < QX / 2; ++j) {
+            float2 N8, D;
+            strip_nd(r, P2, P1, V, i, j, N8, D);
+            const bool p0 = D.x > fabsf(N8.x), p1 = D.y > fabsf(N8.y);
+            ok = ok && p0 && p1;
+            float2 v = __fmul2_rn(N8, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
+            v.x = p0 ? v.x : 0.0f;
+            v.y = p1 ? v.y : 0.0f;
+            const float2 sq = __fmul2_rn(v, v);
+            const float2 P = __ffma2_rn(__ffma2_rn(C2, sq, C1), sq, C0);
+            acc[i][j] = __ffma2_rn(v, P, acc[i][j]);
+        }
+    if (__any_sync(kFull, !ok)) {
+#pragma unroll
+        for (int i = 0; i < QY; ++i)
+#pragma unroll
+            for (int j = 0; j < QX / 2; ++j) {
+                float2 N8, D;
+                strip_nd(r, P2, P1, V, i, j, N8, D);
+                const float lx = fminf(V.l[i][j].x, fminf(P1.l[i][j].x, P2.l[i][j].x));
+                const float ly = fminf(V.l[i][j].y, fminf(P1.l[i][j].y, P2.l[i][j].y));
+                acc[i][j].x = __fadd_rn(acc[i][j].x, strip_slow_term(N8.x, D.x, lx));
+                acc[i][j].y = __fadd_rn(acc[i][j].y, strip_slow_term(N8.y, D.y, ly));
+            }
+    }
+}
+
+// One software-pipelined step: the face part of event k (if it completes a face) and the vertex
+// part of event k + 1 in one basic block, so the compiler can overlap the next vertex's square
+// roots with this face's arithmetic. The next vertex goes into P2's slot, which this face reads
+// first (the scheduler renames registers where it overlaps the two).
+template <int QX, int QY>
+__device__ __forceinline__ void strip_step(const StripRec &r, bool face, const StripRec &rn,
+                                           const float2 (&nqx)[QX / 2], const float (&qy)[QY], float qz,
+                                           StripSlot<QX, QY> &P2, const StripSlot<QX, QY> &P1,
+                                           const StripSlot<QX, QY> &V, float2 (&acc)[QY][QX / 2]) {
+    if (face) {
+        strip_face<QX, QY>(r, P2, P1, V, acc);
+        strip_vertex<QX, QY>(rn, nqx, qy, qz, V, P2);
+    } else {
+        strip_vertex<QX, QY>(rn, nqx, qy, qz, V, P2);
+    }
 }
 
 template <int QX, int QY, bool KAHAN>
@@ -654,21 +672,41 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_grid_strip_kernel(const 
     run_face_tiles(
         pp, a.err,
         [&](const StripRec *tilep, int cnt) {
-            // roles on entry: S1 = P2, S2 = P1 (the two most recent vertices)
+            // On entry S1, S2 hold the vertex parts of the two events before this tile (older,
+            // newer). Event k of the tile goes to slot k mod 3; step k finishes event k's face
+            // and computes event k + 1's vertex part.
+            strip_vertex<QX, QY>(tilep[0], nqx, qy, qz, S2, S0);
+            int k = 0;
 #pragma unroll 1
-            for (int k = 0; k < cnt; k += 3) {
-                {
-                    const StripRec r = tilep[k];
-                    strip_step<QX, QY>(r, r.q.z != 0.0f && k >= first, nqx, qy, qz, S1, S2, S0, acc);
-                }
-                if (k + 1 < cnt) {
-                    const StripRec r = tilep[k + 1];
-                    strip_step<QX, QY>(r, r.q.z != 0.0f && k + 1 >= first, nqx, qy, qz, S2, S0, S1, acc);
-                }
-                if (k + 2 < cnt) {
-                    const StripRec r = tilep[k + 2];
-                    strip_step<QX, QY>(r, r.q.z != 0.0f, nqx, qy, qz, S0, S1, S2, acc);
-                }
+            for (; k + 3 < cnt; k += 3) {
+                strip_step<QX, QY>(tilep[k], tilep[k].q.z != 0.0f && k >= first, tilep[k + 1], nqx, qy, qz, S1,
+                                   S2, S0, acc);
+                strip_step<QX, QY>(tilep[k + 1], tilep[k + 1].q.z != 0.0f && k + 1 >= first, tilep[k + 2], nqx, qy,
+                                   qz, S2, S0, S1, acc);
+                strip_step<QX, QY>(tilep[k + 2], tilep[k + 2].q.z != 0.0f, tilep[k + 3], nqx, qy, qz, S0, S1, S2,
+                                   acc);
+            }
+            // last one to three events of the tile; the vertex part after the tile's last event
+            // belongs to the next tile
+            {
+                const StripRec r = tilep[k];
+                const bool face = r.q.z != 0.0f && k >= first;
+                if (k + 1 < cnt)
+                    strip_step<QX, QY>(r, face, tilep[k + 1], nqx, qy, qz, S1, S2, S0, acc);
+                else if (face)
+                    strip_face<QX, QY>(r, S1, S2, S0, acc);
+            }
+            if (k + 1 < cnt) {
+                const StripRec r = tilep[k + 1];
+                const bool face = r.q.z != 0.0f && k + 1 >= first;
+                if (k + 2 < cnt)
+                    strip_step<QX, QY>(r, face, tilep[k + 2], nqx, qy, qz, S2, S0, S1, acc);
+                else if (face)
+                    strip_face<QX, QY>(r, S2, S0, S1, acc);
+            }
+            if (k + 2 < cnt) {
+                const StripRec r = tilep[k + 2];
+                if (r.q.z != 0.0f) strip_face<QX, QY>(r, S0, S1, S2, acc);
             }
             first = 0;
         },
