@@ -11,6 +11,7 @@ Functions (each follows the passage named in ``oracle.c``):
 * ``atan2_table(y, x)``               Eq. (8)
 * ``winding(V, F, Q)``                Eq. (5) / Algorithm 1, W = (1/4pi) sum Omega
 * ``grid_queries(lo, hi, n)``         cell-centred voxel grid (§3), x fastest
+* ``grid_points(lo, hi, n, cells)``   the same centres for selected linear cell indices
 * ``winding_grad(V, F, Q, g)``        sum_q g_q dW(q)/dV, chain rule through Eq. (7)
 * ``point_mesh_distance(V, F, Q)``    exact Euclidean distance to the nearest face
 * ``vertex_grad_subset(V, F, Q, g, ids)``  rows of winding_grad for selected vertices
@@ -71,6 +72,7 @@ def _load():
         lib.orc_vertex_grad_subset.argtypes = mesh_q + [_d, _i64, _I64, _d, ctypes.c_int]
         lib.orc_winding_grad_scale.argtypes = mesh_q + [_d, _d, ctypes.c_int]
         lib.orc_grid_queries.argtypes = [_f, _f, _i32, _d]
+        lib.orc_grid_points.argtypes = [_f, _f, _i32, _i64, _I64, _d]
         _lib = lib
     return _lib
 
@@ -181,6 +183,18 @@ def grid_queries(lo, hi, n) -> np.ndarray:
     nn = np.ascontiguousarray(np.broadcast_to(np.asarray(n, dtype=np.int32), (3,)))
     out = np.empty((int(np.prod(nn.astype(np.int64))), 3), dtype=np.float64)
     _load().orc_grid_queries(lo.ctypes.data_as(_f), hi.ctypes.data_as(_f), nn.ctypes.data_as(_i32), _dp(out))
+    return out
+
+
+def grid_points(lo, hi, n, cells) -> np.ndarray:
+    """Centres of the grid cells with the given linear indices (x fastest), FP64 [m, 3]."""
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, dtype=np.float32), (3,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, dtype=np.float32), (3,)))
+    nn = np.ascontiguousarray(np.broadcast_to(np.asarray(n, dtype=np.int32), (3,)))
+    c = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).ravel())
+    out = np.empty((len(c), 3), dtype=np.float64)
+    _load().orc_grid_points(lo.ctypes.data_as(_f), hi.ctypes.data_as(_f), nn.ctypes.data_as(_i32),
+                            c.ctypes.data_as(_i64), len(c), _dp(out))
     return out
 
 

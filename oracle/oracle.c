@@ -13,6 +13,7 @@
  *   orc_solid_angle      Eq. (7) read as Omega = 2 * ATAN2(alpha, beta)
  *   orc_winding          Eq. (5) / Algorithm 1: W(q) = (1/4pi) sum_f Omega_f(q)
  *   orc_grid_queries     §3: cell-centred voxel grid over a box
+ *   orc_grid_points      the same centres for selected cells only
  *   orc_winding_grad     derivative of Eq. (5)+(7) by the chain rule through
  *                        the normalized vectors e_j (the paper claims
  *                        differentiability, §1 and §2.4, but prints no formula)
@@ -115,6 +116,13 @@ void orc_winding(const double *V, int64_t nv, const int32_t *F, int64_t nf, cons
 
 /* §3: voxel centres of an n[0] x n[1] x n[2] grid over [lo, hi], x fastest.
  * The box corners arrive as float (the library's grid record) and are widened to double. */
+/* Centre of cell (ix, iy, iz): lo + (i + 1/2) h per axis. */
+static void cell_centre(const float *lo, const double *h, int64_t ix, int64_t iy, int64_t iz, double *out) {
+    out[0] = (double)lo[0] + ((double)ix + 0.5) * h[0];
+    out[1] = (double)lo[1] + ((double)iy + 0.5) * h[1];
+    out[2] = (double)lo[2] + ((double)iz + 0.5) * h[2];
+}
+
 void orc_grid_queries(const float *lo, const float *hi, const int32_t *n, double *out) {
     double h[3];
     for (int k = 0; k < 3; ++k) h[k] = ((double)hi[k] - (double)lo[k]) / (double)n[k];
@@ -122,11 +130,22 @@ void orc_grid_queries(const float *lo, const float *hi, const int32_t *n, double
     for (int32_t iz = 0; iz < n[2]; ++iz)
         for (int32_t iy = 0; iy < n[1]; ++iy)
             for (int32_t ix = 0; ix < n[0]; ++ix) {
-                out[3 * idx + 0] = (double)lo[0] + ((double)ix + 0.5) * h[0];
-                out[3 * idx + 1] = (double)lo[1] + ((double)iy + 0.5) * h[1];
-                out[3 * idx + 2] = (double)lo[2] + ((double)iz + 0.5) * h[2];
+                cell_centre(lo, h, ix, iy, iz, out + 3 * idx);
                 ++idx;
             }
+}
+
+/* The same cell centres for m selected cells, given by their linear index
+ * (iz * n[1] + iy) * n[0] + ix (x fastest), so that a sample of a grid too large
+ * to list can be evaluated. */
+void orc_grid_points(const float *lo, const float *hi, const int32_t *n, const int64_t *cells, int64_t m,
+                     double *out) {
+    double h[3];
+    for (int k = 0; k < 3; ++k) h[k] = ((double)hi[k] - (double)lo[k]) / (double)n[k];
+    for (int64_t j = 0; j < m; ++j) {
+        const int64_t c = cells[j];
+        cell_centre(lo, h, c % n[0], (c / n[0]) % n[1], c / ((int64_t)n[0] * n[1]), out + 3 * j);
+    }
 }
 
 /* Gradient of W(q) with respect to the three vertices of one face, chain rule

@@ -1,8 +1,9 @@
 // Near-surface selection for the FP64 re-evaluation: flag every query within kNearDist of a
 // triangle (Euclidean distance, conservative: a small FP32 margin only adds queries).
 //
-// Grid path: one warp per face visits the voxel centres inside the face's bounding box grown
-// by the threshold, computes the point-triangle distance in FP32 and sets near_flag[q] = 1.
+// Grid path: a warp per (face, z-slice group) visits the voxel centres inside the face's
+// bounding box grown by the threshold, computes the point-triangle distance in FP32 and sets
+// near_flag[q] = 1.
 // Work is O(sum over faces of voxels in the grown box), far below the F x Q pair count.
 // List path: one thread per query scans all faces with a bounding-box reject first.
 #include <math.h>
@@ -12,6 +13,7 @@
 namespace dv {
 
 constexpr float kNearThresh = kNearDist * 1.002f + 1e-6f;  // conservative FP32 margin
+constexpr int kNearZGroups = 32;  // warps sharing one face's z-slices (grid.y of the launch)
 
 __device__ __forceinline__ float dot3f(float ax, float ay, float az, float bx, float by, float bz) {
     return ax * bx + ay * by + az * bz;
@@ -77,16 +79,19 @@ __global__ void near_grid_kernel(const FaceRec *__restrict__ rec, int64_t nf, Gr
             if (i1[k] < i0[k]) empty = true;
         }
         if (empty) continue;
-        const int64_t sx = i1[0] - i0[0] + 1, sy = i1[1] - i0[1] + 1, sz = i1[2] - i0[2] + 1;
-        const int64_t total = sx * sy * sz;
-        for (int64_t t = lane; t < total; t += 32) {
-            const int ix = i0[0] + (int)(t % sx);
-            const int iy = i0[1] + (int)((t / sx) % sy);
-            const int iz = i0[2] + (int)(t / (sx * sy));
-            const float px = __fmaf_rn((float)ix + 0.5f, g.h[0], g.lo[0]);
-            const float py = __fmaf_rn((float)iy + 0.5f, g.h[1], g.lo[1]);
+        const int64_t sx = i1[0] - i0[0] + 1, sy = i1[1] - i0[1] + 1;
+        const int64_t total = sx * sy;
+        // z-slices of the box are shared out over grid.y, so a face much larger than a voxel
+        // is covered by many warps
+        for (int iz = i0[2] + (int)blockIdx.y; iz <= i1[2]; iz += (int)gridDim.y) {
             const float pz = __fmaf_rn((float)iz + 0.5f, g.h[2], g.lo[2]);
-            if (tri_d2(px, py, pz, r) <= T2) flag[((int64_t)iz * g.n[1] + iy) * g.n[0] + ix] = 1;
+            for (int64_t t = lane; t < total; t += 32) {
+                const int ix = i0[0] + (int)(t % sx);
+                const int iy = i0[1] + (int)(t / sx);
+                const float px = __fmaf_rn((float)ix + 0.5f, g.h[0], g.lo[0]);
+                const float py = __fmaf_rn((float)iy + 0.5f, g.h[1], g.lo[1]);
+                if (tri_d2(px, py, pz, r) <= T2) flag[((int64_t)iz * g.n[1] + iy) * g.n[0] + ix] = 1;
+            }
         }
     }
 }
@@ -120,7 +125,12 @@ cudaError_t launch_near_surface(const FaceRec *rec, int64_t nf, const GridF *g, 
         prof_begin("near_surface_grid", s);
         int64_t blocks = (nf * 32 + 255) / 256;
         if (blocks > 16384) blocks = 16384;
-        near_grid_kernel<<<(unsigned)blocks, 256, 0, s>>>(rec, nf, *g, near_flag);
+        // one z-group per 32 z-layers of the grid (faces spanning many layers on fine grids get
+        // more warps), at most kNearZGroups
+        int zg = g->n[2] / 32;
+        zg = zg < 1 ? 1 : (zg > kNearZGroups ? kNearZGroups : zg);
+        const unsigned zgroups = (unsigned)zg;
+        near_grid_kernel<<<dim3((unsigned)blocks, zgroups), 256, 0, s>>>(rec, nf, *g, near_flag);
     }
     count_launch();
     prof_end(queries ? "near_surface_list" : "near_surface_grid", s);

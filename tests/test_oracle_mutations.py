@@ -29,6 +29,7 @@ MUTANTS = {
     "grad_projection": ("(t[k] - e[j][k] * et)", "(t[k] + e[j][k] * et)"),
     "grad_len": ("/ len[j];\n    }\n}", "/ (len[j] * len[j]);\n    }\n}"),
     "grid_corner": ("((double)ix + 0.5)", "((double)ix)"),
+    "grid_points_index": ("(c / n[0]) % n[1], c / ((int64_t)n[0] * n[1])", "(c / n[0]) % n[1], c / n[1]"),
 }
 
 _d = ctypes.POINTER(ctypes.c_double)
@@ -116,7 +117,22 @@ def _pins_pass(lib) -> bool:
             fd[i, k] = (g @ _winding(lib, a, Fp, Qp) - g @ _winding(lib, b, Fp, Qp)) / (2 * h)
     ok &= np.allclose(G, fd, rtol=1e-5, atol=1e-7)
     ok &= np.allclose(_grid(lib, 4)[0], [-0.75, -0.75, -0.75])
+    ok &= np.allclose(_grid_points(lib, (4, 2, 8), [4 * 2 * 8 - 1]), [[0.75, 0.5, 0.875]])
     return bool(ok)
+
+
+def _grid_points(lib, n, cells):
+    lo = np.full(3, -1, np.float32)
+    hi = np.full(3, 1, np.float32)
+    nn = np.asarray(n, np.int32)
+    c = np.asarray(cells, np.int64)
+    out = np.empty((len(c), 3))
+    lib.orc_grid_points(lo.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                        hi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                        nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.c_int64(len(c)),
+                        out.ctypes.data_as(_d))
+    return out
 
 
 def test_unmutated_oracle_passes_condensed_pins(tmp_path):

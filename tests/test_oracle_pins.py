@@ -209,6 +209,16 @@ def test_grid_queries_cell_centred_x_fastest():
     np.testing.assert_allclose(Q[-1], [0.75, 2 / 3, 0.5])
 
 
+def test_grid_points_selected_cells():
+    """Cells picked by linear index (x fastest): closed-form centres, and agreement with the
+    full listing on a grid small enough to list."""
+    P = oracle.grid_points([-1, -1, -1], [1, 1, 1], [4, 3, 2], [0, 5, 23])
+    np.testing.assert_allclose(P, [[-0.75, -2 / 3, -0.5], [-0.25, 0.0, -0.5], [0.75, 2 / 3, 0.5]])
+    Q = oracle.grid_queries([-1, 0, -2], [1, 2, 1], [5, 7, 3])
+    cells = np.array([0, 4, 5, 34, 35, 70, 104])
+    np.testing.assert_array_equal(oracle.grid_points([-1, 0, -2], [1, 2, 1], [5, 7, 3], cells), Q[cells])
+
+
 # ---------------------------------------------------------------- gradient
 
 def _brute_fd(V, F, Q, g, h=1e-6):
