@@ -110,6 +110,8 @@ struct dv_mesh {
     float2 *ws_partial = nullptr;
     int64_t cap_fg = 0;       // floats
     float *ws_fg = nullptr;
+    int64_t cap_bins = 0;     // ints: query bins of the list path's near-surface selection
+    int *ws_bins = nullptr;
 };
 
 namespace {
@@ -221,7 +223,7 @@ dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_gri
         return fail(DV_ERR_UNSUPPORTED, "the FP16 ablation is implemented for grid queries only");
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
-    const int64_t nev = (grid && prec != DV_PREC_FP16) ? m->ne : 0;  // strip order on the grid path
+    const int64_t nev = prec != DV_PREC_FP16 ? m->ne : 0;  // strip order (all but the FP16 ablation)
     const dv::FwdPlan plan = dv::plan_forward(nq, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms, nev);
     const bool mixed = prec == DV_PREC_MIXED;
     dv_status st;
@@ -232,8 +234,10 @@ dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_gri
     const dv::LaunchCtx ctx{s, m->err};
     if (mixed) {
         DV_CUDA(cudaMemsetAsync(m->err + 1, 0, 3 * sizeof(int), s));
-        if (!queries) DV_CUDA(cudaMemsetAsync(m->ws_near, 0, (size_t)nq, s));
-        DV_CUDA(dv::launch_near_surface(m->rec, m->nf, grid ? &gf : nullptr, queries, nq, m->ws_near, s));
+        DV_CUDA(cudaMemsetAsync(m->ws_near, 0, (size_t)nq, s));  // the near kernels only set flags
+        if (queries && (st = grow(m->ws_bins, m->cap_bins, dv::near_list_scratch_ints(nq), s))) return st;
+        DV_CUDA(dv::launch_near_surface(m->rec, m->nf, grid ? &gf : nullptr, queries, nq, m->ws_near, m->ws_bins,
+                                        s));
     }
     int *list = mixed ? m->ws_list : nullptr;
     int *count = mixed ? m->err + 1 : nullptr;
@@ -292,7 +296,7 @@ void dv_mesh_destroy(dv_mesh *m) {
     DeviceGuard dg(m->device);
     void *bufs[] = {m->faces,   m->rec,     m->rec64, m->vtx_ptr, m->vtx_corner, m->ev_vert,    m->ev_face,
                     m->srec,    m->srec64,  m->err,   m->ws_w,    m->ws_near,    m->ws_list,    m->ws_partial,
-                    m->ws_fg};
+                    m->ws_fg,   m->ws_bins};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, m->last_stream);
     delete m;
@@ -387,7 +391,7 @@ dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_quer
     dv_status st;
     int64_t nq = max_list_queries, part = 0, fg = 0;
     if (max_list_queries > 0) {
-        const dv::FwdPlan fp = dv::plan_forward(max_list_queries, m->nf, false, nullptr, m->num_sms);
+        const dv::FwdPlan fp = dv::plan_forward(max_list_queries, m->nf, false, nullptr, m->num_sms, m->ne);
         const dv::BwdPlan bp = dv::plan_backward(max_list_queries, m->nf, false, nullptr, m->num_sms);
         part = fp.nsplit > 1 ? (int64_t)fp.nsplit * max_list_queries : 0;
         fg = (int64_t)bp.nsplit * m->nf * 9;

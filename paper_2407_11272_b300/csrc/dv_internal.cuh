@@ -199,9 +199,9 @@ struct FwdPlan {
     int64_t qblocks;     // CTAs over queries
     int nsplit;          // face splits (grid dimension y); 1 = no split
     int64_t faces_per_split;  // faces, or strip events when strips is set
-    bool strips;         // grid path over the strip events (FP32 / Kahan arithmetic)
+    bool strips;         // over the strip events (FP32 / Kahan arithmetic)
 };
-// n_events > 0 selects the strip-order grid kernel (grid queries, FP32 or Kahan arithmetic).
+// n_events > 0 selects the strip-order kernels (FP32 or Kahan arithmetic, grid or list).
 FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms, int64_t n_events = 0);
 // Per-pair arithmetic of the forward: FP32 with a plain sum, FP32 with Kahan across face tiles,
 // or the FP16 ablation (half2 per-pair terms, FP32 Kahan sums; grid queries only).
@@ -214,8 +214,11 @@ cudaError_t launch_split_reduce(const FwdPlan &p, const float2 *partial, int64_t
                                 const uint8_t *near_flag, int *flag_list, int *flag_count, cudaStream_t s);
 
 // near_surface.cu
+// Near-surface flags (distance <= 1e-3, conservative). The list path needs `scratch` of
+// near_list_scratch_ints(nq) ints (query bins); the grid path ignores it.
 cudaError_t launch_near_surface(const FaceRec *rec, int64_t nf, const GridF *g, const float *queries, int64_t nq,
-                                uint8_t *near_flag, cudaStream_t s);
+                                uint8_t *near_flag, int *scratch, cudaStream_t s);
+int64_t near_list_scratch_ints(int64_t nq);
 
 // winding_fp64.cu
 // FP64 re-evaluation of the flagged queries; over the strip events when srec64 is given

@@ -5,7 +5,8 @@
 // bounding box grown by the threshold, computes the point-triangle distance in FP32 and sets
 // near_flag[q] = 1.
 // Work is O(sum over faces of voxels in the grown box), far below the F x Q pair count.
-// List path: one thread per query scans all faces with a bounding-box reject first.
+// List path: queries binned into cells over the mesh's grown box; each face tests the queries
+// of the cells its grown box overlaps.
 #include <math.h>
 
 #include "dv_internal.cuh"
@@ -96,44 +97,179 @@ __global__ void near_grid_kernel(const FaceRec *__restrict__ rec, int64_t nf, Gr
     }
 }
 
-__global__ void near_list_kernel(const FaceRec *__restrict__ rec, int64_t nf, const float *__restrict__ q,
-                                 int64_t nq, uint8_t *__restrict__ flag) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nq) return;
-    const float px = q[3 * i], py = q[3 * i + 1], pz = q[3 * i + 2];
-    const float T2 = kNearThresh * kNearThresh;
-    uint8_t hit = 0;
-    for (int64_t f = 0; f < nf && !hit; ++f) {
+// List path: the queries are binned into a kBinG^3 grid of cells over the mesh's bounding box
+// grown by the threshold (queries outside it cannot be near), counting-sorted by cell, and each
+// face visits the cells its grown box overlaps, testing the queries there. Work is
+// O(sum over faces of queries in the grown box) instead of O(Q x F).
+constexpr int kBinG = 128;
+constexpr int kBoxThreads = 1024;
+
+// Grown bounding box of all faces: box[0..2] = lo, box[3..5] = hi (one CTA).
+__global__ void __launch_bounds__(kBoxThreads) mesh_box_kernel(const FaceRec *__restrict__ rec, int64_t nf,
+                                                               float *__restrict__ box) {
+    __shared__ float red[6][kBoxThreads / 32];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t f = threadIdx.x; f < nf; f += kBoxThreads) {
         const FaceRec r = rec[f];
-        if (px < fminf(r.r0.x, fminf(r.r1.x, r.r2.x)) - kNearThresh) continue;
-        if (px > fmaxf(r.r0.x, fmaxf(r.r1.x, r.r2.x)) + kNearThresh) continue;
-        if (py < fminf(r.r0.y, fminf(r.r1.y, r.r2.y)) - kNearThresh) continue;
-        if (py > fmaxf(r.r0.y, fmaxf(r.r1.y, r.r2.y)) + kNearThresh) continue;
-        if (pz < fminf(r.r0.z, fminf(r.r1.z, r.r2.z)) - kNearThresh) continue;
-        if (pz > fmaxf(r.r0.z, fmaxf(r.r1.z, r.r2.z)) + kNearThresh) continue;
-        if (tri_d2(px, py, pz, r) <= T2) hit = 1;
+        const float x[3][3] = {{r.r0.x, r.r0.y, r.r0.z}, {r.r1.x, r.r1.y, r.r1.z}, {r.r2.x, r.r2.y, r.r2.z}};
+        for (int v = 0; v < 3; ++v)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fminf(lo[k], x[v][k]);
+                hi[k] = fmaxf(hi[k], x[v][k]);
+            }
     }
-    flag[i] = hit;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(kFull, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(kFull, hi[k], o));
+        }
+        if (lane == 0) {
+            red[k][warp] = lo[k];
+            red[3 + k][warp] = hi[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int k = threadIdx.x;
+        float v = red[k][0];
+        for (int w = 1; w < kBoxThreads / 32; ++w) v = k < 3 ? fminf(v, red[k][w]) : fmaxf(v, red[k][w]);
+        // grown by the threshold plus a relative margin for the FP32 cell arithmetic
+        const float m = kNearThresh + 1e-6f * fabsf(v);
+        box[k] = k < 3 ? v - m : v + m;
+    }
 }
 
+__device__ __forceinline__ bool bin_coords(const float *box, float px, float py, float pz, int c[3]) {
+    const float p[3] = {px, py, pz};
+    for (int k = 0; k < 3; ++k) {
+        if (!(p[k] >= box[k] && p[k] <= box[3 + k])) return false;
+        const float t = (p[k] - box[k]) / (box[3 + k] - box[k]) * (float)kBinG;
+        c[k] = min(max((int)t, 0), kBinG - 1);
+    }
+    return true;
+}
+
+__global__ void bin_count_kernel(const float *__restrict__ q, int64_t nq, const float *__restrict__ box,
+                                 int *__restrict__ counts, int *__restrict__ qcell) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        int c[3];
+        int cell = -1;
+        if (bin_coords(box, q[3 * i], q[3 * i + 1], q[3 * i + 2], c)) {
+            cell = (c[2] * kBinG + c[1]) * kBinG + c[0];
+            atomicAdd(&counts[cell], 1);
+        }
+        qcell[i] = cell;
+    }
+}
+
+// Exclusive scan of the kBinG^3 counts into offsets (one CTA: each thread scans a contiguous
+// chunk, the chunk totals are scanned across the CTA).
+__global__ void __launch_bounds__(kBoxThreads) bin_scan_kernel(const int *__restrict__ counts,
+                                                               int *__restrict__ offsets) {
+    constexpr int kCells = kBinG * kBinG * kBinG;
+    constexpr int kChunk = kCells / kBoxThreads;
+    __shared__ int part[kBoxThreads];
+    const int base = threadIdx.x * kChunk;
+    int s = 0;
+    for (int i = 0; i < kChunk; ++i) s += counts[base + i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < kBoxThreads; o <<= 1) {  // inclusive Hillis-Steele scan of the chunk totals
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+    for (int i = 0; i < kChunk; ++i) {
+        offsets[base + i] = run;
+        run += counts[base + i];
+    }
+    if (threadIdx.x == kBoxThreads - 1) offsets[kCells] = run;
+}
+
+// Queries into cell order; counts[] is consumed (decremented to 0) for the slot within the cell.
+__global__ void bin_scatter_kernel(int64_t nq, const int *__restrict__ qcell, const int *__restrict__ offsets,
+                                   int *__restrict__ counts, int *__restrict__ sorted) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+        const int cell = qcell[i];
+        if (cell < 0) continue;
+        const int slot = atomicSub(&counts[cell], 1) - 1;
+        sorted[offsets[cell] + slot] = (int)i;
+    }
+}
+
+// One warp per (face, z-group of bin layers): test the queries in the bins that the face's
+// grown box overlaps.
+__global__ void near_binned_kernel(const FaceRec *__restrict__ rec, int64_t nf, const float *__restrict__ q,
+                                   const float *__restrict__ box, const int *__restrict__ offsets,
+                                   const int *__restrict__ sorted, uint8_t *__restrict__ flag) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float T2 = kNearThresh * kNearThresh;
+    float b[6];
+    for (int k = 0; k < 6; ++k) b[k] = box[k];
+    for (int64_t f = warp; f < nf; f += nwarps) {
+        const FaceRec r = rec[f];
+        const float vmin[3] = {fminf(r.r0.x, fminf(r.r1.x, r.r2.x)), fminf(r.r0.y, fminf(r.r1.y, r.r2.y)),
+                               fminf(r.r0.z, fminf(r.r1.z, r.r2.z))};
+        const float vmax[3] = {fmaxf(r.r0.x, fmaxf(r.r1.x, r.r2.x)), fmaxf(r.r0.y, fmaxf(r.r1.y, r.r2.y)),
+                               fmaxf(r.r0.z, fmaxf(r.r1.z, r.r2.z))};
+        int c0[3], c1[3];
+        for (int k = 0; k < 3; ++k) {
+            const float sc = (float)kBinG / (b[3 + k] - b[k]);
+            // one bin of slack on each side covers the rounding of the bin coordinates
+            c0[k] = max((int)floorf((vmin[k] - kNearThresh - b[k]) * sc) - 1, 0);
+            c1[k] = min((int)floorf((vmax[k] + kNearThresh - b[k]) * sc) + 1, kBinG - 1);
+        }
+        const int sx = c1[0] - c0[0] + 1, sy = c1[1] - c0[1] + 1;
+        for (int cz = c0[2] + (int)blockIdx.y; cz <= c1[2]; cz += (int)gridDim.y) {
+            for (int t = lane; t < sx * sy; t += 32) {
+                const int cell = (cz * kBinG + c0[1] + t / sx) * kBinG + c0[0] + t % sx;
+                for (int j = offsets[cell]; j < offsets[cell + 1]; ++j) {
+                    const int i = sorted[j];
+                    if (tri_d2(q[3 * (int64_t)i], q[3 * (int64_t)i + 1], q[3 * (int64_t)i + 2], r) <= T2) flag[i] = 1;
+                }
+            }
+        }
+    }
+}
+
+int64_t near_list_scratch_ints(int64_t nq) { return 2LL * kBinG * kBinG * kBinG + 8 + 2 * nq; }
+
 cudaError_t launch_near_surface(const FaceRec *rec, int64_t nf, const GridF *g, const float *queries, int64_t nq,
-                                uint8_t *near_flag, cudaStream_t s) {
+                                uint8_t *near_flag, int *scratch, cudaStream_t s) {
+    const int64_t nfb = (nf * 32 + 255) / 256 < 16384 ? (nf * 32 + 255) / 256 : 16384;
     if (queries) {
+        // scratch (near_list_scratch_ints(nq) ints): counts [G^3], offsets [G^3 + 1], box (6 floats),
+        // cell per query [nq], queries in cell order [nq]
+        constexpr int64_t kCells = (int64_t)kBinG * kBinG * kBinG;
+        int *counts = scratch, *offsets = scratch + kCells;
+        float *box = reinterpret_cast<float *>(scratch + 2 * kCells + 1);
+        int *qcell = scratch + 2 * kCells + 8, *sorted = qcell + nq;
+        const unsigned qb = (unsigned)((nq + 255) / 256 < 65535 ? (nq + 255) / 256 : 65535);
         prof_begin("near_surface_list", s);
-        near_list_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(rec, nf, queries, nq, near_flag);
+        cudaError_t e = cudaMemsetAsync(counts, 0, kCells * sizeof(int), s);
+        if (e != cudaSuccess) return e;
+        mesh_box_kernel<<<1, kBoxThreads, 0, s>>>(rec, nf, box);
+        bin_count_kernel<<<qb, 256, 0, s>>>(queries, nq, box, counts, qcell);
+        bin_scan_kernel<<<1, kBoxThreads, 0, s>>>(counts, offsets);
+        bin_scatter_kernel<<<qb, 256, 0, s>>>(nq, qcell, offsets, counts, sorted);
+        near_binned_kernel<<<dim3((unsigned)nfb, 4), 256, 0, s>>>(rec, nf, queries, box, offsets, sorted, near_flag);
+        for (int k = 0; k < 5; ++k) count_launch();
+        prof_end("near_surface_list", s);
     } else {
         prof_begin("near_surface_grid", s);
-        int64_t blocks = (nf * 32 + 255) / 256;
-        if (blocks > 16384) blocks = 16384;
         // one z-group per 32 z-layers of the grid (faces spanning many layers on fine grids get
         // more warps), at most kNearZGroups
         int zg = g->n[2] / 32;
         zg = zg < 1 ? 1 : (zg > kNearZGroups ? kNearZGroups : zg);
-        const unsigned zgroups = (unsigned)zg;
-        near_grid_kernel<<<dim3((unsigned)blocks, zgroups), 256, 0, s>>>(rec, nf, *g, near_flag);
+        near_grid_kernel<<<dim3((unsigned)nfb, (unsigned)zg), 256, 0, s>>>(rec, nf, *g, near_flag);
+        count_launch();
+        prof_end("near_surface_grid", s);
     }
-    count_launch();
-    prof_end(queries ? "near_surface_list" : "near_surface_grid", s);
     return cudaGetLastError();
 }
 

@@ -805,6 +805,176 @@ __global__ void __launch_bounds__(kFwdThreads, 2) fwd_list_kernel(const FwdArgs 
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// List forward over the strip order: arbitrary queries, so no (y, z) sharing; each thread
+// holds QP pairs of queries (packed FP32x2) and, per pair and strip slot, the vertex offsets,
+// |v - q| and the dot with the previous vertex. Same N, D, fast path and slow path as the grid
+// strip kernel; Kahan state in shared memory.
+template <int QP>
+struct ListSlot {
+    float2 ax[QP], ay[QP], az[QP];  // vertex - query
+    float2 l[QP];                   // |vertex - query|
+    float2 e[QP];                   // (vertex - query).(previous vertex - query)
+};
+
+template <int QP>
+__device__ __forceinline__ void list_nd(const StripRec &r, const ListSlot<QP> &P2, const ListSlot<QP> &P1,
+                                        const ListSlot<QP> &V, int j, float2 &N8, float2 &D) {
+    float2 d2 = __fmul2_rn(V.ax[j], P2.ax[j]);
+    d2 = __ffma2_rn(V.ay[j], P2.ay[j], d2);
+    d2 = __ffma2_rn(V.az[j], P2.az[j], d2);
+    N8 = __fmul2_rn(V.ax[j], make_float2(r.p.w, r.p.w));
+    N8 = __ffma2_rn(V.ay[j], make_float2(r.q.x, r.q.x), N8);
+    N8 = __ffma2_rn(V.az[j], make_float2(r.q.y, r.q.y), N8);
+    D = __fmul2_rn(__ffma2_rn(V.l[j], P1.l[j], V.e[j]), P2.l[j]);
+    D = __ffma2_rn(V.l[j], P1.e[j], D);
+    D = __ffma2_rn(P1.l[j], d2, D);
+}
+
+template <int QP, bool FACE>
+__device__ __forceinline__ void list_event(const StripRec &r, const float2 (&nq)[QP][3], const ListSlot<QP> &P2,
+                                           const ListSlot<QP> &P1, ListSlot<QP> &V, float2 (&acc)[QP]) {
+    const float2 vx = make_float2(r.p.x, r.p.x), vy = make_float2(r.p.y, r.p.y), vz = make_float2(r.p.z, r.p.z);
+    const float2 C0 = make_float2(DV_ATAN_C0, DV_ATAN_C0), C1 = make_float2(DV_ATAN_C1, DV_ATAN_C1);
+    const float2 C2 = make_float2(DV_ATAN_C2, DV_ATAN_C2);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < QP; ++j) {
+        V.ax[j] = __fadd2_rn(vx, nq[j][0]);
+        V.ay[j] = __fadd2_rn(vy, nq[j][1]);
+        V.az[j] = __fadd2_rn(vz, nq[j][2]);
+        float2 l2 = __fmul2_rn(V.ax[j], V.ax[j]);
+        l2 = __ffma2_rn(V.ay[j], V.ay[j], l2);
+        l2 = __ffma2_rn(V.az[j], V.az[j], l2);
+        V.l[j] = make_float2(sqrt_approx(l2.x), sqrt_approx(l2.y));
+        float2 e = __fmul2_rn(V.ax[j], P1.ax[j]);
+        e = __ffma2_rn(V.ay[j], P1.ay[j], e);
+        V.e[j] = __ffma2_rn(V.az[j], P1.az[j], e);
+        if (FACE) {
+            float2 N8, D;
+            list_nd<QP>(r, P2, P1, V, j, N8, D);
+            const bool p0 = D.x > fabsf(N8.x), p1 = D.y > fabsf(N8.y);
+            ok = ok && p0 && p1;
+            float2 v = __fmul2_rn(N8, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
+            v.x = p0 ? v.x : 0.0f;
+            v.y = p1 ? v.y : 0.0f;
+            const float2 sq = __fmul2_rn(v, v);
+            const float2 P = __ffma2_rn(__ffma2_rn(C2, sq, C1), sq, C0);
+            acc[j] = __ffma2_rn(v, P, acc[j]);
+        }
+    }
+    if (FACE && __any_sync(kFull, !ok)) {
+#pragma unroll
+        for (int j = 0; j < QP; ++j) {
+            float2 N8, D;
+            list_nd<QP>(r, P2, P1, V, j, N8, D);
+            const float lx = fminf(V.l[j].x, fminf(P1.l[j].x, P2.l[j].x));
+            const float ly = fminf(V.l[j].y, fminf(P1.l[j].y, P2.l[j].y));
+            acc[j].x = __fadd_rn(acc[j].x, strip_slow_term(N8.x, D.x, lx));
+            acc[j].y = __fadd_rn(acc[j].y, strip_slow_term(N8.y, D.y, ly));
+        }
+    }
+}
+
+template <int QP>
+__device__ __forceinline__ void list_step(const StripRec &r, bool face, const float2 (&nq)[QP][3],
+                                          const ListSlot<QP> &P2, const ListSlot<QP> &P1, ListSlot<QP> &V,
+                                          float2 (&acc)[QP]) {
+    if (face)
+        list_event<QP, true>(r, nq, P2, P1, V, acc);
+    else
+        list_event<QP, false>(r, nq, P2, P1, V, acc);
+}
+
+template <int QP, bool KAHAN>
+__global__ void __launch_bounds__(kStripThreads, 4) fwd_list_strip_kernel(const FwdArgs a) {
+    __shared__ __align__(128) StripRec sm[kStages][kTileEvents];
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ float2 kst[KAHAN ? 2 * QP : 1][kStripThreads];
+
+    // query j of this thread: base + j * blockDim (coalesced loads); pairs (2p, 2p + 1)
+    const int64_t base = (int64_t)blockIdx.x * kStripThreads * 2 * QP + threadIdx.x;
+    float2 nq[QP][3];
+#pragma unroll
+    for (int p = 0; p < QP; ++p) {
+        int64_t i0 = base + (int64_t)(2 * p) * kStripThreads, i1 = i0 + kStripThreads;
+        if (i0 >= a.nq) i0 = a.nq - 1;
+        if (i1 >= a.nq) i1 = a.nq - 1;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) nq[p][c] = make_float2(-a.queries[3 * i0 + c], -a.queries[3 * i1 + c]);
+    }
+    float2 acc[QP];
+    ListSlot<QP> S0, S1, S2;
+#pragma unroll
+    for (int p = 0; p < QP; ++p) {
+        acc[p] = make_float2(0.0f, 0.0f);
+        S0.ax[p] = S0.ay[p] = S0.az[p] = S0.l[p] = S0.e[p] = make_float2(0.0f, 0.0f);
+        S1.ax[p] = S1.ay[p] = S1.az[p] = S1.l[p] = S1.e[p] = make_float2(0.0f, 0.0f);
+        S2.ax[p] = S2.ay[p] = S2.az[p] = S2.l[p] = S2.e[p] = make_float2(0.0f, 0.0f);
+        if (KAHAN) {
+            kst[2 * p][threadIdx.x] = make_float2(0.0f, 0.0f);
+            kst[2 * p + 1][threadIdx.x] = make_float2(0.0f, 0.0f);
+        }
+    }
+
+    const int64_t e0 = (int64_t)blockIdx.y * a.faces_per_split;
+    const int64_t e1 = e0 + a.faces_per_split < a.ne ? e0 + a.faces_per_split : a.ne;
+    const int warm = (int)(e0 < 2 ? e0 : 2);
+    TilePipe<StripRec, kTileEvents> pp;
+    pp.sm = sm;
+    pp.full = full;
+    pp.src = a.srec;
+    pp.f0 = e0 - warm;
+    pp.nfaces = e1 - pp.f0;
+    pp.ntiles = (int)((pp.nfaces + kTileEvents - 1) / kTileEvents);
+
+    int first = warm;
+    run_face_tiles(
+        pp, a.err,
+        [&](const StripRec *tilep, int cnt) {
+            // roles on entry: S1 = P2, S2 = P1 (the two most recent vertices)
+#pragma unroll 1
+            for (int k = 0; k < cnt; k += 3) {
+                {
+                    const StripRec r = tilep[k];
+                    list_step<QP>(r, r.q.z != 0.0f && k >= first, nq, S1, S2, S0, acc);
+                }
+                if (k + 1 < cnt) {
+                    const StripRec r = tilep[k + 1];
+                    list_step<QP>(r, r.q.z != 0.0f && k + 1 >= first, nq, S2, S0, S1, acc);
+                }
+                if (k + 2 < cnt) {
+                    const StripRec r = tilep[k + 2];
+                    list_step<QP>(r, r.q.z != 0.0f, nq, S0, S1, S2, acc);
+                }
+            }
+            first = 0;
+        },
+        [&]() {
+            if (KAHAN) {
+#pragma unroll
+                for (int j = 0; j < 2 * QP; ++j) {
+                    float2 k = kst[j][threadIdx.x];
+                    kahan_add(k.x, k.y, j % 2 ? acc[j / 2].y : acc[j / 2].x);
+                    kst[j][threadIdx.x] = k;
+                    if (j % 2) acc[j / 2] = make_float2(0.0f, 0.0f);
+                }
+            }
+        });
+
+#pragma unroll
+    for (int j = 0; j < 2 * QP; ++j) {
+        const int64_t idx = base + (int64_t)j * kStripThreads;
+        if (idx >= a.nq) continue;
+        const float plain = j % 2 ? acc[j / 2].y : acc[j / 2].x;
+        const float2 k = KAHAN ? kst[j][threadIdx.x] : make_float2(plain, 0.0f);
+        if (a.nsplit > 1)
+            a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(k.x, -k.y);
+        else
+            epilogue(a, idx, __fmul_rn(__fsub_rn(k.x, k.y), kInv2Pi));
+    }
+}
+
 // Sum the face-split partials of each query in FP64, in split order, then the epilogue.
 __global__ void split_reduce_kernel(const float2 *__restrict__ partial, int nsplit, FwdArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -824,18 +994,19 @@ __global__ void split_reduce_kernel(const float2 *__restrict__ partial, int nspl
 constexpr int kGridQX = 4, kGridQY = 2;  // 8 queries per thread on the grid path (3 CTAs per SM)
 constexpr int kListQ = 8;                // 8 queries per thread on the list path
 constexpr int kStripQX = 4, kStripQY = 2;  // 8 queries per thread on the strip grid path
+constexpr int kListQP = 2;                 // 2 packed pairs (4 queries) per thread, strip list path
 
 FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms, int64_t n_events) {
     FwdPlan p{};
-    p.strips = grid && n_events > 0;
+    p.strips = n_events > 0;
     int64_t nrec = nf, tile = kTileFaces, per_sm = grid ? 3 : 2;
     if (p.strips) {
         p.threads = kStripThreads;
-        p.qx = kStripQX;
-        p.qy = kStripQY;
+        p.qx = grid ? kStripQX : 2 * kListQP;
+        p.qy = grid ? kStripQY : 1;
         nrec = n_events;
         tile = kTileEvents;
-        per_sm = 5;
+        per_sm = 4;
     } else {
         p.threads = kFwdThreads;
         p.qx = grid ? kGridQX : kListQ;
@@ -845,7 +1016,7 @@ FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_
         const int64_t tiles = (int64_t)((g->n[0] + p.qx - 1) / p.qx) * ((g->n[1] + p.qy - 1) / p.qy) * g->n[2];
         p.qblocks = (tiles + p.threads - 1) / p.threads;
     } else {
-        p.qblocks = (nq + (int64_t)p.threads * kListQ - 1) / ((int64_t)p.threads * kListQ);
+        p.qblocks = (nq + (int64_t)p.threads * p.qx - 1) / ((int64_t)p.threads * p.qx);
     }
     // per_sm CTAs fit on an SM. Split the face (event) loop when the query CTAs alone would leave
     // the GPU under-filled (fewer than ~4 waves), keeping at least 2 tiles per split.
@@ -889,12 +1060,18 @@ cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, con
     dim3 grid((unsigned)p.qblocks, (unsigned)p.nsplit);
     const bool kahan = arith != kArithFP32;
     if (arith == kArithFP16 && queries) return cudaErrorNotSupported;
-    if (p.strips && (queries || arith == kArithFP16 || !srec || ne < 1)) return cudaErrorInvalidValue;
-    const char *name = queries    ? (kahan ? "fwd_list_kahan" : "fwd_list")
+    if (p.strips && (arith == kArithFP16 || !srec || ne < 1)) return cudaErrorInvalidValue;
+    const char *name = queries    ? (p.strips ? (kahan ? "fwd_list_strip_kahan" : "fwd_list_strip")
+                                              : (kahan ? "fwd_list_kahan" : "fwd_list"))
                        : p.strips ? (kahan ? "fwd_strip_kahan" : "fwd_strip")
                                   : (arith == kArithFP16 ? "fwd_grid_fp16" : (kahan ? "fwd_grid_kahan" : "fwd_grid"));
     prof_begin(name, ctx.stream);
-    if (queries) {
+    if (queries && p.strips) {
+        if (kahan)
+            fwd_list_strip_kernel<kListQP, true><<<grid, kStripThreads, 0, ctx.stream>>>(a);
+        else
+            fwd_list_strip_kernel<kListQP, false><<<grid, kStripThreads, 0, ctx.stream>>>(a);
+    } else if (queries) {
         if (kahan)
             fwd_list_kernel<kListQ, true><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
         else

@@ -5,6 +5,7 @@ strips cut by face splits (small grids split the face loop across CTAs, so a spl
 the middle of a strip and must warm up on the two events before it), and a ragged grid."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from _util import check_forward, make_mesh, oracle_grid
@@ -66,3 +67,37 @@ def test_strip_order_ragged_grid(cuda_device):
     for prec in ("fp32", "mixed"):
         w, occ, _ = dv.dv_voxelize_grid(mesh, grid, precision=prec)
         check_forward(w.cpu().numpy(), w64, d, prec, occ.cpu().numpy(), f"ragged/{prec}")
+
+
+@pytest.mark.parametrize("kind", ["torus", "soup"])
+def test_list_path_near_surface_queries(cuda_device, kind):
+    """Query lists in strip order, with many queries within 1e-3 of a face (centroids pushed
+    off the face by 1e-6 .. 9e-4, and points next to edges and vertices) among uniform ones:
+    every near query must come back at FP64 accuracy (the binned near-surface selection must
+    find all of them), far ones within the FP32 bar."""
+    if kind == "torus":
+        V, F = meshgen.jittered_torus(nu=80, nv=40, sigma=0.01, delete_frac=0.1, seed=5)
+    else:
+        V, F = _soup(400, seed=13)
+    rng = np.random.default_rng(17)
+    V64 = V.astype(np.float64)
+    P = V64[F]
+    cen = P.mean(axis=1)
+    n = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    pick = rng.choice(len(F), size=1500, replace=True)
+    off = rng.uniform(1e-6, 9e-4, size=len(pick)) * rng.choice([-1.0, 1.0], size=len(pick))
+    near_c = cen[pick] + off[:, None] * n[pick]
+    t = rng.uniform(0.05, 0.95, size=len(pick))[:, None]
+    near_e = P[pick, 0] * t + P[pick, 1] * (1 - t) + rng.normal(scale=3e-4, size=(len(pick), 3))
+    near_v = P[pick, 2] + rng.normal(scale=3e-4, size=(len(pick), 3))
+    far = rng.uniform(-1, 1, size=(6000, 3))
+    Q = np.vstack([near_c, near_e, near_v, far]).astype(np.float32)
+    w64 = oracle.winding(V, F, Q)
+    d = oracle.point_mesh_distance(V, F, Q)
+    assert (d <= 1e-3).sum() > 3000
+    mesh = make_mesh(V, F, cuda_device)
+    Qd = torch.from_numpy(Q).to(cuda_device)
+    for prec in ("kahan", "mixed"):
+        w = dv.dv_winding(mesh, queries=Qd, precision=prec).cpu().numpy()
+        check_forward(w, w64, d, prec, None, f"list/{kind}/{prec}")
