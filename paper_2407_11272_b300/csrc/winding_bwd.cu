@@ -158,18 +158,8 @@ __device__ __forceinline__ void bwd_pair2(const FaceF2 &F, const RowB2 &R, float
     X[6] = __ffma2_rn(alC, ax, X[6]);
 }
 
-struct Kahan {
-    float s, c;
-    __device__ __forceinline__ void add(float x) {
-        const float y = __fsub_rn(x, c);
-        const float t = __fadd_rn(s, y);
-        c = __fsub_rn(__fsub_rn(t, s), y);
-        s = t;
-    }
-};
-
-// Per-face sums of the grid kernel, kept in shared memory (touched once per row of queries, so
-// the registers of the pair loop stay free): slot k of thread t is ks[k][t] = (sum, compensation),
+// Per-face sums, kept in shared memory (touched once per row or chunk of queries, so the
+// registers of the pair loop stay free): slot k of thread t is ks[k][t] = (sum, compensation),
 // k = 0..5 for T_cD, T_P, T_Q, T_R, T_ab, T_ac and 6 + 3i + j for U_i component j
 // (U_cD, U_a, U_b, U_c).
 constexpr int kFaceSlots = 18;
@@ -201,34 +191,6 @@ __device__ __forceinline__ void fold_sm(float2 (*ks)[kBwdThreads], const float (
         kahan_sm(&ks[8 + 3 * i][t], az * ws[i]);
     }
 }
-
-// Per-face sums: T[0..5] = T_cD, T_P, T_Q, T_R, T_ab, T_ac; U[0..3][3] = U_cD, U_a, U_b, U_c.
-struct FaceSums {
-    Kahan T[6];
-    Kahan U[4][3];
-    __device__ __forceinline__ void zero() {
-        for (int i = 0; i < 6; ++i) T[i].s = T[i].c = 0.f;
-        for (int i = 0; i < 4; ++i)
-            for (int k = 0; k < 3; ++k) U[i][k].s = U[i][k].c = 0.f;
-    }
-    // Fold one row's sums (row constants ay, az).
-    __device__ __forceinline__ void fold(const float (&S)[7], const float (&X)[7], float ay, float az) {
-        T[0].add(S[0]);
-        T[1].add(S[1]);
-        T[2].add(S[2]);
-        T[3].add(S[3]);
-        T[4].add(S[5]);
-        T[5].add(S[6]);
-        const float ws[4] = {S[0], S[4] + S[3] + S[2], S[5] + S[1] + S[3], S[6] + S[2] + S[1]};
-        const float wx[4] = {X[0], X[4] + X[3] + X[2], X[5] + X[1] + X[3], X[6] + X[2] + X[1]};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            U[i][0].add(wx[i]);
-            U[i][1].add(ay * ws[i]);
-            U[i][2].add(az * ws[i]);
-        }
-    }
-};
 
 __device__ __forceinline__ FaceF load_face(const FaceRec *rec, int64_t f) {
     const FaceRec r = rec[f];
@@ -262,14 +224,6 @@ __device__ __forceinline__ void write_face_grad_d(const FaceF &F, const double (
         out[3 + k] = (float)(g1 * kInv2PiD);
         out[6 + k] = (float)(g2 * kInv2PiD);
     }
-}
-
-__device__ __forceinline__ void write_face_grad(const FaceF &F, const FaceSums &fs, float *out) {
-    double T[6], U[4][3];
-    for (int i = 0; i < 6; ++i) T[i] = (double)fs.T[i].s - (double)fs.T[i].c;
-    for (int i = 0; i < 4; ++i)
-        for (int k = 0; k < 3; ++k) U[i][k] = (double)fs.U[i][k].s - (double)fs.U[i][k].c;
-    write_face_grad_d(F, T, U, out);
 }
 
 __device__ __forceinline__ void write_face_grad_sm(const FaceF &F, float2 (*ks)[kBwdThreads], float *out) {
@@ -383,34 +337,127 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_grid_kernel(const BwdArgs 
     if (f < a.nf) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
-// List path: arbitrary queries, no shared row parts; each query is its own "row".
-__global__ void __launch_bounds__(kBwdThreads) bwd_list_kernel(const BwdArgs a) {
-    __shared__ float4 win[kBwdWin / 2];  // (x, y, z, g)
+// List path: arbitrary queries, so no row sharing. Two queries per packed FP32x2 instruction;
+// per pair of queries the adjoint terms go straight into the 6 T sums and the 4 a-weighted
+// combinations U_i = sum W_i a (12 FMAs), plain FP32 over chunks of kListChunk queries, folded
+// per chunk into the Kahan face sums (shared memory). A chunk whose sums are not finite (a query
+// on a vertex or an edge line) is recomputed by the guarded scalar path.
+constexpr int kListChunk = 128;
+
+struct FaceL2 {
+    float2 v0x, v0y, v0z, v1x, v1y, v1z, v2x, v2y, v2z, nx, ny, nz;
+};
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float4 q1, float2 (&T)[6],
+                                               float2 (&U)[4][3]) {
+    // window entries are (-x, -y, -z, g)
+    const float2 nqx = make_float2(q0.x, q1.x), nqy = make_float2(q0.y, q1.y), nqz = make_float2(q0.z, q1.z);
+    const float2 g = make_float2(q0.w, q1.w);
+    const float2 ax = __fadd2_rn(F.v0x, nqx), ay = __fadd2_rn(F.v0y, nqy), az = __fadd2_rn(F.v0z, nqz);
+    const float2 bx = __fadd2_rn(F.v1x, nqx), by = __fadd2_rn(F.v1y, nqy), bz = __fadd2_rn(F.v1z, nqz);
+    const float2 cx = __fadd2_rn(F.v2x, nqx), cy = __fadd2_rn(F.v2y, nqy), cz = __fadd2_rn(F.v2z, nqz);
+    const float2 la2 = __ffma2_rn(az, az, __ffma2_rn(ay, ay, __fmul2_rn(ax, ax)));
+    const float2 lb2 = __ffma2_rn(bz, bz, __ffma2_rn(by, by, __fmul2_rn(bx, bx)));
+    const float2 lc2 = __ffma2_rn(cz, cz, __ffma2_rn(cy, cy, __fmul2_rn(cx, cx)));
+    const float2 ia = make_float2(rsqrt_approx(la2.x), rsqrt_approx(la2.y));
+    const float2 ib = make_float2(rsqrt_approx(lb2.x), rsqrt_approx(lb2.y));
+    const float2 ic = make_float2(rsqrt_approx(lc2.x), rsqrt_approx(lc2.y));
+    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
+    const float2 ab = __ffma2_rn(az, bz, __ffma2_rn(ay, by, __fmul2_rn(ax, bx)));
+    const float2 bcd = __ffma2_rn(bz, cz, __ffma2_rn(by, cy, __fmul2_rn(bx, cx)));
+    const float2 ca = __ffma2_rn(cz, az, __ffma2_rn(cy, ay, __fmul2_rn(cx, ax)));
+    const float2 N = __ffma2_rn(az, F.nz, __ffma2_rn(ay, F.ny, __fmul2_rn(ax, F.nx)));
+    const float2 tc = __ffma2_rn(la, lb, ab);
+    float2 D = __fmul2_rn(tc, lc);
+    D = __ffma2_rn(la, bcd, D);
+    D = __ffma2_rn(lb, ca, D);
+    const float2 den = __ffma2_rn(N, N, __fmul2_rn(D, D));
+    const float2 gr = __fmul2_rn(g, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    const float2 cD = __fmul2_rn(gr, D), cN = __fmul2_rn(gr, N);
+    const float2 P = __fmul2_rn(cN, la), Qb = __fmul2_rn(cN, lb), Rc = __fmul2_rn(cN, lc);
+    const float2 alA = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lb, lc, bcd), ia));
+    const float2 alB = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lc, la, ca), ib));
+    const float2 alC = __fmul2_rn(cN, __fmul2_rn(tc, ic));
+    T[0] = __fadd2_rn(T[0], cD);
+    T[1] = __fadd2_rn(T[1], P);
+    T[2] = __fadd2_rn(T[2], Qb);
+    T[3] = __fadd2_rn(T[3], Rc);
+    T[4] = __fadd2_rn(T[4], alB);
+    T[5] = __fadd2_rn(T[5], alC);
+    const float2 W[4] = {cD, __fadd2_rn(alA, __fadd2_rn(Rc, Qb)), __fadd2_rn(alB, __fadd2_rn(P, Rc)),
+                         __fadd2_rn(alC, __fadd2_rn(Qb, P))};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        U[i][0] = __ffma2_rn(W[i], ax, U[i][0]);
+        U[i][1] = __ffma2_rn(W[i], ay, U[i][1]);
+        U[i][2] = __ffma2_rn(W[i], az, U[i][2]);
+    }
+}
+
+__global__ void __launch_bounds__(kBwdThreads, 4) bwd_list_kernel(const BwdArgs a) {
+    __shared__ float4 win[kBwdWin / 2];  // (-x, -y, -z, g), padded to an even count with g = 0
+    __shared__ float2 ks[kFaceSlots][kBwdThreads];
     const int64_t f = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     const FaceF F = load_face(a.rec, f < a.nf ? f : a.nf - 1);
+    FaceL2 F2;
+    F2.v0x = bc2(F.v0x); F2.v0y = bc2(F.v0y); F2.v0z = bc2(F.v0z);
+    F2.v1x = bc2(F.v1x); F2.v1y = bc2(F.v1y); F2.v1z = bc2(F.v1z);
+    F2.v2x = bc2(F.v2x); F2.v2y = bc2(F.v2y); F2.v2z = bc2(F.v2z);
+    F2.nx = bc2(F.nx); F2.ny = bc2(F.ny); F2.nz = bc2(F.nz);
     const int64_t q0 = (int64_t)blockIdx.y * a.rows_per_split;
     const int64_t q1 = q0 + a.rows_per_split < a.nq ? q0 + a.rows_per_split : a.nq;
-    FaceSums fs;
-    fs.zero();
+#pragma unroll
+    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
     for (int64_t w0 = q0; w0 < q1; w0 += kBwdWin / 2) {
         const int len = (int)(q1 - w0 < kBwdWin / 2 ? q1 - w0 : kBwdWin / 2);
+        const int len2 = (len + 1) & ~1;
         __syncthreads();
-        for (int i = threadIdx.x; i < len; i += kBwdThreads) {
-            const int64_t k = w0 + i;
-            win[i] = make_float4(a.queries[3 * k], a.queries[3 * k + 1], a.queries[3 * k + 2], a.upstream[k]);
+        for (int i = threadIdx.x; i < len2; i += kBwdThreads) {
+            const int64_t k = w0 + (i < len ? i : len - 1);
+            win[i] = make_float4(-a.queries[3 * k], -a.queries[3 * k + 1], -a.queries[3 * k + 2],
+                                 i < len ? a.upstream[k] : 0.0f);
         }
         __syncthreads();
-        for (int i = 0; i < len; ++i) {
-            const float4 q = win[i];
-            const RowB R = row_b(F, q.y, q.z);
-            float S[7], X[7];
+        for (int c0 = 0; c0 < len2; c0 += kListChunk) {
+            const int c1 = c0 + kListChunk < len2 ? c0 + kListChunk : len2;
+            float2 T[6], U[4][3];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-            bwd_pair<true>(F, R, q.x, q.w, S, X);
-            fs.fold(S, X, R.ay, R.az);
+            for (int k = 0; k < 6; ++k) T[k] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) U[i][0] = U[i][1] = U[i][2] = make_float2(0.f, 0.f);
+#pragma unroll 2
+            for (int i = c0; i < c1; i += 2) bwd_list_pair2(F2, win[i], win[i + 1], T, U);
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) t += T[k].x + T[k].y;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) t += U[i][0].x + U[i][0].y + U[i][1].x + U[i][1].y + U[i][2].x + U[i][2].y;
+            if (isfinite(t)) {
+                const int th = threadIdx.x;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) kahan_sm(&ks[k][th], T[k].x + T[k].y);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) kahan_sm(&ks[6 + 3 * i + j][th], U[i][j].x + U[i][j].y);
+            } else {
+                // guarded scalar recompute of this chunk, one query at a time
+                const int ce = c1 < len ? c1 : len;
+                for (int i = c0; i < ce; ++i) {
+                    const float4 q = win[i];
+                    const RowB R = row_b(F, -q.y, -q.z);
+                    float S[7], X[7];
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
+                    bwd_pair<true>(F, R, -q.x, q.w, S, X);
+                    fold_sm(ks, S, X, R.ay, R.az);
+                }
+            }
         }
     }
-    if (f < a.nf) write_face_grad(F, fs, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+    if (f < a.nf) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
 BwdPlan plan_backward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms) {

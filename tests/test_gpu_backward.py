@@ -61,6 +61,25 @@ def test_list_gradient(cuda_device):
     grad_close(G, G_ref, "list", oracle.winding_grad_scale(V, F, Q, g))
 
 
+def test_list_gradient_odd_count_and_queries_on_the_mesh(cuda_device):
+    """Odd query count (the packed pairs are padded), and queries exactly on vertices and on an
+    edge's midpoint: their packed sums are not finite, so their chunks take the guarded path."""
+    V, F = meshgen.jittered_torus(nu=30, nv=15, sigma=0.01, delete_frac=0.1, seed=6)
+    rng = np.random.default_rng(37)
+    on = np.vstack([V[F[3]], V[F[40, :1]], 0.5 * (V[F[7, 0]] + V[F[7, 1]])]).astype(np.float32)
+    Q = np.vstack([rng.uniform(-1, 1, size=(1000, 3)).astype(np.float32), on])
+    Q = Q[rng.permutation(len(Q))]
+    assert len(Q) % 2 == 1
+    d = oracle.point_mesh_distance(V, F, Q)
+    g = _masked_upstream(len(Q), d, seed=9)
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    mesh = make_mesh(V, F, cuda_device)
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device),
+                               queries=to_dev(Q, cuda_device)).cpu().numpy()
+    assert np.all(np.isfinite(G))
+    grad_close(G, G_ref, "list odd/on-mesh", oracle.winding_grad_scale(V, F, Q, g))
+
+
 def test_closed_mesh_gradient_is_cancellation_noise(cuda_device):
     """Closed icosphere: exact dL/dV = 0. Remove one face and the same vertices get O(1) gradients;
     the closed-mesh values must be orders of magnitude below those."""
