@@ -47,3 +47,27 @@ def test_estimate_grows_with_size():
     assert estimate_bytes(1000, 2000, 64, False) > a
     assert estimate_bytes(1000, 20000, 32, False) > a
     assert estimate_bytes(1000, 2000, 32, True) > a
+
+
+def test_laplacian_energy_matches_autograd():
+    """The morphing loop's gather-only Laplacian energy equals mean |L V|^2 of the scatter-add
+    Laplacian, and its backward equals autograd's gradient of that expression (FP64, CPU)."""
+    import torch
+
+    from paper_2407_11272_b300 import meshgen
+    from paper_2407_11272_b300.morph import LaplacianEnergy, laplacian, neighbour_table, uniform_laplacian_edges
+
+    V0, F = meshgen.jittered_torus(nu=12, nv=7, sigma=0.02, delete_frac=0.2, seed=1)
+    V = torch.from_numpy(V0.astype(np.float64))
+    edges, deg = uniform_laplacian_edges(F, len(V0))
+    nbr, w, wt = (torch.from_numpy(a) for a in neighbour_table(F, len(V0)))
+    w, wt = w.double(), wt.double()
+    Va = V.clone().requires_grad_(True)
+    ref = laplacian(Va, torch.from_numpy(edges).long(), torch.from_numpy(deg).double()).pow(2).sum(dim=1).mean()
+    ref.backward()
+    Vb = V.clone().requires_grad_(True)
+    E = LaplacianEnergy.apply(Vb, nbr, w, wt)
+    E.backward()
+    # the table's weights 1/deg are FP32 values: agreement to their rounding
+    assert abs(float(E.detach()) - float(ref.detach())) <= 1e-6 * abs(float(ref.detach()))
+    assert torch.allclose(Vb.grad, Va.grad, rtol=1e-6, atol=1e-9)
