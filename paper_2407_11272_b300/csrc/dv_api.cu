@@ -413,6 +413,9 @@ dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_quer
     if ((st = reserve_queries(m, nq, s))) return st;
     if (part > 0 && (st = grow(m->ws_partial, m->cap_partial, part, s))) return st;
     if (fg > 0 && (st = grow(m->ws_fg, m->cap_fg, fg, s))) return st;
+    if (max_list_queries > 0 &&
+        (st = grow(m->ws_bins, m->cap_bins, dv::near_list_scratch_ints(max_list_queries), s)))
+        return st;
     DV_CUDA(cudaStreamSynchronize(s));
     return DV_OK;
 }
