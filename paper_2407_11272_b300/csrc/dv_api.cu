@@ -250,8 +250,7 @@ dv_status run_forward(dv_mesh *m, const float *queries, int64_t nq, const dv_gri
     if (mixed) {
         dv::GridD gd{};
         if (grid) gd = to_gridd(grid);
-        DV_CUDA(dv::launch_reeval_fp64(m->rec64, m->nf, m->srec64, m->ne, grid ? &gd : nullptr, queries, list, count,
-                                       nq, w, occ,
+        DV_CUDA(dv::launch_reeval_fp64(m->srec64, m->ne, grid ? &gd : nullptr, queries, list, count, nq, w, occ,
                                        (unsigned *)(m->err + 3), m->err + 2, m->num_sms, s));
     }
     if (report) {

@@ -221,12 +221,11 @@ cudaError_t launch_near_surface(const FaceRec *rec, int64_t nf, const GridF *g, 
 int64_t near_list_scratch_ints(int64_t nq);
 
 // winding_fp64.cu
-// FP64 re-evaluation of the flagged queries; over the strip events when srec64 is given
-// (ne > 0), else over the face records.
-cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const StripRec64 *srec64, int64_t ne,
-                               const GridD *g, const float *queries, const int *flag_list, const int *flag_count,
-                               int64_t max_flagged, float *w_out, uint8_t *occ_out, unsigned *stat_maxdiff_bits,
-                               int *stat_occ_changed, int num_sms, cudaStream_t s);
+// FP64 re-evaluation of the flagged queries over the strip events.
+cudaError_t launch_reeval_fp64(const StripRec64 *srec64, int64_t ne, const GridD *g, const float *queries,
+                               const int *flag_list, const int *flag_count, int64_t max_flagged, float *w_out,
+                               uint8_t *occ_out, unsigned *stat_maxdiff_bits, int *stat_occ_changed, int num_sms,
+                               cudaStream_t s);
 
 // dipole.cu (Eq. (4) surrogate)
 int dipole_bwd_splits(int64_t nq, int64_t nf, int num_sms);

@@ -1,8 +1,8 @@
 // FP64 re-evaluation of the flagged queries (|w - 0.5| < 1e-3 or within 1e-3 of a triangle):
 // the full sum of Eq. (5) over every face, each term ATAN2(N, D) of Eq. (7)/(8) in FP64, then
 // w and the occupancy of those queries are overwritten. The flagged list and its length stay on
-// the device; a persistent grid walks the list in batches of QB queries, threads stride over the
-// faces, and each batch is reduced across the CTA in a fixed order (deterministic).
+// the device; a persistent grid walks the list in batches of kRsQB queries, and each batch is
+// reduced across the CTA in a fixed order (deterministic).
 #include <math.h>
 
 #include "dv_internal.cuh"
@@ -10,100 +10,7 @@
 namespace dv {
 
 constexpr int kReThreads = 256;
-constexpr int kReQB = 4;
-
-// ATAN2(N, D) of one face in FP64. Fast path for D > 8|N| (a face seen under less than
-// ~0.25 sr, almost every face): atan(u) = u Q(u^2), u = N/D, Q a degree-6 Remez fit with
-// relative error below 2e-18 (atan_poly.h). Otherwise CUDA's atan2 with Eq. (8)'s conventions.
-__device__ __forceinline__ double half_angle64(const FaceRec64 &r, double qx, double qy, double qz) {
-    const double ax = r.v[0] - qx, ay = r.v[1] - qy, az = r.v[2] - qz;
-    const double bx = r.v[3] - qx, by = r.v[4] - qy, bz = r.v[5] - qz;
-    const double cx = r.v[6] - qx, cy = r.v[7] - qy, cz = r.v[8] - qz;
-    const double la = sqrt(ax * ax + ay * ay + az * az);
-    const double lb = sqrt(bx * bx + by * by + bz * bz);
-    const double lc = sqrt(cx * cx + cy * cy + cz * cz);
-    const double N = ax * r.v[9] + ay * r.v[10] + az * r.v[11];
-    const double D = (la * lb + (ax * bx + ay * by + az * bz)) * lc + la * (bx * cx + by * cy + bz * cz) +
-                     lb * (cx * ax + cy * ay + cz * az);
-    if (D > 8.0 * fabs(N)) {
-        const double u = N / D;
-        const double s = u * u;
-        double P = DV_ATAN64_C6;
-        P = fma(P, s, DV_ATAN64_C5);
-        P = fma(P, s, DV_ATAN64_C4);
-        P = fma(P, s, DV_ATAN64_C3);
-        P = fma(P, s, DV_ATAN64_C2);
-        P = fma(P, s, DV_ATAN64_C1);
-        P = fma(P, s, DV_ATAN64_C0);
-        return u * P;
-    }
-    if (N == 0.0 && D == 0.0) return 0.0;  // ATAN2(0, 0) = 0 (q on a vertex or an edge)
-    return atan2(N + 0.0, D);              // -0 -> +0: the table's case y >= 0
-}
-
-__global__ void __launch_bounds__(kReThreads) reeval_fp64_kernel(const FaceRec64 *__restrict__ rec, int64_t nf,
-                                                                 GridD g, const float *__restrict__ queries,
-                                                                 const int *__restrict__ list,
-                                                                 const int *__restrict__ count, float *w_out,
-                                                                 uint8_t *occ_out, unsigned *maxdiff_bits,
-                                                                 int *occ_changed) {
-    __shared__ double red[kReThreads / 32][kReQB];
-    const int M = *count;
-    const int nb = (M + kReQB - 1) / kReQB;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-        double qx[kReQB], qy[kReQB], qz[kReQB], s[kReQB];
-        int ids[kReQB];
-#pragma unroll
-        for (int j = 0; j < kReQB; ++j) {
-            const int k = b * kReQB + j < M ? b * kReQB + j : M - 1;
-            const int idx = list[k];
-            ids[j] = idx;
-            if (queries) {
-                qx[j] = (double)queries[3 * (int64_t)idx];
-                qy[j] = (double)queries[3 * (int64_t)idx + 1];
-                qz[j] = (double)queries[3 * (int64_t)idx + 2];
-            } else {
-                const int ix = idx % g.n[0], iy = (idx / g.n[0]) % g.n[1], iz = idx / (g.n[0] * g.n[1]);
-                qx[j] = g.lo[0] + ((double)ix + 0.5) * g.h[0];
-                qy[j] = g.lo[1] + ((double)iy + 0.5) * g.h[1];
-                qz[j] = g.lo[2] + ((double)iz + 0.5) * g.h[2];
-            }
-            s[j] = 0.0;
-        }
-        for (int64_t f = threadIdx.x; f < nf; f += kReThreads) {
-            const FaceRec64 r = rec[f];
-#pragma unroll
-            for (int j = 0; j < kReQB; ++j) s[j] += half_angle64(r, qx[j], qy[j], qz[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < kReQB; ++j) {
-            double v = s[j];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-            if (lane == 0) red[warp][j] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < kReQB && b * kReQB + (int)threadIdx.x < M) {
-            const int j = threadIdx.x;
-            double t = 0.0;
-            for (int w = 0; w < kReThreads / 32; ++w) t += red[w][j];
-            const double w64 = t * kInv2PiD;
-            const int idx = ids[j];
-            const float w32 = w_out[idx];
-            const float wn = (float)w64;
-            w_out[idx] = wn;
-            const uint8_t o_new = w64 > 0.5 ? 1 : 0;
-            if (occ_out) occ_out[idx] = o_new;
-            const float diff = fabsf(w32 - wn);
-            atomicMax(maxdiff_bits, __float_as_uint(isfinite(diff) ? diff : 3.0e38f));
-            if ((w32 > 0.5f ? 1 : 0) != o_new) atomicAdd(occ_changed, 1);
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
-// The same re-evaluation over the strip order of the faces (strips.cu): every thread walks a
+// The faces are visited in strip order (strips.cu): every thread walks a
 // contiguous run of events and keeps, per query of the batch, the offset, |P - q| and the dot
 // with the previous vertex of the two most recent vertices; a face then costs one FP64 square
 // root and two dots instead of three of each (D and N as in the FP32 strip kernel). A thread's
@@ -115,8 +22,11 @@ struct Slot64 {
     double ax[kRsQB], ay[kRsQB], az[kRsQB], l[kRsQB], e[kRsQB];
 };
 
-// ATAN2(N, D) of one strip face in FP64 with the fast path of half_angle64; a query on one of
-// the face's vertices (a distance of exactly 0, where N and D vanish) contributes 0.
+// ATAN2(N, D) of one strip face in FP64. Fast path for D > 8|N| (a face seen under less than
+// ~0.25 sr, almost every face): atan(u) = u Q(u^2), u = N/D, Q a degree-6 Remez fit with
+// relative error below 2e-18 (atan_poly.h). Otherwise CUDA's atan2 with Eq. (8)'s conventions
+// (-0 -> +0; ATAN2(0, 0) = 0); a query on one of the face's vertices (a distance of exactly 0,
+// where N and D vanish) contributes 0.
 __device__ __forceinline__ double strip_half_angle64(double N, double D, double lV, double l1, double l2) {
     if (D > 8.0 * fabs(N)) {
         const double u = N / D;
@@ -223,26 +133,19 @@ __global__ void __launch_bounds__(kReThreads, 2)
     }
 }
 
-cudaError_t launch_reeval_fp64(const FaceRec64 *rec64, int64_t nf, const StripRec64 *srec64, int64_t ne,
-                               const GridD *g, const float *queries, const int *flag_list, const int *flag_count,
-                               int64_t max_flagged, float *w_out, uint8_t *occ_out, unsigned *stat_maxdiff_bits,
-                               int *stat_occ_changed, int num_sms, cudaStream_t s) {
+cudaError_t launch_reeval_fp64(const StripRec64 *srec64, int64_t ne, const GridD *g, const float *queries,
+                               const int *flag_list, const int *flag_count, int64_t max_flagged, float *w_out,
+                               uint8_t *occ_out, unsigned *stat_maxdiff_bits, int *stat_occ_changed, int num_sms,
+                               cudaStream_t s) {
+    if (!srec64 || ne < 1) return cudaErrorInvalidValue;
     GridD gd{};
     if (g) gd = *g;
-    const bool strips = srec64 != nullptr && ne > 0;
-    const int qb = strips ? kRsQB : kReQB;
     int64_t blocks = 4LL * num_sms;
-    const int64_t need = (max_flagged + qb - 1) / qb;
+    const int64_t need = (max_flagged + kRsQB - 1) / kRsQB;
     if (need < blocks) blocks = need > 0 ? need : 1;
     prof_begin("reeval_fp64", s);
-    if (strips)
-        reeval_strip_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(srec64, ne, gd, queries, flag_list, flag_count,
-                                                                    w_out, occ_out, stat_maxdiff_bits,
-                                                                    stat_occ_changed);
-    else
-        reeval_fp64_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(rec64, nf, gd, queries, flag_list, flag_count,
-                                                                   w_out, occ_out, stat_maxdiff_bits,
-                                                                   stat_occ_changed);
+    reeval_strip_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(srec64, ne, gd, queries, flag_list, flag_count, w_out,
+                                                                occ_out, stat_maxdiff_bits, stat_occ_changed);
     count_launch();
     prof_end("reeval_fp64", s);
     return cudaGetLastError();

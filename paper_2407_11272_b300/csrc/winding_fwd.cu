@@ -80,18 +80,6 @@ __device__ __forceinline__ PairOut pair_terms(float ax, float bx, float cx, floa
     return o;
 }
 
-// Fast-path arctangent: contributes atan(N/D) when D > |8N|, else 0 (slow path handles it).
-__device__ __forceinline__ float fast_term_fma(const PairOut &o, float acc, bool &ok) {
-    const bool p = o.D > fabsf(o.N8);
-    ok = ok && p;
-    float v = __fmul_rn(o.N8, rcp_approx(o.D));
-    v = p ? v : 0.0f;
-    const float s = __fmul_rn(v, v);
-    float P = __fmaf_rn(DV_ATAN_C2, s, DV_ATAN_C1);
-    P = __fmaf_rn(P, s, DV_ATAN_C0);
-    return __fmaf_rn(v, P, acc);
-}
-
 // Slow-path term for a pair the fast path skipped: ATAN2(N, D) per Eq. (8) (-0 treated as +0,
 // the table's y >= 0 case), and 0 when q coincides with a vertex (ATAN2(0,0)).
 __device__ __forceinline__ float slow_term(const PairOut &o, float la2_min) {
@@ -279,26 +267,6 @@ __device__ __forceinline__ bool face_grid_h(const FaceRec &r, const float (&qx)[
                 }
             }
         }
-    }
-    return ok;
-}
-
-// One face against QL arbitrary queries (list path: no shared parts).
-template <int QL, bool SLOW>
-__device__ __forceinline__ bool face_list(const FaceRec &r, const float (&q)[QL][3], float (&acc)[QL]) {
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < QL; ++j) {
-        const float az = __fsub_rn(r.r0.z, q[j][2]), bz = __fsub_rn(r.r1.z, q[j][2]), cz = __fsub_rn(r.r2.z, q[j][2]);
-        const RowPart p = row_part(r, q[j][1], __fmul_rn(az, az), __fmul_rn(bz, bz), __fmul_rn(cz, cz),
-                                   __fmul_rn(az, bz), __fmul_rn(bz, cz), __fmul_rn(cz, az), __fmul_rn(az, r.r2.w));
-        float m;
-        const PairOut o = pair_terms(__fsub_rn(r.r0.x, q[j][0]), __fsub_rn(r.r1.x, q[j][0]), __fsub_rn(r.r2.x, q[j][0]),
-                                     p.La, p.Lb, p.Lc, p.Pab, p.Pbc, p.Pca, p.Nyz, r.r0.w, m);
-        if (SLOW)
-            acc[j] = __fadd_rn(acc[j], slow_term(o, m));
-        else
-            acc[j] = fast_term_fma(o, acc[j], ok);
     }
     return ok;
 }
@@ -744,67 +712,6 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_grid_strip_kernel(const 
     }
 }
 
-template <int QL, bool KAHAN>
-__global__ void __launch_bounds__(kFwdThreads, 2) fwd_list_kernel(const FwdArgs a) {
-    __shared__ __align__(128) FaceRec sm[kStages][kTileFaces];
-    __shared__ __align__(8) uint64_t full[kStages];
-
-    const int64_t base = (int64_t)blockIdx.x * kFwdThreads * QL + threadIdx.x;
-    float q[QL][3];
-#pragma unroll
-    for (int j = 0; j < QL; ++j) {
-        int64_t idx = base + (int64_t)j * kFwdThreads;
-        if (idx >= a.nq) idx = a.nq - 1;
-        q[j][0] = a.queries[3 * idx];
-        q[j][1] = a.queries[3 * idx + 1];
-        q[j][2] = a.queries[3 * idx + 2];
-    }
-    float acc[QL], ks[QL], kc[QL];
-#pragma unroll
-    for (int j = 0; j < QL; ++j) acc[j] = ks[j] = kc[j] = 0.0f;
-
-    TilePipe<FaceRec> pp;
-    pp.sm = sm;
-    pp.full = full;
-    pp.src = a.rec;
-    pp.f0 = (int64_t)blockIdx.y * a.faces_per_split;
-    const int64_t f1 = pp.f0 + a.faces_per_split < a.nf ? pp.f0 + a.faces_per_split : a.nf;
-    pp.nfaces = f1 - pp.f0;
-    pp.ntiles = (int)((pp.nfaces + kTileFaces - 1) / kTileFaces);
-
-    run_face_tiles(
-        pp, a.err,
-        [&](const FaceRec *tilep, int cnt) {
-#pragma unroll 1
-            for (int k = 0; k < cnt; ++k) {
-                const FaceRec r = tilep[k];
-                const bool ok = face_list<QL, false>(r, q, acc);
-                if (__any_sync(kFull, !ok)) face_list<QL, true>(r, q, acc);
-            }
-        },
-        [&]() {
-            if (KAHAN) {
-#pragma unroll
-                for (int j = 0; j < QL; ++j) {
-                    kahan_add(ks[j], kc[j], acc[j]);
-                    acc[j] = 0.0f;
-                }
-            }
-        });
-
-#pragma unroll
-    for (int j = 0; j < QL; ++j) {
-        const int64_t idx = base + (int64_t)j * kFwdThreads;
-        if (idx >= a.nq) continue;
-        const float s = KAHAN ? ks[j] : acc[j];
-        const float c = KAHAN ? kc[j] : 0.0f;
-        if (a.nsplit > 1)
-            a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(s, -c);
-        else
-            epilogue(a, idx, __fmul_rn(__fsub_rn(s, c), kInv2Pi));
-    }
-}
-
 // ---------------------------------------------------------------------------------------------
 // List forward over the strip order: arbitrary queries, so no (y, z) sharing; each thread
 // holds QP pairs of queries (packed FP32x2) and, per pair and strip slot, the vertex offsets,
@@ -992,7 +899,6 @@ __global__ void split_reduce_kernel(const float2 *__restrict__ partial, int nspl
 // ---------------------------------------------------------------------------------------------
 // Host side.
 constexpr int kGridQX = 4, kGridQY = 2;  // 8 queries per thread on the grid path (3 CTAs per SM)
-constexpr int kListQ = 8;                // 8 queries per thread on the list path
 constexpr int kStripQX = 4, kStripQY = 2;  // 8 queries per thread on the strip grid path
 constexpr int kListQP = 2;                 // 2 packed pairs (4 queries) per thread, strip list path
 
@@ -1008,9 +914,11 @@ FwdPlan plan_forward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_
         tile = kTileEvents;
         per_sm = 4;
     } else {
+        // face order: the grid kernel only (the FP16 ablation and the allocation-free entry);
+        // query lists always run in strip order
         p.threads = kFwdThreads;
-        p.qx = grid ? kGridQX : kListQ;
-        p.qy = grid ? kGridQY : 1;
+        p.qx = kGridQX;
+        p.qy = kGridQY;
     }
     if (grid) {
         const int64_t tiles = (int64_t)((g->n[0] + p.qx - 1) / p.qx) * ((g->n[1] + p.qy - 1) / p.qy) * g->n[2];
@@ -1060,22 +968,17 @@ cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, con
     dim3 grid((unsigned)p.qblocks, (unsigned)p.nsplit);
     const bool kahan = arith != kArithFP32;
     if (arith == kArithFP16 && queries) return cudaErrorNotSupported;
+    if (queries && !p.strips) return cudaErrorInvalidValue;  // lists run in strip order only
     if (p.strips && (arith == kArithFP16 || !srec || ne < 1)) return cudaErrorInvalidValue;
-    const char *name = queries    ? (p.strips ? (kahan ? "fwd_list_strip_kahan" : "fwd_list_strip")
-                                              : (kahan ? "fwd_list_kahan" : "fwd_list"))
+    const char *name = queries    ? (kahan ? "fwd_list_strip_kahan" : "fwd_list_strip")
                        : p.strips ? (kahan ? "fwd_strip_kahan" : "fwd_strip")
                                   : (arith == kArithFP16 ? "fwd_grid_fp16" : (kahan ? "fwd_grid_kahan" : "fwd_grid"));
     prof_begin(name, ctx.stream);
-    if (queries && p.strips) {
+    if (queries) {
         if (kahan)
             fwd_list_strip_kernel<kListQP, true><<<grid, kStripThreads, 0, ctx.stream>>>(a);
         else
             fwd_list_strip_kernel<kListQP, false><<<grid, kStripThreads, 0, ctx.stream>>>(a);
-    } else if (queries) {
-        if (kahan)
-            fwd_list_kernel<kListQ, true><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
-        else
-            fwd_list_kernel<kListQ, false><<<grid, kFwdThreads, 0, ctx.stream>>>(a);
     } else {
         if (p.strips) {
             if (kahan)
