@@ -138,24 +138,26 @@ __device__ __forceinline__ void bwd_pair2(const FaceF2 &F, const RowB2 &R, float
     const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
     const float2 gr = __fmul2_rn(g, r);
     const float2 cD = __fmul2_rn(gr, D), cN = __fmul2_rn(gr, N);
-    const float2 P = __fmul2_rn(cN, la), Qb = __fmul2_rn(cN, lb), Rc = __fmul2_rn(cN, lc);
-    const float2 alA = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lb, lc, bc), ia));
-    const float2 alB = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lc, la, ca), ib));
-    const float2 alC = __fmul2_rn(cN, __fmul2_rn(tc, ic));
+    // the six cN-scaled coefficients (cN |a|, cN |b|, cN |c|, alpha_a, alpha_b, alpha_c) enter
+    // the sums through one FMA each: S += cN * k and X += (cN * ax) * k
+    const float2 kA = __fmul2_rn(__ffma2_rn(lb, lc, bc), ia);
+    const float2 kB = __fmul2_rn(__ffma2_rn(lc, la, ca), ib);
+    const float2 kC = __fmul2_rn(tc, ic);
+    const float2 pa = __fmul2_rn(cN, ax);
     S[0] = __fadd2_rn(S[0], cD);
-    S[1] = __fadd2_rn(S[1], P);
-    S[2] = __fadd2_rn(S[2], Qb);
-    S[3] = __fadd2_rn(S[3], Rc);
-    S[4] = __fadd2_rn(S[4], alA);
-    S[5] = __fadd2_rn(S[5], alB);
-    S[6] = __fadd2_rn(S[6], alC);
+    S[1] = __ffma2_rn(cN, la, S[1]);
+    S[2] = __ffma2_rn(cN, lb, S[2]);
+    S[3] = __ffma2_rn(cN, lc, S[3]);
+    S[4] = __ffma2_rn(cN, kA, S[4]);
+    S[5] = __ffma2_rn(cN, kB, S[5]);
+    S[6] = __ffma2_rn(cN, kC, S[6]);
     X[0] = __ffma2_rn(cD, ax, X[0]);
-    X[1] = __ffma2_rn(P, ax, X[1]);
-    X[2] = __ffma2_rn(Qb, ax, X[2]);
-    X[3] = __ffma2_rn(Rc, ax, X[3]);
-    X[4] = __ffma2_rn(alA, ax, X[4]);
-    X[5] = __ffma2_rn(alB, ax, X[5]);
-    X[6] = __ffma2_rn(alC, ax, X[6]);
+    X[1] = __ffma2_rn(pa, la, X[1]);
+    X[2] = __ffma2_rn(pa, lb, X[2]);
+    X[3] = __ffma2_rn(pa, lc, X[3]);
+    X[4] = __ffma2_rn(pa, kA, X[4]);
+    X[5] = __ffma2_rn(pa, kB, X[5]);
+    X[6] = __ffma2_rn(pa, kC, X[6]);
 }
 
 // Per-face sums, kept in shared memory (touched once per row or chunk of queries, so the
@@ -376,18 +378,19 @@ __device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float
     const float2 den = __ffma2_rn(N, N, __fmul2_rn(D, D));
     const float2 gr = __fmul2_rn(g, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
     const float2 cD = __fmul2_rn(gr, D), cN = __fmul2_rn(gr, N);
-    const float2 P = __fmul2_rn(cN, la), Qb = __fmul2_rn(cN, lb), Rc = __fmul2_rn(cN, lc);
-    const float2 alA = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lb, lc, bcd), ia));
-    const float2 alB = __fmul2_rn(cN, __fmul2_rn(__ffma2_rn(lc, la, ca), ib));
-    const float2 alC = __fmul2_rn(cN, __fmul2_rn(tc, ic));
+    const float2 kA = __fmul2_rn(__ffma2_rn(lb, lc, bcd), ia);
+    const float2 kB = __fmul2_rn(__ffma2_rn(lc, la, ca), ib);
+    const float2 kC = __fmul2_rn(tc, ic);
     T[0] = __fadd2_rn(T[0], cD);
-    T[1] = __fadd2_rn(T[1], P);
-    T[2] = __fadd2_rn(T[2], Qb);
-    T[3] = __fadd2_rn(T[3], Rc);
-    T[4] = __fadd2_rn(T[4], alB);
-    T[5] = __fadd2_rn(T[5], alC);
-    const float2 W[4] = {cD, __fadd2_rn(alA, __fadd2_rn(Rc, Qb)), __fadd2_rn(alB, __fadd2_rn(P, Rc)),
-                         __fadd2_rn(alC, __fadd2_rn(Qb, P))};
+    T[1] = __ffma2_rn(cN, la, T[1]);
+    T[2] = __ffma2_rn(cN, lb, T[2]);
+    T[3] = __ffma2_rn(cN, lc, T[3]);
+    T[4] = __ffma2_rn(cN, kB, T[4]);
+    T[5] = __ffma2_rn(cN, kC, T[5]);
+    // W_a = alpha_a + cN |c| + cN |b| = cN (k_a + |b| + |c|), cyclically
+    const float2 W[4] = {cD, __fmul2_rn(cN, __fadd2_rn(kA, __fadd2_rn(lc, lb))),
+                         __fmul2_rn(cN, __fadd2_rn(kB, __fadd2_rn(la, lc))),
+                         __fmul2_rn(cN, __fadd2_rn(kC, __fadd2_rn(lb, la)))};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         U[i][0] = __ffma2_rn(W[i], ax, U[i][0]);
