@@ -116,11 +116,11 @@ def morph(V0: np.ndarray, F: np.ndarray, target: np.ndarray, grid: dv.Grid, step
     nbr, lw, lwt = (torch.from_numpy(a).to(dev) for a in neighbour_table(F, len(V0)))
     field = WindingNumber(V0d, Fd, grid=grid, kind="exact" if surrogate == "exact" else "dipole",
                           precision="mixed")
-    judge = dv.dv_mesh_create(V0d, Fd)
+    eval_mesh = dv.dv_mesh_create(V0d, Fd)
 
     def exact_iou(V):
-        dv.dv_mesh_update_verts(judge, V.detach().contiguous())
-        _, occ, _ = dv.dv_voxelize_grid(judge, grid, precision="mixed", want_w=False)
+        dv.dv_mesh_update_verts(eval_mesh, V.detach().contiguous())
+        _, occ, _ = dv.dv_voxelize_grid(eval_mesh, grid, precision="mixed", want_w=False)
         return iou(occ, tgt)
 
     def loss_of(V):
