@@ -45,8 +45,8 @@ OPS_BWD = 120
 # SHA-256 of the kernel's source file at capture time: if that file has changed since, the
 # counters no longer describe the kernel and the bench line reports traffic as null.
 TRAFFIC = {
-    ("torus_128", "bwd_grid"): (10280448, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "cfd343b6bb4291dc4e9892644c60f4cefcff06df46f54f0838557b623ac033a0"),
+    ("torus_128", "bwd_grid"): (10702080, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                "1c2ad25bdb2c7630f4ee9aefc9b97499b20b13a6032e1c122457e44ba7b84fa8"),
 }
 
 WORKLOADS = {

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_grid_kernel(const BwdArgs 
 #pragma unroll
                     for (int k = 0; k < 7; ++k) S2[k] = X2[k] = make_float2(0.f, 0.f);
                     const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
-#pragma unroll 2
+#pragma unroll 4
                     for (int p = 0; p < nx / 2; ++p) {
                         const float4 q = wp[p];
                         bwd_pair2(F2, R2, make_float2(q.x, q.y), make_float2(q.z, q.w), S2, X2);
