@@ -317,6 +317,7 @@ def run_native(args):
     times_ms = [a.elapsed_time(b) for a, b in evs]
     prof = dv.dv_profile_read()
     total_ms, value = aggregate_ranks(float(sum(times_ms)), pairs, args.steps, ws, dev)
+    bnd = _boundary_adjoint(mesh, g, grid, dV, prof, stream, dev)
 
     # roofline of the dominant kernel: algorithmic FP32 lane operations per launch / measured duration
     peaks, peak_src = _peaks()
@@ -353,6 +354,7 @@ def run_native(args):
                        "fp64_reevaluated_queries": rep["n_flagged"]},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
+            "adjoint_boundary": bnd,
             "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"],
                        "samples": ck["samples"]},
         }
@@ -364,6 +366,35 @@ def run_native(args):
         dist.destroy_process_group()
     mesh.close()
     return 0
+
+
+def _boundary_adjoint(mesh, g, grid, dV_faces, prof, stream, dev):
+    """Outside the timed step: the boundary form of the adjoint (dv_winding_backward_boundary) on
+    the same upstream, its time per call and its difference from the face-by-face result."""
+    import torch
+
+    from paper_2407_11272_b300 import dv
+
+    out = torch.empty_like(dV_faces)
+    dv.dv_winding_backward_boundary(mesh, g, grid=grid, out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    reps = 3
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        dv.dv_winding_backward_boundary(mesh, g, grid=grid, out=out, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / reps
+    ref = dV_faces.double()
+    rel = float(torch.linalg.norm(out.double() - ref) / torch.linalg.norm(ref).clamp_min(1e-300))
+    face_ms = prof["bwd_grid"][0] / max(prof["bwd_grid"][1], 1) if "bwd_grid" in prof else None
+    nb = dv.dv_mesh_num_boundary_edges(mesh)
+    note = "same dL/dV from the boundary edges; not part of the timed step"
+    if nb == 0:
+        note += "; closed mesh: the exact gradient is 0 and the face adjoint's value is cancellation noise"
+    return {"ms_per_call": ms, "face_adjoint_ms": face_ms, "boundary_edges": nb, "rel_diff_vs_face_adjoint": rel,
+            "face_adjoint_norm": float(torch.linalg.norm(ref)), "note": note}
 
 
 def _e2e(args, V, F, grid, dev):

@@ -141,9 +141,12 @@ dv_status dv_mesh_update_verts(dv_mesh *mesh, const float *d_verts, void *stream
  * and synchronizes that stream. */
 dv_status dv_mesh_reserve(dv_mesh *mesh, const dv_grid *grid, int64_t max_list_queries);
 
-/* Number of vertices / faces of a mesh (-1 if mesh is NULL). */
+/* Number of vertices / faces / boundary edges (directed edges with nonzero net
+ * multiplicity over the faces; 0 for a closed, consistently oriented mesh) of a
+ * mesh (-1 if mesh is NULL). */
 int64_t dv_mesh_num_verts(const dv_mesh *mesh);
 int64_t dv_mesh_num_faces(const dv_mesh *mesh);
+int64_t dv_mesh_num_boundary_edges(const dv_mesh *mesh);
 
 /* Synchronize `stream` and report (then clear) the sticky device error word
  * of the mesh: DV_ERR_TIMEOUT if a kernel's bounded wait ran out. */
@@ -177,6 +180,23 @@ dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_ou
  * (no floating-point atomics). Stream-ordered, no sync. */
 dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                               const float *d_upstream, float *d_dverts, void *stream);
+
+/* The same adjoint as dv_winding_backward (same arguments, same result up to
+ * FP32 rounding, for queries off the mesh), computed from the mesh's boundary
+ * curve: the solid angle of a surface depends only on its boundary, so summed
+ * over the faces the derivative of Eq. (7) cancels on every edge shared by two
+ * consistently oriented faces. What remains is, per directed edge p -> r with
+ * net multiplicity m and a = p - q, b = r - q,
+ *     dOmega/dp = m (b x a) / (|a| (|a||b| + a.b)),
+ *     dOmega/dr = m (b x a) / (|b| (|a||b| + a.b)),
+ * one evaluation per (boundary edge, query) instead of per (face, query). The
+ * gradient is exactly 0 for a closed mesh and off the boundary vertices. A
+ * query on a boundary edge (|a||b| + a.b = 0) contributes nothing. No
+ * counterpart in the paper: an evaluation of the same derivative. FP32 pair
+ * arithmetic, FP64 vertex gather in a fixed order (deterministic).
+ * Stream-ordered, no sync. */
+dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                                       const float *d_upstream, float *d_dverts, void *stream);
 
 /* No counterpart in the paper: a service of this library.
  * Winding numbers of the voxel centres of *grid (as dv_winding with

@@ -16,7 +16,7 @@ from . import dv
 
 class _WindingFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, verts, mesh, grid, queries, precision, kind):
+    def forward(ctx, verts, mesh, grid, queries, precision, kind, adjoint):
         v = verts.detach().contiguous()
         dv.dv_mesh_update_verts(mesh, v)
         if kind == "exact":
@@ -25,7 +25,7 @@ class _WindingFn(torch.autograd.Function):
             w = dv.dv_dipole_winding(mesh, queries=queries, grid=grid)
         else:
             raise ValueError(f"unknown kind {kind!r}")
-        ctx.mesh, ctx.grid, ctx.queries, ctx.kind = mesh, grid, queries, kind
+        ctx.mesh, ctx.grid, ctx.queries, ctx.kind, ctx.adjoint = mesh, grid, queries, kind, adjoint
         ctx.save_for_backward(v)
         return w
 
@@ -35,19 +35,24 @@ class _WindingFn(torch.autograd.Function):
         # re-pack from the vertices of this forward (another forward may have moved the mesh since)
         dv.dv_mesh_update_verts(ctx.mesh, v)
         g = grad_w.detach().to(torch.float32).contiguous()
-        fn = dv.dv_winding_backward if ctx.kind == "exact" else dv.dv_dipole_backward
+        if ctx.kind == "dipole":
+            fn = dv.dv_dipole_backward
+        else:
+            fn = dv.dv_winding_backward_boundary if ctx.adjoint == "boundary" else dv.dv_winding_backward
         dV = fn(ctx.mesh, g, queries=ctx.queries, grid=ctx.grid)
-        return dV, None, None, None, None, None
+        return dV, None, None, None, None, None, None
 
 
 class WindingNumber(torch.nn.Module):
     """Differentiable w(q) of a mesh with fixed faces over a grid or a fixed query list.
 
     verts [nv,3] float32 CUDA tensor -> w [nq] float32. ``kind`` is "exact" (Eq. (5)/(7), with
-    ``precision`` "fp32" | "kahan" | "mixed") or "dipole" (Eq. (4))."""
+    ``precision`` "fp32" | "kahan" | "mixed") or "dipole" (Eq. (4)). For "exact", ``adjoint``
+    selects the face-by-face derivative ("faces") or the same derivative from the mesh's boundary
+    edges ("boundary", dv_winding_backward_boundary)."""
 
     def __init__(self, verts, faces, grid: dv.Grid | None = None, queries=None, precision: str = "mixed",
-                 kind: str = "exact"):
+                 kind: str = "exact", adjoint: str = "faces"):
         super().__init__()
         self.mesh = dv.dv_mesh_create(verts.detach().contiguous(), faces.contiguous())
         if grid is not None:
@@ -56,9 +61,12 @@ class WindingNumber(torch.nn.Module):
         self.queries = queries
         self.precision = precision
         self.kind = kind
+        if adjoint not in ("faces", "boundary"):
+            raise ValueError(f"unknown adjoint {adjoint!r}")
+        self.adjoint = adjoint
 
     def forward(self, verts):
-        return _WindingFn.apply(verts, self.mesh, self.grid, self.queries, self.precision, self.kind)
+        return _WindingFn.apply(verts, self.mesh, self.grid, self.queries, self.precision, self.kind, self.adjoint)
 
 
 def winding_number(verts, module: WindingNumber):

@@ -100,6 +100,11 @@ struct dv_mesh {
     int32_t *ev_face = nullptr;           // [ne], -1 for a strip's first two events
     dv::StripRec *srec = nullptr;         // [ne]
     dv::StripRec64 *srec64 = nullptr;     // [ne]
+    int64_t nb = 0;                       // boundary edges (net multiplicity != 0)
+    int32_t *bnd_edges = nullptr;         // [nb][3]: u, v, m
+    dv::BndRec *bnd_rec = nullptr;        // [nb]
+    int32_t *bnd_vptr = nullptr;          // [nv + 1]
+    int32_t *bnd_vend = nullptr;          // [2 nb]
     int *err = nullptr;             // sticky error word + small counters: [0]=err [1]=flag_count [2]=occ_changed [3]=maxdiff bits
     // scratch, grown on demand
     int64_t cap_q = 0;
@@ -112,6 +117,8 @@ struct dv_mesh {
     float *ws_fg = nullptr;
     int64_t cap_bins = 0;     // ints: query bins of the list path's near-surface selection
     int *ws_bins = nullptr;
+    int64_t cap_bpart = 0;    // floats: per-split boundary-edge sums
+    float *ws_bpart = nullptr;
 };
 
 namespace {
@@ -295,7 +302,7 @@ void dv_mesh_destroy(dv_mesh *m) {
     DeviceGuard dg(m->device);
     void *bufs[] = {m->faces,   m->rec,     m->rec64, m->vtx_ptr, m->vtx_corner, m->ev_vert,    m->ev_face,
                     m->srec,    m->srec64,  m->err,   m->ws_w,    m->ws_near,    m->ws_list,    m->ws_partial,
-                    m->ws_fg,   m->ws_bins};
+                    m->ws_fg,   m->ws_bins, m->bnd_edges, m->bnd_rec, m->bnd_vptr, m->bnd_vend, m->ws_bpart};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, m->last_stream);
     delete m;
@@ -356,6 +363,23 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
     if (!e) e = cudaMallocAsync((void **)&m->srec, (size_t)m->ne * sizeof(dv::StripRec), s);
     if (!e) e = cudaMallocAsync((void **)&m->srec64, (size_t)m->ne * sizeof(dv::StripRec64), s);
     if (e) return bail(fail(DV_ERR_OOM, "strip storage: %s", cudaGetErrorString(e)));
+    // boundary edges for the boundary form of the adjoint
+    std::vector<int32_t> b_edges, b_vptr, b_vend;
+    dv::build_boundary(hf.data(), nf, nv, b_edges, b_vptr, b_vend);
+    m->nb = (int64_t)b_edges.size() / 3;
+    e = cudaMallocAsync((void **)&m->bnd_vptr, b_vptr.size() * sizeof(int32_t), s);
+    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_edges, b_edges.size() * sizeof(int32_t), s);
+    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_rec, (size_t)m->nb * sizeof(dv::BndRec), s);
+    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_vend, b_vend.size() * sizeof(int32_t), s);
+    if (e) return bail(fail(DV_ERR_OOM, "boundary storage: %s", cudaGetErrorString(e)));
+    if ((e = cudaMemcpyAsync(m->bnd_vptr, b_vptr.data(), b_vptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                             s)) ||
+        (m->nb > 0 && (e = cudaMemcpyAsync(m->bnd_edges, b_edges.data(), b_edges.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s))) ||
+        (m->nb > 0 && (e = cudaMemcpyAsync(m->bnd_vend, b_vend.data(), b_vend.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s))) ||
+        (e = dv::launch_pack_boundary(d_verts, m->bnd_edges, m->nb, m->bnd_rec, s)))
+        return bail(fail(DV_ERR_CUDA, "boundary upload: %s", cudaGetErrorString(e)));
     if ((e = cudaMemcpyAsync(m->vtx_ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(m->vtx_corner, corner.data(), corner.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                              s)) ||
@@ -381,6 +405,7 @@ dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
     DV_CUDA(dv::launch_pack(d_verts, m->faces, m->nf, m->rec, m->rec64, (cudaStream_t)stream));
     DV_CUDA(dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64,
                                    (cudaStream_t)stream));
+    DV_CUDA(dv::launch_pack_boundary(d_verts, m->bnd_edges, m->nb, m->bnd_rec, (cudaStream_t)stream));
     return DV_OK;
 }
 
@@ -479,6 +504,29 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
                                      s));
     return DV_OK;
 }
+
+dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
+                                       const float *d_upstream, float *d_dverts, void *stream) {
+    int64_t n = 0;
+    dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
+    if (st) return st;
+    if (!d_upstream || !d_dverts) return fail(DV_ERR_INVALID_ARG, "d_upstream or d_dverts is NULL");
+    dv_mesh *m = const_cast<dv_mesh *>(mesh);
+    DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    dv::GridF gf{};
+    if (grid) gf = to_gridf(grid);
+    const dv::BndPlan plan = dv::plan_boundary(n, m->nb, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
+    m->last_stream = s;
+    if (m->nb > 0 && (st = grow(m->ws_bpart, m->cap_bpart, (int64_t)plan.nsplit * m->nb * 8, s))) return st;
+    DV_CUDA(dv::launch_boundary_backward(plan, m->bnd_rec, m->nb, grid ? &gf : nullptr, d_queries, n, d_upstream,
+                                         m->ws_bpart, s));
+    DV_CUDA(dv::launch_boundary_gather(m->nv, m->bnd_rec, m->nb, m->ws_bpart, plan.nsplit, m->bnd_vptr, m->bnd_vend,
+                                       d_dverts, s));
+    return DV_OK;
+}
+
+int64_t dv_mesh_num_boundary_edges(const dv_mesh *mesh) { return mesh ? mesh->nb : -1; }
 
 // ------------------------------------------------------------------------------------------
 // Batches of independent requests as one CUDA graph (request server).

@@ -51,6 +51,13 @@ struct StripRec64 {
     double pad;
 };
 
+// One directed boundary edge p -> r of the mesh (net multiplicity m != 0 over all faces), for the
+// boundary form of the adjoint (winding_bnd.cu). 32 bytes.
+struct BndRec {
+    float4 p;  // start vertex, m (as float)
+    float4 r;  // end vertex, 0
+};
+
 // Cell-centred grid, FP32 form used by the FP32 kernels: x = lo + (i + 0.5) * h.
 struct GridF {
     float lo[3];
@@ -181,6 +188,26 @@ cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, Fa
 cudaError_t launch_pack_strips(const float *verts, const int32_t *ev_vert, const int32_t *ev_face, int64_t ne,
                                const FaceRec *rec, const FaceRec64 *rec64, StripRec *srec, StripRec64 *srec64,
                                cudaStream_t s);
+
+// winding_bnd.cu: the adjoint from the mesh's boundary edges.
+struct BndPlan {
+    int64_t eblocks;    // CTAs over boundary edges
+    int nsplit;         // query (row) splits (grid dimension y)
+    int64_t per_split;  // grid: rows per split; list: queries per split
+};
+BndPlan plan_boundary(int64_t nq, int64_t nb, bool grid, const GridF *g, int num_sms);
+cudaError_t launch_pack_boundary(const float *verts, const int32_t *edges, int64_t nb, BndRec *rec, cudaStream_t s);
+// Per-split edge sums into part [nsplit][nb][8]; nothing to do when nb == 0.
+cudaError_t launch_boundary_backward(const BndPlan &p, const BndRec *rec, int64_t nb, const GridF *g,
+                                     const float *queries, int64_t nq, const float *upstream, float *part,
+                                     cudaStream_t s);
+// dverts [nv][3] (overwritten; 0 off the boundary) from the split sums, FP64, fixed order.
+cudaError_t launch_boundary_gather(int64_t nv, const BndRec *rec, int64_t nb, const float *part, int nsplit,
+                                   const int32_t *vptr, const int32_t *vend, float *dverts, cudaStream_t s);
+// Directed edges with nonzero net multiplicity as (u, v, m) triples, and per vertex the list of
+// (edge << 1 | endpoint) codes in edge order (CSR: vptr [nv + 1], vend [2 nb]); host.
+void build_boundary(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int32_t> &edges,
+                    std::vector<int32_t> &vptr, std::vector<int32_t> &vend);
 
 // strips.cu: vertex-sharing strip order of the faces (host, once per mesh).
 void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int32_t> &ev_vert,

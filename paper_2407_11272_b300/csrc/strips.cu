@@ -1,4 +1,7 @@
-// Vertex-sharing triangle strips of a mesh (host code, run once per mesh at creation).
+// Mesh topology on the host, once per mesh at creation: the vertex-sharing strip order of the
+// faces (below) and the boundary edges used by the boundary form of the adjoint (build_boundary).
+//
+// Vertex-sharing triangle strips.
 //
 // The forward pass evaluates ATAN2(N, D) of Eq. (7) for every (query, face) pair; |a|, |b|, |c|
 // (one square root each) and the dots a.b, b.c, c.a depend on a vertex or an edge only. When the
@@ -149,6 +152,46 @@ void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int3
                 const int32_t h = nb[(size_t)g * 3 + k];
                 if (h >= 0 && !used[h]) bucket[--deg[h]].push_back(h);
             }
+    }
+}
+
+void build_boundary(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int32_t> &edges,
+                    std::vector<int32_t> &vptr, std::vector<int32_t> &vend) {
+    // net multiplicity of every undirected edge {u < v}: +1 per face traversing u -> v, -1 per v -> u
+    std::vector<std::pair<uint64_t, int32_t>> he;
+    he.reserve((size_t)nf * 3);
+    for (int64_t f = 0; f < nf; ++f)
+        for (int k = 0; k < 3; ++k) {
+            const int32_t u = faces[3 * f + k], v = faces[3 * f + (k + 1) % 3];
+            if (u == v) continue;  // a zero-length edge of a degenerate face contributes nothing
+            const uint64_t lo = (uint32_t)(u < v ? u : v), hi = (uint32_t)(u < v ? v : u);
+            he.push_back({lo * (uint64_t)nv + hi, u < v ? 1 : -1});
+        }
+    std::sort(he.begin(), he.end());
+    edges.clear();
+    for (size_t i = 0; i < he.size();) {
+        size_t j = i;
+        int32_t m = 0;
+        while (j < he.size() && he[j].first == he[i].first) m += he[j++].second;
+        if (m != 0) {
+            edges.push_back((int32_t)(he[i].first / (uint64_t)nv));
+            edges.push_back((int32_t)(he[i].first % (uint64_t)nv));
+            edges.push_back(m);
+        }
+        i = j;
+    }
+    const int64_t nb = (int64_t)edges.size() / 3;
+    vptr.assign((size_t)nv + 1, 0);
+    for (int64_t e = 0; e < nb; ++e) {
+        vptr[(size_t)edges[3 * e] + 1]++;
+        vptr[(size_t)edges[3 * e + 1] + 1]++;
+    }
+    for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+    vend.assign((size_t)nb * 2, 0);
+    std::vector<int32_t> fill(vptr.begin(), vptr.end() - 1);
+    for (int64_t e = 0; e < nb; ++e) {
+        vend[(size_t)fill[edges[3 * e]]++] = (int32_t)(2 * e);
+        vend[(size_t)fill[edges[3 * e + 1]]++] = (int32_t)(2 * e + 1);
     }
 }
 

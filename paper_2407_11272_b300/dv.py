@@ -16,6 +16,7 @@ from . import build as _build
 __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
+    "dv_winding_backward_boundary", "dv_mesh_num_boundary_edges",
     "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
@@ -108,6 +109,10 @@ def load():
     lib.dv_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, ctypes.c_int, _P]
     lib.dv_voxelize_grid.argtypes = [_P, ctypes.POINTER(_Grid), _P, _P, ctypes.c_int, ctypes.POINTER(_Report), _P]
     lib.dv_winding_backward.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P, _P]
+    lib.dv_winding_backward_boundary.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P, _P]
+    lib.dv_winding_backward_boundary.restype = ctypes.c_int
+    lib.dv_mesh_num_boundary_edges.argtypes = [_P]
+    lib.dv_mesh_num_boundary_edges.restype = _I64
     lib.dv_run_batch.argtypes = [ctypes.POINTER(_Request), ctypes.c_int, ctypes.c_int, _P]
     lib.dv_run_batch.restype = ctypes.c_int
     lib.dv_dipole_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P]
@@ -295,6 +300,28 @@ def dv_winding_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = 
                                       ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                       _stream(stream)), "dv_winding_backward")
     return out
+
+
+def dv_winding_backward_boundary(mesh: Mesh, upstream, queries=None, grid: Grid | None = None, out=None,
+                                 stream=None):
+    """The same dL/dV as ``dv_winding_backward``, evaluated from the mesh's boundary edges."""
+    import torch
+
+    qp, nq_arg, g, nq, _ = _queries_or_grid(queries, grid)
+    up = _tensor(upstream, torch.float32, None, "upstream")
+    if up.numel() != nq:
+        raise ValueError("upstream must have one value per query")
+    if out is None:
+        out = torch.empty((mesh.num_verts, 3), dtype=torch.float32, device=mesh.device)
+    out = _tensor(out, torch.float32, (3,), "out")
+    _check(load().dv_winding_backward_boundary(mesh.handle, qp, nq_arg, ctypes.byref(g) if g is not None else None,
+                                               ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                               _stream(stream)), "dv_winding_backward_boundary")
+    return out
+
+
+def dv_mesh_num_boundary_edges(mesh: Mesh) -> int:
+    return int(load().dv_mesh_num_boundary_edges(mesh.handle))
 
 
 def dv_run_batch(requests, precision: str = "mixed", stream=None) -> None:
