@@ -160,25 +160,28 @@ class ClockSampler:
 
 
 def _cpu_baseline(V, F, grid_n, budget_s=12.0, seed=4):
-    """The FP64 oracle as it stands, on this host's cores: forward + gradient on a seeded query sample."""
+    """The FP64 oracle as it stands, on this host's cores: forward + gradient on a seeded query
+    sample sized (from two calibration runs) to about budget_s seconds."""
     import oracle
     from paper_2407_11272_b300 import meshgen
 
-    Q = oracle.grid_queries([-1.0] * 3, [1.0] * 3, [grid_n] * 3)
-    g = meshgen.upstream_gradient(len(Q), seed=1).astype(np.float64)
-    probe = meshgen.query_subsample(len(Q), 512, seed=seed)
-    t0 = time.perf_counter()
-    oracle.winding(V, F, Q[probe])
-    oracle.winding_grad(V, F, Q[probe], g[probe])
-    t_probe = max(time.perf_counter() - t0, 1e-3)
-    n = int(np.clip(512 * budget_s / t_probe, 512, len(Q)))
-    idx = meshgen.query_subsample(len(Q), n, seed=seed)
-    t0 = time.perf_counter()
-    oracle.winding(V, F, Q[idx])
-    oracle.winding_grad(V, F, Q[idx], g[idx])
-    dt = time.perf_counter() - t0
+    nq = grid_n ** 3
+    g = meshgen.upstream_gradient(nq, seed=1).astype(np.float64)
+
+    def run(idx):
+        Q = oracle.grid_points([-1.0] * 3, [1.0] * 3, [grid_n] * 3, idx)
+        t0 = time.perf_counter()
+        oracle.winding(V, F, Q)
+        oracle.winding_grad(V, F, Q, g[idx])
+        return max(time.perf_counter() - t0, 1e-4)
+
+    per_q = run(meshgen.query_subsample(nq, 512, seed=seed + 1)) / 512
+    n2 = int(np.clip(1.5 / per_q, 512, nq))
+    per_q = run(meshgen.query_subsample(nq, n2, seed=seed + 2)) / n2
+    n = int(np.clip(budget_s / per_q, 512, nq))
+    dt = run(meshgen.query_subsample(nq, n, seed=seed))
     return {"value": n * len(F) / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{n} seeded grid queries (of {len(Q)}) x all {len(F)} faces, FP64 forward + gradient, "
+            "sample": f"{n} seeded grid queries (of {nq}) x all {len(F)} faces, FP64 forward + gradient, "
                       f"{dt:.1f} s"}
 
 
@@ -206,21 +209,26 @@ def run_reference(args):
     import oracle
     from paper_2407_11272_b300 import meshgen
 
-    Q = oracle.grid_queries([-1.0] * 3, [1.0] * 3, [n] * 3)
-    g = meshgen.upstream_gradient(len(Q), seed=1).astype(np.float64)
+    nq = n ** 3
+    g = meshgen.upstream_gradient(nq, seed=1).astype(np.float64)
+
+    def cells(idx):  # voxel centres of the sampled cells only (the full grid may not fit)
+        return oracle.grid_points([-1.0] * 3, [1.0] * 3, [n] * 3, idx)
+
     # size each step to a few seconds of CPU work
-    probe = meshgen.query_subsample(len(Q), 512, seed=6)
+    probe = meshgen.query_subsample(nq, 512, seed=6)
     t0 = time.perf_counter()
-    oracle.winding(V, F, Q[probe])
-    oracle.winding_grad(V, F, Q[probe], g[probe])
+    oracle.winding(V, F, cells(probe))
+    oracle.winding_grad(V, F, cells(probe), g[probe])
     per_q = max(time.perf_counter() - t0, 1e-4) / 512
-    nsamp = int(np.clip(4.0 / per_q, 32, len(Q)))
+    nsamp = int(np.clip(4.0 / per_q, 32, nq))
     times = []
     for step in range(args.warmup + args.steps):
-        idx = meshgen.query_subsample(len(Q), nsamp, seed=100 + step)
+        idx = meshgen.query_subsample(nq, nsamp, seed=100 + step)
+        Qs = cells(idx)
         t0 = time.perf_counter()
-        oracle.winding(V, F, Q[idx])
-        oracle.winding_grad(V, F, Q[idx], g[idx])
+        oracle.winding(V, F, Qs)
+        oracle.winding_grad(V, F, Qs, g[idx])
         if step >= args.warmup:
             times.append(time.perf_counter() - t0)
     total = sum(times)
