@@ -96,6 +96,14 @@ typedef struct {
 /* Version of this ABI (DV_ABI_VERSION). */
 int dv_abi_version(void);
 
+/* Self-test of the bounded waits used by every shared-memory copy pipeline of
+ * this library (no counterpart in the paper). One CTA waits on a barrier phase
+ * with a limit of limit_us microseconds (1 .. 1e7). With arrive != 0 the phase
+ * completes and the call returns DV_OK; with arrive == 0 nothing arrives, the
+ * wait gives up after the limit, the kernel records and returns
+ * DV_ERR_TIMEOUT, and the CUDA context stays usable. Synchronizes `stream`. */
+dv_status dv_selftest_bounded_wait(int64_t limit_us, int arrive, void *stream);
+
 /* Strip order of a mesh's faces, the visiting order of the forward passes
  * (the sum of Eq. (5) is order-free; this order lets consecutive faces share
  * the per-vertex |v - q| and per-edge dot terms of Eq. (7)). HOST function, no

@@ -17,7 +17,7 @@ __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
     "dv_winding_backward_boundary", "dv_mesh_num_boundary_edges",
-    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_selftest_bounded_wait", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2, "fp16": 3}
@@ -121,6 +121,8 @@ def load():
     lib.dv_dipole_backward.restype = ctypes.c_int
     lib.dv_flipped_duplication.argtypes = [_P, _P, ctypes.c_float, _P, _P, _P]
     lib.dv_flipped_duplication.restype = ctypes.c_int
+    lib.dv_selftest_bounded_wait.argtypes = [_I64, ctypes.c_int, _P]
+    lib.dv_selftest_bounded_wait.restype = ctypes.c_int
     lib.dv_build_strips.argtypes = [_P, _I64, _I64, _P, _P, _I64, ctypes.POINTER(_I64)]
     lib.dv_build_strips.restype = ctypes.c_int
     lib.dv_profile_enable.argtypes = [ctypes.c_int]
@@ -380,6 +382,11 @@ def dv_dipole_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = N
                                      ctypes.c_void_p(up.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                      _stream(stream)), "dv_dipole_backward")
     return out
+
+
+def dv_selftest_bounded_wait(limit_us: int, arrive: bool, stream=None) -> int:
+    """Status code of one bounded wait on the GPU (0 = DV_OK, 5 = DV_ERR_TIMEOUT); no exception."""
+    return int(load().dv_selftest_bounded_wait(int(limit_us), 1 if arrive else 0, _stream(stream)))
 
 
 def dv_build_strips(faces, nv: int):
