@@ -8,21 +8,28 @@
 // and w = sum / (2 pi)  (Eq. (5)).
 //
 // Design for sm_103a:
-//   * Face records (48 B) stream through shared memory in tiles moved by 1-D TMA bulk copies
-//     (cp.async.bulk + mbarrier), 4-stage ring; every warp reads each face as a broadcast.
+//   * Main path (grid and list queries, FP32 / Kahan): the faces are visited in the
+//     vertex-sharing strip order of strips.cu. Strip events (32 B: vertex + face normal) stream
+//     through shared memory in tiles of 96 moved by 1-D TMA bulk copies (cp.async.bulk +
+//     mbarrier, 4-stage ring, bounded waits); every warp reads each event as a broadcast. Each
+//     event brings one vertex: |v - q| (one MUFU square root) and the dot with the previous
+//     vertex are computed once and kept in three rotating register slots, so a face costs one
+//     square root, two dots and D = (|V||P1| + V.P1)|P2| + |V|(P1.P2) + |P1|(V.P2).
 //   * Voxel-centre queries are generated in registers from the grid index; each thread owns
-//     QX consecutive x positions on QY consecutive rows at one z. Parts of a, b, c, |.|^2, dots
-//     and N that depend on z only, or on (y, z) only, are computed once per face per thread and
-//     reused across the thread's queries, so the per-query cost is ~18 FP32 ops + 4 MUFU
-//     (|a|, |b|, |c| by MUFU square root, D = (|a||b| + a.b)|c| + |a|(b.c) + |b|(c.a)).
-//   * ATAN2 fast path: with the record's normal pre-scaled by 8, the test D > |8N| selects
-//     |N/D| < 1/8, where atan(N/D) = v P(v^2), v = 8N/D, P a degree-2 Remez polynomial
-//     (atan_poly.h). Terms failing the test contribute 0 on the fast path; if any lane of the
-//     warp has such a term for the current face, a slow path adds ATAN2 via atan2f for exactly
-//     those terms (re-computed bit-identically: every operation is an explicit _rn intrinsic).
-//   * Compensated summation: plain FP32 over a tile of 64 faces, Kahan across tiles.
-//   * Split over faces (grid.y) for small query counts; partial sums (sum, -compensation) go
-//     to a scratch buffer and are reduced in FP64, in fixed order, by split_reduce_kernel.
+//     QX consecutive x positions (paired into packed FP32x2 instructions) on QY rows at one z;
+//     the (y, z) parts of offsets, lengths, dots and N are computed once per event per row.
+//   * ATAN2 fast path: with the normal pre-scaled by 8, the test D > |8N| selects |N/D| < 1/8,
+//     where atan(N/D) = v P(v^2), v = 8N/D, P a degree-2 Remez polynomial (atan_poly.h). Terms
+//     failing the test contribute 0 on the fast path; if any lane of the warp has such a term
+//     for the current face, a slow path recomputes N and D with the same operations and adds
+//     ATAN2 via atan2f for exactly those terms.
+//   * Compensated summation: plain FP32 within a tile, Kahan across tiles (state in shared
+//     memory).
+//   * Split over the event range (grid.y) for small query counts, each split starting with two
+//     warm-up events; partial sums (sum, -compensation) go to a scratch buffer and are reduced
+//     in FP64, in fixed order, by split_reduce_kernel.
+//   * Face order (48 B face records, tiles of 64) remains for the FP16 ablation and the
+//     allocation-free entry point (noalloc.cu), which build no strip order.
 #include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
