@@ -10,7 +10,9 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dv_api.h"
@@ -348,24 +350,33 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
         return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
     if (bad == 1) return bail(fail(DV_ERR_INVALID_MESH, "a face index is outside [0, %lld)", (long long)nv));
     if (bad == 2) return bail(fail(DV_ERR_INVALID_MESH, "a vertex coordinate is not finite"));
-    // vertex -> (face, corner) adjacency, CSR, in face order (deterministic gather)
+    // Host topology, independent parts on two threads: the strip order of the faces (forward
+    // passes) on a worker; the vertex -> (face, corner) CSR (deterministic gather) and the
+    // boundary edges (boundary form of the adjoint) here.
+    std::vector<int32_t> ev_vert, ev_face;
+    bool strip_oom = false;
+    std::thread strip_worker([&] {
+        try {
+            dv::build_strips(hf.data(), nf, nv, ev_vert, ev_face);
+        } catch (const std::bad_alloc &) {
+            strip_oom = true;
+        }
+    });
     std::vector<int32_t> ptr((size_t)nv + 1, 0), corner((size_t)nf * 3);
     for (int64_t i = 0; i < 3 * nf; ++i) ptr[(size_t)hf[i] + 1]++;
     for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
     std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
     for (int64_t i = 0; i < 3 * nf; ++i) corner[(size_t)fill[hf[i]]++] = (int32_t)i;
-    // vertex-sharing strip order of the faces for the forward passes
-    std::vector<int32_t> ev_vert, ev_face;
-    dv::build_strips(hf.data(), nf, nv, ev_vert, ev_face);
+    std::vector<int32_t> b_edges, b_vptr, b_vend;
+    dv::build_boundary(hf.data(), nf, nv, b_edges, b_vptr, b_vend);
+    strip_worker.join();
+    if (strip_oom) return bail(fail(DV_ERR_OOM, "host memory for the strip order"));
     m->ne = (int64_t)ev_vert.size();
     e = cudaMallocAsync((void **)&m->ev_vert, (size_t)m->ne * sizeof(int32_t), s);
     if (!e) e = cudaMallocAsync((void **)&m->ev_face, (size_t)m->ne * sizeof(int32_t), s);
     if (!e) e = cudaMallocAsync((void **)&m->srec, (size_t)m->ne * sizeof(dv::StripRec), s);
     if (!e) e = cudaMallocAsync((void **)&m->srec64, (size_t)m->ne * sizeof(dv::StripRec64), s);
     if (e) return bail(fail(DV_ERR_OOM, "strip storage: %s", cudaGetErrorString(e)));
-    // boundary edges for the boundary form of the adjoint
-    std::vector<int32_t> b_edges, b_vptr, b_vend;
-    dv::build_boundary(hf.data(), nf, nv, b_edges, b_vptr, b_vend);
     m->nb = (int64_t)b_edges.size() / 3;
     e = cudaMallocAsync((void **)&m->bnd_vptr, b_vptr.size() * sizeof(int32_t), s);
     if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_edges, b_edges.size() * sizeof(int32_t), s);

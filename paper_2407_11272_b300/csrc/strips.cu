@@ -134,8 +134,8 @@ void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int3
                 extend(seq, fs);
             }
             if (fs.size() > best_fs.size()) {
-                best_seq = seq;
-                best_fs = fs;
+                best_seq.swap(seq);
+                best_fs.swap(fs);
             }
         }
         ev_vert.push_back(best_seq[0]);
