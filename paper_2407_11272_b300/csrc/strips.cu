@@ -26,6 +26,7 @@
 // with face index >= 0 completes the face formed with the two vertices before it.
 #include <algorithm>
 #include <cstdint>
+#include <new>
 #include <utility>
 #include <vector>
 
@@ -205,7 +206,11 @@ extern "C" dv_status dv_build_strips(const int32_t *faces, int64_t nf, int64_t n
         if (faces[i] < 0 || faces[i] >= nv)
             return dv::report_error(DV_ERR_INVALID_MESH, "dv_build_strips: face index outside [0, nv)");
     std::vector<int32_t> v, f;
-    dv::build_strips(faces, nf, nv, v, f);
+    try {
+        dv::build_strips(faces, nf, nv, v, f);
+    } catch (const std::bad_alloc &) {
+        return dv::report_error(DV_ERR_OOM, "dv_build_strips: host memory");
+    }
     *n_events = (int64_t)v.size();
     if (!ev_vert || !ev_face) return DV_OK;  // size query
     if (capacity < (int64_t)v.size())
