@@ -12,7 +12,6 @@
 #include <mutex>
 #include <new>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "../../include/dv_api.h"
@@ -310,9 +309,11 @@ void dv_mesh_destroy(dv_mesh *m) {
     delete m;
 }
 
-dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,
-                         dv_mesh **out) {
-    g_last_error.clear();
+namespace {
+// The body of dv_mesh_create; `m` is set as soon as the mesh object exists so that the caller
+// can release it if a host allocation throws.
+dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,
+                           dv_mesh **out, dv_mesh *&held) {
     if (!out) return fail(DV_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!d_verts || !d_faces) return fail(DV_ERR_INVALID_ARG, "vertex or face pointer is NULL");
@@ -322,6 +323,7 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
         return fail(DV_ERR_UNSUPPORTED, "mesh too large (nv %lld, nf %lld)", (long long)nv, (long long)nf);
     cudaStream_t s = (cudaStream_t)stream;
     dv_mesh *m = new dv_mesh();
+    held = m;
     m->nv = nv;
     m->nf = nf;
     cudaGetDevice(&m->device);
@@ -350,27 +352,17 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
         return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
     if (bad == 1) return bail(fail(DV_ERR_INVALID_MESH, "a face index is outside [0, %lld)", (long long)nv));
     if (bad == 2) return bail(fail(DV_ERR_INVALID_MESH, "a vertex coordinate is not finite"));
-    // Host topology, independent parts on two threads: the strip order of the faces (forward
-    // passes) on a worker; the vertex -> (face, corner) CSR (deterministic gather) and the
-    // boundary edges (boundary form of the adjoint) here.
-    std::vector<int32_t> ev_vert, ev_face;
-    bool strip_oom = false;
-    std::thread strip_worker([&] {
-        try {
-            dv::build_strips(hf.data(), nf, nv, ev_vert, ev_face);
-        } catch (const std::bad_alloc &) {
-            strip_oom = true;
-        }
-    });
+    // Host topology: the vertex -> (face, corner) CSR (deterministic gather), the strip order of
+    // the faces (forward passes) and the boundary edges (boundary form of the adjoint).
     std::vector<int32_t> ptr((size_t)nv + 1, 0), corner((size_t)nf * 3);
     for (int64_t i = 0; i < 3 * nf; ++i) ptr[(size_t)hf[i] + 1]++;
     for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
     std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
     for (int64_t i = 0; i < 3 * nf; ++i) corner[(size_t)fill[hf[i]]++] = (int32_t)i;
+    std::vector<int32_t> ev_vert, ev_face;
+    dv::build_strips(hf.data(), nf, nv, ev_vert, ev_face);
     std::vector<int32_t> b_edges, b_vptr, b_vend;
     dv::build_boundary(hf.data(), nf, nv, b_edges, b_vptr, b_vend);
-    strip_worker.join();
-    if (strip_oom) return bail(fail(DV_ERR_OOM, "host memory for the strip order"));
     m->ne = (int64_t)ev_vert.size();
     e = cudaMallocAsync((void **)&m->ev_vert, (size_t)m->ne * sizeof(int32_t), s);
     if (!e) e = cudaMallocAsync((void **)&m->ev_face, (size_t)m->ne * sizeof(int32_t), s);
@@ -407,6 +399,21 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
     if ((e = cudaStreamSynchronize(s))) return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
     *out = m;
     return DV_OK;
+}
+}  // namespace
+
+dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,
+                         dv_mesh **out) {
+    g_last_error.clear();
+    dv_mesh *held = nullptr;
+    try {
+        return mesh_create_impl(d_verts, nv, d_faces, nf, stream, out, held);
+    } catch (const std::bad_alloc &) {
+        // a host vector could not grow; the device buffers made so far are released in stream order
+        if (out) *out = nullptr;
+        if (held) dv_mesh_destroy(held);
+        return fail(DV_ERR_OOM, "host memory while building the mesh");
+    }
 }
 
 dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
