@@ -45,8 +45,8 @@ OPS_BWD = 120
 # SHA-256 of the kernel's source file at capture time: if that file has changed since, the
 # counters no longer describe the kernel and the bench line reports traffic as null.
 TRAFFIC = {
-    ("torus_128", "bwd_grid"): (10702080, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "1c2ad25bdb2c7630f4ee9aefc9b97499b20b13a6032e1c122457e44ba7b84fa8"),
+    ("torus_128", "bwd_grid"): (10864640, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                "57acc5daefcec86e7a270b61d393a0b1a42824a6403c2b6acfd9e179f4457e3f"),
 }
 
 WORKLOADS = {

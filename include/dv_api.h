@@ -119,6 +119,24 @@ dv_status dv_selftest_bounded_wait(int64_t limit_us, int arrive, void *stream);
 dv_status dv_build_strips(const int32_t *faces, int64_t nf, int64_t nv, int32_t *ev_vert, int32_t *ev_face,
                           int64_t capacity, int64_t *n_events);
 
+/* Edge-sharing face pairs of the grid adjoint: consecutive faces of the strip
+ * order (dv_build_strips) taken two at a time, so that per (query, pair) four
+ * vertex distances and five edge dots of the derivative of Eq. (7) serve two
+ * faces. HOST function, no GPU needed. faces int32 [nf][3] (host), indices in
+ * [0, nv). Output, host, caller-owned: pairs int32 [n_pairs][8] = p0, p1, p2,
+ * p3, fA, fB, code, 0 with face fA = (p0, p1, p2) in its input orientation
+ * (a rotation of its corners) and face fB the vertex set {p1, p2, p3}, taken
+ * as (p2, p1, p3); code holds for each corner c = 0, 1, 2 of (p0, p1, p2) the
+ * input corner of fA it is (bits 2c), for each corner of (p2, p1, p3) the
+ * input corner of fB (bits 6 + 2c), and bit 12 when fB's input orientation is
+ * the reverse of (p2, p1, p3); singles int32 [n_singles] = the faces in no
+ * pair. Every face is in exactly one pair or in singles. With pairs or singles
+ * NULL only the counts are set (size query); DV_ERR_INVALID_ARG if a capacity
+ * is below its count. No counterpart in the paper (an evaluation order). */
+dv_status dv_build_face_pairs(const int32_t *faces, int64_t nf, int64_t nv, int32_t *pairs, int32_t *singles,
+                              int64_t capacity_pairs, int64_t capacity_singles, int64_t *n_pairs,
+                              int64_t *n_singles);
+
 /* Human-readable name of a status code. Never NULL. */
 const char *dv_status_string(dv_status s);
 

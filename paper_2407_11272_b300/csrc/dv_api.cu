@@ -101,6 +101,10 @@ struct dv_mesh {
     int32_t *ev_face = nullptr;           // [ne], -1 for a strip's first two events
     dv::StripRec *srec = nullptr;         // [ne]
     dv::StripRec64 *srec64 = nullptr;     // [ne]
+    int64_t np = 0, nsingle = 0;          // edge-sharing face pairs and unpaired faces (grid adjoint)
+    int32_t *ptopo = nullptr;             // [np][8]
+    dv::PairRec *prec = nullptr;          // [np]
+    int32_t *singles = nullptr;           // [nsingle]
     int64_t nb = 0;                       // boundary edges (net multiplicity != 0)
     int32_t *bnd_edges = nullptr;         // [nb][3]: u, v, m
     dv::BndRec *bnd_rec = nullptr;        // [nb]
@@ -123,6 +127,10 @@ struct dv_mesh {
 };
 
 namespace {
+
+dv::BwdFaces bwd_faces(const dv_mesh *m) {
+    return dv::BwdFaces{m->rec, m->nf, m->prec, m->ptopo, m->np, m->singles, m->nsingle};
+}
 
 struct DeviceGuard {
     int prev = -1;
@@ -303,7 +311,8 @@ void dv_mesh_destroy(dv_mesh *m) {
     DeviceGuard dg(m->device);
     void *bufs[] = {m->faces,   m->rec,     m->rec64, m->vtx_ptr, m->vtx_corner, m->ev_vert,    m->ev_face,
                     m->srec,    m->srec64,  m->err,   m->ws_w,    m->ws_near,    m->ws_list,    m->ws_partial,
-                    m->ws_fg,   m->ws_bins, m->bnd_edges, m->bnd_rec, m->bnd_vptr, m->bnd_vend, m->ws_bpart};
+                    m->ws_fg,   m->ws_bins, m->bnd_edges, m->bnd_rec, m->bnd_vptr, m->bnd_vend, m->ws_bpart,
+                    m->ptopo,   m->prec,    m->singles};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, m->last_stream);
     delete m;
@@ -359,8 +368,9 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
     for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
     std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
     for (int64_t i = 0; i < 3 * nf; ++i) corner[(size_t)fill[hf[i]]++] = (int32_t)i;
-    std::vector<int32_t> ev_vert, ev_face;
+    std::vector<int32_t> ev_vert, ev_face, p_topo, p_singles;
     dv::build_strips(hf.data(), nf, nv, ev_vert, ev_face);
+    dv::build_pairs(hf.data(), nf, ev_vert, ev_face, p_topo, p_singles);
     std::vector<int32_t> b_edges, b_vptr, b_vend;
     dv::build_boundary(hf.data(), nf, nv, b_edges, b_vptr, b_vend);
     m->ne = (int64_t)ev_vert.size();
@@ -369,6 +379,17 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
     if (!e) e = cudaMallocAsync((void **)&m->srec, (size_t)m->ne * sizeof(dv::StripRec), s);
     if (!e) e = cudaMallocAsync((void **)&m->srec64, (size_t)m->ne * sizeof(dv::StripRec64), s);
     if (e) return bail(fail(DV_ERR_OOM, "strip storage: %s", cudaGetErrorString(e)));
+    m->np = (int64_t)p_topo.size() / 8;
+    m->nsingle = (int64_t)p_singles.size();
+    if (m->np > 0) e = cudaMallocAsync((void **)&m->ptopo, p_topo.size() * sizeof(int32_t), s);
+    if (!e && m->np > 0) e = cudaMallocAsync((void **)&m->prec, (size_t)m->np * sizeof(dv::PairRec), s);
+    if (!e && m->nsingle > 0) e = cudaMallocAsync((void **)&m->singles, p_singles.size() * sizeof(int32_t), s);
+    if (e) return bail(fail(DV_ERR_OOM, "face pair storage: %s", cudaGetErrorString(e)));
+    if ((m->np > 0 && (e = cudaMemcpyAsync(m->ptopo, p_topo.data(), p_topo.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s))) ||
+        (m->nsingle > 0 && (e = cudaMemcpyAsync(m->singles, p_singles.data(), p_singles.size() * sizeof(int32_t),
+                                                cudaMemcpyHostToDevice, s))))
+        return bail(fail(DV_ERR_CUDA, "face pair upload: %s", cudaGetErrorString(e)));
     m->nb = (int64_t)b_edges.size() / 3;
     e = cudaMallocAsync((void **)&m->bnd_vptr, b_vptr.size() * sizeof(int32_t), s);
     if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_edges, b_edges.size() * sizeof(int32_t), s);
@@ -393,7 +414,8 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
         (e = cudaMemcpyAsync(m->faces, d_faces, (size_t)nf * 3 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)))
         return bail(fail(DV_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e)));
     if ((e = dv::launch_pack(d_verts, m->faces, nf, m->rec, m->rec64, s)) ||
-        (e = dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64, s)))
+        (e = dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64, s)) ||
+        (e = dv::launch_pack_pairs(m->rec, m->ptopo, m->np, m->prec, s)))
         return bail(fail(DV_ERR_CUDA, "pack: %s", cudaGetErrorString(e)));
     // the host vectors above must outlive the async uploads
     if ((e = cudaStreamSynchronize(s))) return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
@@ -423,6 +445,7 @@ dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
     DV_CUDA(dv::launch_pack(d_verts, m->faces, m->nf, m->rec, m->rec64, (cudaStream_t)stream));
     DV_CUDA(dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64,
                                    (cudaStream_t)stream));
+    DV_CUDA(dv::launch_pack_pairs(m->rec, m->ptopo, m->np, m->prec, (cudaStream_t)stream));
     DV_CUDA(dv::launch_pack_boundary(d_verts, m->bnd_edges, m->nb, m->bnd_rec, (cudaStream_t)stream));
     return DV_OK;
 }
@@ -434,7 +457,7 @@ dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_quer
     int64_t nq = max_list_queries, part = 0, fg = 0;
     if (max_list_queries > 0) {
         const dv::FwdPlan fp = dv::plan_forward(max_list_queries, m->nf, false, nullptr, m->num_sms, m->ne);
-        const dv::BwdPlan bp = dv::plan_backward(max_list_queries, m->nf, false, nullptr, m->num_sms);
+        const dv::BwdPlan bp = dv::plan_backward(max_list_queries, bwd_faces(m), false, nullptr, m->num_sms);
         part = fp.nsplit > 1 ? (int64_t)fp.nsplit * max_list_queries : 0;
         fg = (int64_t)bp.nsplit * m->nf * 9;
     }
@@ -445,7 +468,7 @@ dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_quer
         // the strip plan (FP32 / Kahan / mixed) and the face plan (FP16 ablation)
         const dv::FwdPlan fp = dv::plan_forward(gq, m->nf, true, &gf, m->num_sms, m->ne);
         const dv::FwdPlan fp16 = dv::plan_forward(gq, m->nf, true, &gf, m->num_sms);
-        const dv::BwdPlan bp = dv::plan_backward(gq, m->nf, true, &gf, m->num_sms);
+        const dv::BwdPlan bp = dv::plan_backward(gq, bwd_faces(m), true, &gf, m->num_sms);
         nq = std::max(nq, gq);
         part = std::max(part, fp.nsplit > 1 ? (int64_t)fp.nsplit * gq : (int64_t)0);
         part = std::max(part, fp16.nsplit > 1 ? (int64_t)fp16.nsplit * gq : (int64_t)0);
@@ -513,11 +536,11 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
     cudaStream_t s = (cudaStream_t)stream;
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
-    const dv::BwdPlan plan = dv::plan_backward(n, m->nf, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
+    const dv::BwdPlan plan = dv::plan_backward(n, bwd_faces(m), grid != nullptr, grid ? &gf : nullptr, m->num_sms);
     m->last_stream = s;
     if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)plan.nsplit * m->nf * 9, s))) return st;
     const dv::LaunchCtx ctx{s, m->err};
-    DV_CUDA(dv::launch_backward(plan, m->rec, m->nf, grid ? &gf : nullptr, d_queries, n, d_upstream, m->ws_fg, ctx));
+    DV_CUDA(dv::launch_backward(plan, bwd_faces(m), grid ? &gf : nullptr, d_queries, n, d_upstream, m->ws_fg, ctx));
     DV_CUDA(dv::launch_gather_dverts(nullptr, m->ws_fg, plan.nsplit, m->nf, m->vtx_ptr, m->vtx_corner, m->nv, d_dverts,
                                      s));
     return DV_OK;
@@ -596,7 +619,7 @@ dv_status reserve_request(dv_mesh *m, const dv_request &r, dv_precision prec, cu
     if (fp.nsplit > 1 && (st = grow(m->ws_partial, m->cap_partial, (int64_t)fp.nsplit * nq, s))) return st;
     if ((prec == DV_PREC_MIXED || r.d_out_w == nullptr) && (st = reserve_queries(m, nq, s))) return st;
     if (r.d_upstream) {
-        const dv::BwdPlan bp = dv::plan_backward(nq, m->nf, true, &gf, m->num_sms);
+        const dv::BwdPlan bp = dv::plan_backward(nq, bwd_faces(m), true, &gf, m->num_sms);
         if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)bp.nsplit * m->nf * 9, s))) return st;
     }
     return DV_OK;
@@ -604,11 +627,11 @@ dv_status reserve_request(dv_mesh *m, const dv_request &r, dv_precision prec, cu
 
 dv_status backward_on(dv_mesh *m, const dv_grid *grid, int64_t nq, const float *up, float *dverts, cudaStream_t s) {
     const dv::GridF gf = to_gridf(grid);
-    const dv::BwdPlan plan = dv::plan_backward(nq, m->nf, true, &gf, m->num_sms);
+    const dv::BwdPlan plan = dv::plan_backward(nq, bwd_faces(m), true, &gf, m->num_sms);
     dv_status st;
     if ((st = grow(m->ws_fg, m->cap_fg, (int64_t)plan.nsplit * m->nf * 9, s))) return st;
     const dv::LaunchCtx ctx{s, m->err};
-    DV_CUDA(dv::launch_backward(plan, m->rec, m->nf, &gf, nullptr, nq, up, m->ws_fg, ctx));
+    DV_CUDA(dv::launch_backward(plan, bwd_faces(m), &gf, nullptr, nq, up, m->ws_fg, ctx));
     DV_CUDA(dv::launch_gather_dverts(nullptr, m->ws_fg, plan.nsplit, m->nf, m->vtx_ptr, m->vtx_corner, m->nv, dverts,
                                      s));
     return DV_OK;

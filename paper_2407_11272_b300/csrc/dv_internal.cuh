@@ -51,6 +51,19 @@ struct StripRec64 {
     double pad;
 };
 
+// Two faces sharing an edge, for the grid adjoint (winding_bwd.cu; pairing in strips.cu):
+// face A = (p0, p1, p2), face B = (p2, p1, p3), each with its unit-free normal n = e1 x e2 in
+// that canonical orientation (FP32, the face record's 8 n / 8, negated for B when its input
+// orientation is reversed). 80 bytes.
+struct PairRec {
+    float4 r0;  // p0, nA.x
+    float4 r1;  // p1, nA.y
+    float4 r2;  // p2, nA.z
+    float4 r3;  // p3, nB.x
+    float4 r4;  // nB.y, nB.z, 0, 0
+};
+static_assert(sizeof(PairRec) == 80, "pair record must be 80 bytes");
+
 // One directed boundary edge p -> r of the mesh (net multiplicity m != 0 over all faces), for the
 // boundary form of the adjoint (winding_bnd.cu). 32 bytes.
 struct BndRec {
@@ -212,6 +225,12 @@ void build_boundary(const int32_t *faces, int64_t nf, int64_t nv, std::vector<in
 // strips.cu: vertex-sharing strip order of the faces (host, once per mesh).
 void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int32_t> &ev_vert,
                   std::vector<int32_t> &ev_face);
+// Edge-sharing face pairs from the strip order: pairs [np][8] = p0, p1, p2, p3, fA, fB, code, 0
+// and the faces left unpaired (host).
+void build_pairs(const int32_t *faces, int64_t nf, const std::vector<int32_t> &ev_vert,
+                 const std::vector<int32_t> &ev_face, std::vector<int32_t> &pairs, std::vector<int32_t> &singles);
+// Pair records from the packed face records (after launch_pack).
+cudaError_t launch_pack_pairs(const FaceRec *rec, const int32_t *ptopo, int64_t np, PairRec *prec, cudaStream_t s);
 cudaError_t launch_flipped_duplication(const float *verts, int64_t nv, const int32_t *faces, int64_t nf,
                                        const FaceRec64 *rec64, const int32_t *vtx_ptr, const int32_t *vtx_corner,
                                        double eps, float *out_verts, int32_t *out_faces, cudaStream_t s);
@@ -262,14 +281,26 @@ cudaError_t launch_dipole_backward(const FaceRec *rec, int64_t nf, const GridF *
                                    const float *upstream, int nsplit, float *face_grad, cudaStream_t s);
 
 // winding_bwd.cu
+// The faces as the adjoint sees them: the face records, and for grid queries the edge-sharing
+// pairs (records + topology) and the unpaired faces (prec == nullptr: every face alone).
+struct BwdFaces {
+    const FaceRec *rec;
+    int64_t nf;
+    const PairRec *prec;
+    const int32_t *ptopo;  // [np][8]
+    int64_t np;
+    const int32_t *singles;  // [nsingle]
+    int64_t nsingle;
+};
 struct BwdPlan {
     int threads;
-    int64_t fblocks;
+    int64_t fblocks;         // CTAs along x: pair CTAs first (grid), then single-face CTAs
+    int64_t pblocks;         // of which take pairs
     int nsplit;
     int64_t rows_per_split;  // grid: rows (z,y) per split; list: queries per split
 };
-BwdPlan plan_backward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms);
-cudaError_t launch_backward(const BwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
-                            int64_t nq, const float *upstream, float *face_grad, const LaunchCtx &ctx);
+BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g, int num_sms);
+cudaError_t launch_backward(const BwdPlan &p, const BwdFaces &fc, const GridF *g, const float *queries, int64_t nq,
+                            const float *upstream, float *face_grad, const LaunchCtx &ctx);
 
 }  // namespace dv

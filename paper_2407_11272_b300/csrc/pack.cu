@@ -148,6 +148,39 @@ cudaError_t launch_pack_strips(const float *verts, const int32_t *ev_vert, const
     return cudaGetLastError();
 }
 
+// Pair records (canonical A = (p0, p1, p2), B = (p2, p1, p3)) from the packed face records:
+// the vertices of A in the rotation the topology code names, p3 from B, the normals unscaled
+// (8 n / 8 is exact) and B's negated when its input orientation is reversed.
+__device__ __forceinline__ float4 rec_corner(const FaceRec &r, int c) { return c == 0 ? r.r0 : (c == 1 ? r.r1 : r.r2); }
+
+__global__ void pack_pairs_kernel(const FaceRec *__restrict__ rec, const int32_t *__restrict__ ptopo, int64_t np,
+                                  PairRec *__restrict__ prec) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *t = ptopo + 8 * i;
+        const int code = t[6];
+        const FaceRec A = rec[t[4]], B = rec[t[5]];
+        const float4 c0 = rec_corner(A, code & 3), c1 = rec_corner(A, (code >> 2) & 3),
+                     c2 = rec_corner(A, (code >> 4) & 3), c3 = rec_corner(B, (code >> 10) & 3);
+        const float inv = 1.0f / kNormalScale, sb = (code >> 12) & 1 ? -inv : inv;
+        PairRec r;
+        r.r0 = make_float4(c0.x, c0.y, c0.z, A.r0.w * inv);
+        r.r1 = make_float4(c1.x, c1.y, c1.z, A.r1.w * inv);
+        r.r2 = make_float4(c2.x, c2.y, c2.z, A.r2.w * inv);
+        r.r3 = make_float4(c3.x, c3.y, c3.z, B.r0.w * sb);
+        r.r4 = make_float4(B.r1.w * sb, B.r2.w * sb, 0.0f, 0.0f);
+        prec[i] = r;
+    }
+}
+
+cudaError_t launch_pack_pairs(const FaceRec *rec, const int32_t *ptopo, int64_t np, PairRec *prec, cudaStream_t s) {
+    if (np == 0) return cudaSuccess;
+    prof_begin("pack_pairs", s);
+    pack_pairs_kernel<<<blocks_for(np, 256), 256, 0, s>>>(rec, ptopo, np, prec);
+    count_launch();
+    prof_end("pack_pairs", s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_dverts(const double *, const float *face_grad, int nsplit, int64_t nf,
                                  const int32_t *vtx_ptr, const int32_t *vtx_corner, int64_t nv, float *dverts,
                                  cudaStream_t s) {

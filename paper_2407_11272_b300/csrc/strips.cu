@@ -1,5 +1,6 @@
 // Mesh topology on the host, once per mesh at creation: the vertex-sharing strip order of the
-// faces (below) and the boundary edges used by the boundary form of the adjoint (build_boundary).
+// faces (below), the edge-sharing face pairs of the grid adjoint (build_pairs) and the boundary
+// edges used by the boundary form of the adjoint (build_boundary).
 //
 // Vertex-sharing triangle strips.
 //
@@ -156,6 +157,57 @@ void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int3
     }
 }
 
+// Pairs of faces that share an edge, for the grid adjoint (winding_bwd.cu): two consecutive
+// faces of a strip share the edge formed by the two events between them, so per (query, pair)
+// four vertex distances and five edge dots serve both faces instead of six and six. Faces of a
+// strip are paired front to back; what is left (odd strip ends, singletons) is listed in
+// `singles`. Pair record (8 ints): p0, p1, p2, p3, fA, fB, code, 0, where face A is (p0, p1, p2)
+// in its own orientation (a rotation of its input corners) and face B is the vertex set
+// {p1, p2, p3} taken as (p2, p1, p3); `code` holds, for the canonical corners c = 0, 1, 2 of A
+// and then of B, the input corner each one is (2 bits each, A at bit 2c, B at bit 6 + 2c), and
+// bit 12 when B's input orientation is the reverse of (p2, p1, p3).
+void build_pairs(const int32_t *faces, int64_t nf, const std::vector<int32_t> &ev_vert,
+                 const std::vector<int32_t> &ev_face, std::vector<int32_t> &pairs, std::vector<int32_t> &singles) {
+    pairs.clear();
+    singles.clear();
+    pairs.reserve((size_t)nf * 4);
+    singles.reserve((size_t)nf / 4 + 16);
+    const int64_t ne = (int64_t)ev_vert.size();
+    auto corner_of = [&](int32_t f, int32_t v) {
+        for (int c = 0; c < 3; ++c)
+            if (faces[3 * (int64_t)f + c] == v) return c;
+        return -1;
+    };
+    for (int64_t k = 0; k < ne; ++k) {
+        const int32_t fa = ev_face[(size_t)k];
+        if (fa < 0) continue;
+        const int32_t fb = k + 1 < ne ? ev_face[(size_t)k + 1] : -1;
+        bool paired = false;
+        if (fb >= 0 && k >= 2) {
+            const int32_t u = ev_vert[(size_t)k - 2], s1 = ev_vert[(size_t)k - 1], s2 = ev_vert[(size_t)k],
+                          w = ev_vert[(size_t)k + 1];
+            const bool distinct = u != s1 && u != s2 && u != w && s1 != s2 && s1 != w && s2 != w;
+            const int ra = distinct ? corner_of(fa, u) : -1;
+            if (ra >= 0 && !degenerate(faces + 3 * (int64_t)fa) && !degenerate(faces + 3 * (int64_t)fb)) {
+                const int32_t p1 = faces[3 * (int64_t)fa + (ra + 1) % 3], p2 = faces[3 * (int64_t)fa + (ra + 2) % 3];
+                const int b0 = corner_of(fb, p2), b1 = corner_of(fb, p1), b2 = corner_of(fb, w);
+                if (((p1 == s1 && p2 == s2) || (p1 == s2 && p2 == s1)) && b0 >= 0 && b1 >= 0 && b2 >= 0) {
+                    const bool rev = b1 != (b0 + 1) % 3;
+                    const int32_t code = ra | ((ra + 1) % 3) << 2 | ((ra + 2) % 3) << 4 | b0 << 6 | b1 << 8 |
+                                         b2 << 10 | (rev ? 1 << 12 : 0);
+                    const int32_t rec[8] = {u, p1, p2, w, fa, fb, code, 0};
+                    pairs.insert(pairs.end(), rec, rec + 8);
+                    paired = true;
+                }
+            }
+        }
+        if (paired)
+            ++k;  // fb is taken
+        else
+            singles.push_back(fa);
+    }
+}
+
 void build_boundary(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int32_t> &edges,
                     std::vector<int32_t> &vptr, std::vector<int32_t> &vend) {
     // net multiplicity of every undirected edge {u < v}: +1 per face traversing u -> v, -1 per v -> u
@@ -217,5 +269,30 @@ extern "C" dv_status dv_build_strips(const int32_t *faces, int64_t nf, int64_t n
         return dv::report_error(DV_ERR_INVALID_ARG, "dv_build_strips: capacity below the number of events");
     std::copy(v.begin(), v.end(), ev_vert);
     std::copy(f.begin(), f.end(), ev_face);
+    return DV_OK;
+}
+
+extern "C" dv_status dv_build_face_pairs(const int32_t *faces, int64_t nf, int64_t nv, int32_t *pairs,
+                                         int32_t *singles, int64_t capacity_pairs, int64_t capacity_singles,
+                                         int64_t *n_pairs, int64_t *n_singles) {
+    if (!faces || !n_pairs || !n_singles || nf < 1 || nv < 3 || capacity_pairs < 0 || capacity_singles < 0)
+        return dv::report_error(DV_ERR_INVALID_ARG, "dv_build_face_pairs: bad arguments");
+    for (int64_t i = 0; i < 3 * nf; ++i)
+        if (faces[i] < 0 || faces[i] >= nv)
+            return dv::report_error(DV_ERR_INVALID_MESH, "dv_build_face_pairs: face index outside [0, nv)");
+    std::vector<int32_t> v, f, p, sg;
+    try {
+        dv::build_strips(faces, nf, nv, v, f);
+        dv::build_pairs(faces, nf, v, f, p, sg);
+    } catch (const std::bad_alloc &) {
+        return dv::report_error(DV_ERR_OOM, "dv_build_face_pairs: host memory");
+    }
+    *n_pairs = (int64_t)p.size() / 8;
+    *n_singles = (int64_t)sg.size();
+    if (!pairs || !singles) return DV_OK;  // size query
+    if (capacity_pairs < *n_pairs || capacity_singles < *n_singles)
+        return dv::report_error(DV_ERR_INVALID_ARG, "dv_build_face_pairs: capacity below the count");
+    std::copy(p.begin(), p.end(), pairs);
+    std::copy(sg.begin(), sg.end(), singles);
     return DV_OK;
 }

@@ -19,9 +19,14 @@
 //   dL/dv2 = k [-e1 x U_cD - T_P e1 - T_ac e2 - U_c],   k = 1/(2 pi).
 // On a grid row (fixed y, z) the y and z parts of a are constant, so the sums over a row are
 // kept as 7 scalars and their x-weighted versions (14 FMAs per pair) and folded per row.
+// On the grid, a thread owns two faces that share an edge (consecutive faces of a strip, paired
+// on the host): per query the four vertex distances (one MUFU reciprocal square root each) and
+// the five edge dots serve both faces; the faces left unpaired run one per thread.
 // Per-face sums are FP32 with Kahan compensation; per-split face gradients are summed over
 // splits and incident faces in FP64 by the gather kernel (pack.cu), in a fixed order.
 #include <math.h>
+
+#include <atomic>
 
 #include "dv_internal.cuh"
 
@@ -40,6 +45,13 @@ struct BwdArgs {
     int64_t rows_per_split;  // grid: rows; list: queries
     float *face_grad;        // [nsplit][nf][9]
     int *err;
+    // grid path: edge-sharing pairs (CTAs [0, pblocks)) and unpaired faces (null: all faces)
+    const PairRec *prec;
+    const int32_t *ptopo;
+    int64_t np;
+    const int32_t *singles;
+    int64_t nsingle;
+    int64_t pblocks;
 };
 
 struct FaceF {
@@ -113,6 +125,8 @@ __device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx
 // a packed FP32x2 instruction (Blackwell FFMA2/FADD2/FMUL2: one issue slot for both queries);
 // only the MUFU reciprocal square roots and reciprocals stay scalar. The even and odd queries of
 // the row accumulate in the two halves of S2/X2.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
 struct FaceF2 {
     float2 v0x, v1x, v2x, nx;
 };
@@ -120,16 +134,13 @@ struct RowB2 {
     float2 La, Lb, Lc, Pab, Pbc, Pca, Nyz;
 };
 
-__device__ __forceinline__ void bwd_pair2(const FaceF2 &F, const RowB2 &R, float2 nqx, float2 g, float2 (&S)[7],
-                                          float2 (&X)[7]) {
-    const float2 ax = __fadd2_rn(F.v0x, nqx), bx = __fadd2_rn(F.v1x, nqx), cx = __fadd2_rn(F.v2x, nqx);
-    const float2 la2 = __ffma2_rn(ax, ax, R.La), lb2 = __ffma2_rn(bx, bx, R.Lb), lc2 = __ffma2_rn(cx, cx, R.Lc);
-    const float2 ia = make_float2(rsqrt_approx(la2.x), rsqrt_approx(la2.y));
-    const float2 ib = make_float2(rsqrt_approx(lb2.x), rsqrt_approx(lb2.y));
-    const float2 ic = make_float2(rsqrt_approx(lc2.x), rsqrt_approx(lc2.y));
-    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
-    const float2 ab = __ffma2_rn(ax, bx, R.Pab), bc = __ffma2_rn(bx, cx, R.Pbc), ca = __ffma2_rn(cx, ax, R.Pca);
-    const float2 N = __ffma2_rn(ax, F.nx, R.Nyz);
+__device__ __forceinline__ float2 rsqrt2(float2 v) { return make_float2(rsqrt_approx(v.x), rsqrt_approx(v.y)); }
+
+// The adjoint terms of one face for two queries of a row, from the distances |a|, |b|, |c|, their
+// reciprocals, the edge dots, N and the x offset of the face's first vertex.
+__device__ __forceinline__ void bwd_face2(float2 la, float2 lb, float2 lc, float2 ia, float2 ib, float2 ic,
+                                          float2 ab, float2 bc, float2 ca, float2 N, float2 ax, float2 g,
+                                          float2 (&S)[7], float2 (&X)[7]) {
     const float2 tc = __ffma2_rn(la, lb, ab);
     float2 D = __fmul2_rn(tc, lc);
     D = __ffma2_rn(la, bc, D);
@@ -158,6 +169,73 @@ __device__ __forceinline__ void bwd_pair2(const FaceF2 &F, const RowB2 &R, float
     X[4] = __ffma2_rn(pa, kA, X[4]);
     X[5] = __ffma2_rn(pa, kB, X[5]);
     X[6] = __ffma2_rn(pa, kC, X[6]);
+}
+
+__device__ __forceinline__ void bwd_pair2(const FaceF2 &F, const RowB2 &R, float2 nqx, float2 g, float2 (&S)[7],
+                                          float2 (&X)[7]) {
+    const float2 ax = __fadd2_rn(F.v0x, nqx), bx = __fadd2_rn(F.v1x, nqx), cx = __fadd2_rn(F.v2x, nqx);
+    const float2 la2 = __ffma2_rn(ax, ax, R.La), lb2 = __ffma2_rn(bx, bx, R.Lb), lc2 = __ffma2_rn(cx, cx, R.Lc);
+    const float2 ia = rsqrt2(la2), ib = rsqrt2(lb2), ic = rsqrt2(lc2);
+    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
+    const float2 ab = __ffma2_rn(ax, bx, R.Pab), bc = __ffma2_rn(bx, cx, R.Pbc), ca = __ffma2_rn(cx, ax, R.Pca);
+    const float2 N = __ffma2_rn(ax, F.nx, R.Nyz);
+    bwd_face2(la, lb, lc, ia, ib, ic, ab, bc, ca, N, ax, g, S, X);
+}
+
+// Two faces sharing the edge (p1, p2): A = (p0, p1, p2) and B = (p2, p1, p3). Per pair of queries
+// the four distances (four MUFU square roots per query instead of six) and the five edge dots
+// serve both faces; the per-face arithmetic is bwd_face2, as for a face alone.
+struct PairF2 {
+    float2 p0x, p1x, p2x, p3x, nAx, nBx;
+};
+struct PairRow2 {
+    float2 L0, L1, L2, L3, P01, P12, P20, P13, P32, NA, NB;
+};
+
+__device__ __forceinline__ PairRow2 pair_row(const PairRec &P, float qy, float qz) {
+    const float y0 = P.r0.y - qy, z0 = P.r0.z - qz, y1 = P.r1.y - qy, z1 = P.r1.z - qz;
+    const float y2 = P.r2.y - qy, z2 = P.r2.z - qz, y3 = P.r3.y - qy, z3 = P.r3.z - qz;
+    PairRow2 R;
+    R.L0 = bc2(fmaf(y0, y0, z0 * z0));
+    R.L1 = bc2(fmaf(y1, y1, z1 * z1));
+    R.L2 = bc2(fmaf(y2, y2, z2 * z2));
+    R.L3 = bc2(fmaf(y3, y3, z3 * z3));
+    R.P01 = bc2(fmaf(y0, y1, z0 * z1));
+    R.P12 = bc2(fmaf(y1, y2, z1 * z2));
+    R.P20 = bc2(fmaf(y2, y0, z2 * z0));
+    R.P13 = bc2(fmaf(y1, y3, z1 * z3));
+    R.P32 = bc2(fmaf(y3, y2, z3 * z2));
+    R.NA = bc2(fmaf(y0, P.r1.w, z0 * P.r2.w));
+    R.NB = bc2(fmaf(y2, P.r4.x, z2 * P.r4.y));
+    return R;
+}
+
+__device__ __forceinline__ void bwd_quad2(const PairF2 &P, const PairRow2 &R, float2 nqx, float2 g, float2 (&SA)[7],
+                                          float2 (&XA)[7], float2 (&SB)[7], float2 (&XB)[7]) {
+    const float2 x0 = __fadd2_rn(P.p0x, nqx), x1 = __fadd2_rn(P.p1x, nqx);
+    const float2 x2 = __fadd2_rn(P.p2x, nqx), x3 = __fadd2_rn(P.p3x, nqx);
+    const float2 m0 = __ffma2_rn(x0, x0, R.L0), m1 = __ffma2_rn(x1, x1, R.L1);
+    const float2 m2 = __ffma2_rn(x2, x2, R.L2), m3 = __ffma2_rn(x3, x3, R.L3);
+    const float2 i0 = rsqrt2(m0), i1 = rsqrt2(m1), i2 = rsqrt2(m2), i3 = rsqrt2(m3);
+    const float2 l0 = __fmul2_rn(m0, i0), l1 = __fmul2_rn(m1, i1), l2 = __fmul2_rn(m2, i2), l3 = __fmul2_rn(m3, i3);
+    const float2 d01 = __ffma2_rn(x0, x1, R.P01), d12 = __ffma2_rn(x1, x2, R.P12), d20 = __ffma2_rn(x2, x0, R.P20);
+    const float2 d13 = __ffma2_rn(x1, x3, R.P13), d32 = __ffma2_rn(x3, x2, R.P32);
+    const float2 NA = __ffma2_rn(x0, P.nAx, R.NA), NB = __ffma2_rn(x2, P.nBx, R.NB);
+    bwd_face2(l0, l1, l2, i0, i1, i2, d01, d12, d20, NA, x0, g, SA, XA);  // A: a = p0, b = p1, c = p2
+    bwd_face2(l2, l1, l3, i2, i1, i3, d12, d13, d32, NB, x2, g, SB, XB);  // B: a = p2, b = p1, c = p3
+}
+
+// Face A (which = 0) or B (which = 1) of a pair as a face alone, in its canonical corner order.
+__device__ __forceinline__ FaceF pair_face(const PairRec &P, int which) {
+    FaceF F;
+    const float4 a = which ? P.r2 : P.r0, c = which ? P.r3 : P.r2;
+    F.v0x = a.x; F.v0y = a.y; F.v0z = a.z;
+    F.v1x = P.r1.x; F.v1y = P.r1.y; F.v1z = P.r1.z;
+    F.v2x = c.x; F.v2y = c.y; F.v2z = c.z;
+    F.nx = which ? P.r3.w : P.r0.w;
+    F.ny = which ? P.r4.x : P.r1.w;
+    F.nz = which ? P.r4.y : P.r2.w;
+    return F;
 }
 
 // Per-face sums, kept in shared memory (touched once per row or chunk of queries, so the
@@ -207,9 +285,12 @@ __device__ __forceinline__ FaceF load_face(const FaceRec *rec, int64_t f) {
 }
 
 // Combine the face sums (T, U as compensated FP64 values) into the 9 gradient components (FP64
-// arithmetic) and store them.
+// arithmetic) and store them: corner c of F goes to the input corner (code >> 2c) & 3 of the face,
+// times sign (-1 when F is the face with its orientation reversed).
+constexpr int kCornersIdentity = 0 | 1 << 2 | 2 << 4;
+
 __device__ __forceinline__ void write_face_grad_d(const FaceF &F, const double (&T)[6], const double (&U)[4][3],
-                                                  float *out) {
+                                                  float *out, int code = kCornersIdentity, double sign = 1.0) {
     const double e1[3] = {(double)F.v1x - F.v0x, (double)F.v1y - F.v0y, (double)F.v1z - F.v0z};
     const double e2[3] = {(double)F.v2x - F.v0x, (double)F.v2y - F.v0y, (double)F.v2z - F.v0z};
     const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -222,26 +303,21 @@ __device__ __forceinline__ void write_face_grad_d(const FaceF &F, const double (
         const double g0 = T[0] * n[k] + dxu[k] - T[3] * e1[k] - T[2] * e2[k] - U[1][k];
         const double g1 = e2xu[k] - T[4] * e1[k] - T[1] * e2[k] - U[2][k];
         const double g2 = -e1xu[k] - T[1] * e1[k] - T[5] * e2[k] - U[3][k];
-        out[k] = (float)(g0 * kInv2PiD);
-        out[3 + k] = (float)(g1 * kInv2PiD);
-        out[6 + k] = (float)(g2 * kInv2PiD);
+        const double k2 = sign * kInv2PiD;
+        out[3 * (code & 3) + k] = (float)(g0 * k2);
+        out[3 * ((code >> 2) & 3) + k] = (float)(g1 * k2);
+        out[3 * ((code >> 4) & 3) + k] = (float)(g2 * k2);
     }
 }
 
-__device__ __forceinline__ void write_face_grad_sm(const FaceF &F, float2 (*ks)[kBwdThreads], float *out) {
+__device__ __forceinline__ void write_face_grad_sm(const FaceF &F, float2 (*ks)[kBwdThreads], float *out,
+                                                   int code = kCornersIdentity, double sign = 1.0) {
     const int t = threadIdx.x;
     double T[6], U[4][3];
     for (int i = 0; i < 6; ++i) T[i] = (double)ks[i][t].x - (double)ks[i][t].y;
     for (int i = 0; i < 4; ++i)
         for (int k = 0; k < 3; ++k) U[i][k] = (double)ks[6 + 3 * i + k][t].x - (double)ks[6 + 3 * i + k][t].y;
-    write_face_grad_d(F, T, U, out);
-}
-
-__device__ __forceinline__ bool all_finite(const float (&S)[7], const float (&X)[7]) {
-    float t = 0.f;
-#pragma unroll
-    for (int i = 0; i < 7; ++i) t += S[i] + X[i];
-    return isfinite(t);
+    write_face_grad_d(F, T, U, out, code, sign);
 }
 
 // Staged queries of a window, in pairs: for query i (pair p = i/2, k = i%2) the window holds
@@ -250,24 +326,16 @@ __device__ __forceinline__ bool all_finite(const float (&S)[7], const float (&X)
 __device__ __forceinline__ float win_nqx(const float *wf, int64_t i) { return wf[4 * (i >> 1) + (i & 1)]; }
 __device__ __forceinline__ float win_g(const float *wf, int64_t i) { return wf[4 * (i >> 1) + 2 + (i & 1)]; }
 
-__global__ void __launch_bounds__(kBwdThreads, 4) bwd_grid_kernel(const BwdArgs a) {
-    __shared__ __align__(16) float wf[2 * kBwdWin];
-    __shared__ float2 ks[kFaceSlots][kBwdThreads];
-    const int64_t f = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    const FaceF F = load_face(a.rec, f < a.nf ? f : a.nf - 1);
-    FaceF2 F2;
-    F2.v0x = make_float2(F.v0x, F.v0x);
-    F2.v1x = make_float2(F.v1x, F.v1x);
-    F2.v2x = make_float2(F.v2x, F.v2x);
-    F2.nx = make_float2(F.nx, F.nx);
+// Rows of the grid are processed in windows of whole rows when a row fits the window (packed
+// pairs of queries when the row length is even); longer rows go in pieces through the guarded
+// path. visit(qy, qz, i0, xlen, packed) handles one row (or piece) whose queries sit at window
+// indices i0 .. i0 + xlen - 1.
+template <typename RowFn>
+__device__ __forceinline__ void for_each_row(const BwdArgs &a, float *wf, RowFn &&visit) {
     const int nx = a.g.n[0], ny = a.g.n[1];
     const int64_t nrows = (int64_t)a.g.n[1] * a.g.n[2];
     const int64_t r0 = (int64_t)blockIdx.y * a.rows_per_split;
     const int64_t r1 = r0 + a.rows_per_split < nrows ? r0 + a.rows_per_split : nrows;
-#pragma unroll
-    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
-    // Rows are processed in windows of whole rows when a row fits the window (packed pairs of
-    // queries when the row length is even); longer rows go in pieces through the guarded path.
     const bool whole = nx <= kBwdWin;
     const bool packed = whole && (nx % 2 == 0);
     const int rows_per_win = whole ? kBwdWin / nx : 1;
@@ -290,53 +358,147 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_grid_kernel(const BwdArgs 
                 const int iy = (int)(row % ny), iz = (int)(row / ny);
                 const float qy = __fmaf_rn((float)iy + 0.5f, a.g.h[1], a.g.lo[1]);
                 const float qz = __fmaf_rn((float)iz + 0.5f, a.g.h[2], a.g.lo[2]);
-                const RowB R = row_b(F, qy, qz);
-                const int64_t i0 = whole ? rr * nx : 0;  // first window index of this row
-                float S[7], X[7];
-#pragma unroll
-                for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-                if (packed) {
-                    RowB2 R2;
-                    R2.La = make_float2(R.La, R.La);
-                    R2.Lb = make_float2(R.Lb, R.Lb);
-                    R2.Lc = make_float2(R.Lc, R.Lc);
-                    R2.Pab = make_float2(R.Pab, R.Pab);
-                    R2.Pbc = make_float2(R.Pbc, R.Pbc);
-                    R2.Pca = make_float2(R.Pca, R.Pca);
-                    R2.Nyz = make_float2(R.Nyz, R.Nyz);
-                    float2 S2[7], X2[7];
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) S2[k] = X2[k] = make_float2(0.f, 0.f);
-                    const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
-#pragma unroll 4
-                    for (int p = 0; p < nx / 2; ++p) {
-                        const float4 q = wp[p];
-                        bwd_pair2(F2, R2, make_float2(q.x, q.y), make_float2(q.z, q.w), S2, X2);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) {
-                        S[k] = S2[k].x + S2[k].y;
-                        X[k] = X2[k].x + X2[k].y;
-                    }
-                } else if (whole) {
-#pragma unroll 4
-                    for (int ix = 0; ix < nx; ++ix)
-                        bwd_pair<false>(F, R, -win_nqx(wf, i0 + ix), win_g(wf, i0 + ix), S, X);
-                }
-                if (!whole || !all_finite(S, X)) {
-                    // pieces of long rows, and rows whose unguarded sums are not finite (a query on a
-                    // vertex or on an edge line): the guarded scalar path
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-                    for (int ix = 0; ix < xlen; ++ix)
-                        bwd_pair<true>(F, R, -win_nqx(wf, i0 + ix), win_g(wf, i0 + ix), S, X);
-                }
-                fold_sm(ks, S, X, R.ay, R.az);
+                visit(qy, qz, whole ? rr * nx : (int64_t)0, xlen, packed);
             }
             if (whole) break;
         }
     }
-    if (f < a.nf) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+}
+
+// The guarded scalar path over one row (or piece) for one face, folded into its face sums: rows
+// with an odd number of queries, pieces of long rows, and rows whose packed sums are not finite
+// (a query on a vertex or on an edge line).
+__device__ __noinline__ void row_guarded(const FaceF F, float qy, float qz, const float *wf, int64_t i0, int xlen,
+                                         float2 (*ks)[kBwdThreads]) {
+    const RowB R = row_b(F, qy, qz);
+    float S[7], X[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
+    for (int ix = 0; ix < xlen; ++ix) bwd_pair<true>(F, R, -win_nqx(wf, i0 + ix), win_g(wf, i0 + ix), S, X);
+    fold_sm(ks, S, X, R.ay, R.az);
+}
+
+__device__ __forceinline__ bool all_finite2(const float2 (&S)[7], const float2 (&X)[7]) {
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) t += (S[i].x + S[i].y) + (X[i].x + X[i].y);
+    return isfinite(t);
+}
+
+__device__ __forceinline__ void fold_sm2(float2 (*ks)[kBwdThreads], const float2 (&S2)[7], const float2 (&X2)[7],
+                                         float ay, float az) {
+    float S[7], X[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        S[k] = S2[k].x + S2[k].y;
+        X[k] = X2[k].x + X2[k].y;
+    }
+    fold_sm(ks, S, X, ay, az);
+}
+
+// A CTA of single faces: thread t owns one face (from the list of unpaired faces, or face index
+// order when there is no list).
+__device__ __forceinline__ void bwd_grid_singles(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads]) {
+    const int64_t count = a.singles ? a.nsingle : a.nf;
+    const int64_t idx = ((int64_t)blockIdx.x - a.pblocks) * kBwdThreads + threadIdx.x;
+    const int64_t ic = idx < count ? idx : count - 1;
+    const int64_t f = a.singles ? (int64_t)a.singles[ic] : ic;
+    const FaceF F = load_face(a.rec, f);
+    FaceF2 F2;
+    F2.v0x = bc2(F.v0x);
+    F2.v1x = bc2(F.v1x);
+    F2.v2x = bc2(F.v2x);
+    F2.nx = bc2(F.nx);
+#pragma unroll
+    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
+    for_each_row(a, wf, [&](float qy, float qz, int64_t i0, int xlen, bool packed) {
+        bool ok = false;
+        if (packed) {
+            const RowB R = row_b(F, qy, qz);
+            RowB2 R2;
+            R2.La = bc2(R.La);
+            R2.Lb = bc2(R.Lb);
+            R2.Lc = bc2(R.Lc);
+            R2.Pab = bc2(R.Pab);
+            R2.Pbc = bc2(R.Pbc);
+            R2.Pca = bc2(R.Pca);
+            R2.Nyz = bc2(R.Nyz);
+            float2 S2[7], X2[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) S2[k] = X2[k] = make_float2(0.f, 0.f);
+            const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
+#pragma unroll 4
+            for (int p = 0; p < xlen / 2; ++p) {
+                const float4 q = wp[p];
+                bwd_pair2(F2, R2, make_float2(q.x, q.y), make_float2(q.z, q.w), S2, X2);
+            }
+            ok = all_finite2(S2, X2);
+            if (ok) fold_sm2(ks, S2, X2, R.ay, R.az);
+        }
+        if (!ok) row_guarded(F, qy, qz, wf, i0, xlen, ks);
+    });
+    if (idx < count) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+}
+
+// A CTA of edge-sharing face pairs: thread t owns pair t; its two faces keep separate sums
+// (shared-memory slots 0..17 for A, 18..35 for B).
+__device__ __forceinline__ void bwd_grid_pairs(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads]) {
+    const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    const int64_t ic = idx < a.np ? idx : a.np - 1;
+    const PairRec P = a.prec[ic];
+    PairF2 P2;
+    P2.p0x = bc2(P.r0.x);
+    P2.p1x = bc2(P.r1.x);
+    P2.p2x = bc2(P.r2.x);
+    P2.p3x = bc2(P.r3.x);
+    P2.nAx = bc2(P.r0.w);
+    P2.nBx = bc2(P.r3.w);
+    float2(*ksB)[kBwdThreads] = ks + kFaceSlots;
+#pragma unroll
+    for (int k = 0; k < 2 * kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
+    for_each_row(a, wf, [&](float qy, float qz, int64_t i0, int xlen, bool packed) {
+        bool okA = false, okB = false;
+        if (packed) {
+            const PairRow2 R = pair_row(P, qy, qz);
+            float2 SA[7], XA[7], SB[7], XB[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) SA[k] = XA[k] = SB[k] = XB[k] = make_float2(0.f, 0.f);
+            const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
+#pragma unroll 2
+            for (int p = 0; p < xlen / 2; ++p) {
+                const float4 q = wp[p];
+                bwd_quad2(P2, R, make_float2(q.x, q.y), make_float2(q.z, q.w), SA, XA, SB, XB);
+            }
+            okA = all_finite2(SA, XA);
+            okB = all_finite2(SB, XB);
+            if (okA) fold_sm2(ks, SA, XA, P.r0.y - qy, P.r0.z - qz);
+            if (okB) fold_sm2(ksB, SB, XB, P.r2.y - qy, P.r2.z - qz);
+        }
+        if (!okA) row_guarded(pair_face(P, 0), qy, qz, wf, i0, xlen, ks);
+        if (!okB) row_guarded(pair_face(P, 1), qy, qz, wf, i0, xlen, ksB);
+    });
+    if (idx < a.np) {
+        const int32_t *t = a.ptopo + 8 * idx;
+        const int code = t[6];
+        float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
+        write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
+        write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
+                           (code >> 12) & 1 ? -1.0 : 1.0);
+    }
+}
+
+// Grid adjoint: CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces. Dynamic
+// shared memory: the query window, then 2 x 18 face-sum slots per thread.
+constexpr size_t kBwdGridSmem = sizeof(float) * 2 * kBwdWin + sizeof(float2) * 2 * kFaceSlots * kBwdThreads;
+
+__global__ void __launch_bounds__(kBwdThreads, 3) bwd_grid_kernel(const BwdArgs a) {
+    extern __shared__ __align__(16) float bwd_smem[];
+    float *wf = bwd_smem;
+    float2(*ks)[kBwdThreads] = reinterpret_cast<float2(*)[kBwdThreads]>(bwd_smem + 2 * kBwdWin);
+    if ((int64_t)blockIdx.x < a.pblocks)
+        bwd_grid_pairs(a, wf, ks);
+    else
+        bwd_grid_singles(a, wf, ks);
 }
 
 // List path: arbitrary queries, so no row sharing. Two queries per packed FP32x2 instruction;
@@ -349,8 +511,6 @@ constexpr int kListChunk = 128;
 struct FaceL2 {
     float2 v0x, v0y, v0z, v1x, v1y, v1z, v2x, v2y, v2z, nx, ny, nz;
 };
-
-__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
 __device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float4 q1, float2 (&T)[6],
                                                float2 (&U)[4][3]) {
@@ -463,12 +623,18 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_list_kernel(const BwdArgs 
     if (f < a.nf) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
-BwdPlan plan_backward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num_sms) {
+BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g, int num_sms) {
     BwdPlan p{};
     p.threads = kBwdThreads;
-    p.fblocks = (nf + kBwdThreads - 1) / kBwdThreads;
+    if (grid && fc.prec) {
+        p.pblocks = (fc.np + kBwdThreads - 1) / kBwdThreads;
+        p.fblocks = p.pblocks + (fc.nsingle + kBwdThreads - 1) / kBwdThreads;
+    } else {
+        p.pblocks = 0;
+        p.fblocks = (fc.nf + kBwdThreads - 1) / kBwdThreads;
+    }
     const int64_t units = grid ? (int64_t)g->n[1] * g->n[2] : nq;  // rows or queries
-    // About 5 CTAs of 128 threads are resident per SM; aim for >= 4 waves in total.
+    // 3 to 5 CTAs of 128 threads are resident per SM; aim for >= 4 waves in total.
     const int64_t target = 20LL * num_sms;
     int64_t ns = (target + p.fblocks - 1) / p.fblocks;
     if (ns < 1) ns = 1;
@@ -480,11 +646,11 @@ BwdPlan plan_backward(int64_t nq, int64_t nf, bool grid, const GridF *g, int num
     return p;
 }
 
-cudaError_t launch_backward(const BwdPlan &p, const FaceRec *rec, int64_t nf, const GridF *g, const float *queries,
-                            int64_t nq, const float *upstream, float *face_grad, const LaunchCtx &ctx) {
+cudaError_t launch_backward(const BwdPlan &p, const BwdFaces &fc, const GridF *g, const float *queries, int64_t nq,
+                            const float *upstream, float *face_grad, const LaunchCtx &ctx) {
     BwdArgs a{};
-    a.rec = rec;
-    a.nf = nf;
+    a.rec = fc.rec;
+    a.nf = fc.nf;
     if (g) a.g = *g;
     a.queries = queries;
     a.nq = nq;
@@ -492,13 +658,34 @@ cudaError_t launch_backward(const BwdPlan &p, const FaceRec *rec, int64_t nf, co
     a.rows_per_split = p.rows_per_split;
     a.face_grad = face_grad;
     a.err = ctx.d_err;
+    a.pblocks = p.pblocks;
+    if (p.pblocks > 0) {
+        a.prec = fc.prec;
+        a.ptopo = fc.ptopo;
+        a.np = fc.np;
+        a.singles = fc.singles;
+        a.nsingle = fc.nsingle;
+    }
     dim3 grid((unsigned)p.fblocks, (unsigned)p.nsplit);
     const char *name = queries ? "bwd_list" : "bwd_grid";
+    if (!queries) {
+        // once per device: the grid kernel's dynamic shared memory exceeds the 48 KB default
+        static std::atomic<uint64_t> smem_set{0};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        const uint64_t bit = 1ull << (dev & 63);
+        if (!(smem_set.load() & bit)) {
+            e = cudaFuncSetAttribute(bwd_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdGridSmem);
+            if (e != cudaSuccess) return e;
+            smem_set.fetch_or(bit);
+        }
+    }
     prof_begin(name, ctx.stream);
     if (queries)
         bwd_list_kernel<<<grid, kBwdThreads, 0, ctx.stream>>>(a);
     else
-        bwd_grid_kernel<<<grid, kBwdThreads, 0, ctx.stream>>>(a);
+        bwd_grid_kernel<<<grid, kBwdThreads, kBwdGridSmem, ctx.stream>>>(a);
     count_launch();
     prof_end(name, ctx.stream);
     return cudaGetLastError();

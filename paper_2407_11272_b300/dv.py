@@ -17,7 +17,7 @@ __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
     "dv_winding_backward_boundary", "dv_mesh_num_boundary_edges",
-    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_selftest_bounded_wait", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_build_face_pairs", "dv_selftest_bounded_wait", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2, "fp16": 3}
@@ -125,6 +125,9 @@ def load():
     lib.dv_selftest_bounded_wait.restype = ctypes.c_int
     lib.dv_build_strips.argtypes = [_P, _I64, _I64, _P, _P, _I64, ctypes.POINTER(_I64)]
     lib.dv_build_strips.restype = ctypes.c_int
+    lib.dv_build_face_pairs.argtypes = [_P, _I64, _I64, _P, _P, _I64, _I64, ctypes.POINTER(_I64),
+                                        ctypes.POINTER(_I64)]
+    lib.dv_build_face_pairs.restype = ctypes.c_int
     lib.dv_profile_enable.argtypes = [ctypes.c_int]
     lib.dv_profile_enable.restype = None
     lib.dv_profile_reset.restype = None
@@ -404,6 +407,26 @@ def dv_build_strips(faces, nv: int):
     _check(lib.dv_build_strips(ptr, nf, int(nv), ctypes.c_void_p(ev_vert.ctypes.data),
                                ctypes.c_void_p(ev_face.ctypes.data), n.value, ctypes.byref(n)), "dv_build_strips")
     return ev_vert, ev_face
+
+
+def dv_build_face_pairs(faces, nv: int):
+    """Edge-sharing face pairs of the grid adjoint (host call, no GPU): returns (pairs [n, 8],
+    singles [m]) int32 numpy arrays; see dv_build_face_pairs in dv_api.h for the record layout."""
+    import numpy as np
+
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    nf = f.shape[0]
+    lib = load()
+    n_p, n_s = _I64(0), _I64(0)
+    ptr = ctypes.c_void_p(f.ctypes.data)
+    _check(lib.dv_build_face_pairs(ptr, nf, int(nv), None, None, 0, 0, ctypes.byref(n_p), ctypes.byref(n_s)),
+           "dv_build_face_pairs")
+    pairs = np.empty((n_p.value, 8), dtype=np.int32)
+    singles = np.empty(n_s.value, dtype=np.int32)
+    _check(lib.dv_build_face_pairs(ptr, nf, int(nv), ctypes.c_void_p(pairs.ctypes.data),
+                                   ctypes.c_void_p(singles.ctypes.data), n_p.value, n_s.value, ctypes.byref(n_p),
+                                   ctypes.byref(n_s)), "dv_build_face_pairs")
+    return pairs, singles
 
 
 def dv_flipped_duplication(mesh: Mesh, verts, eps: float = 0.01, stream=None):

@@ -48,6 +48,52 @@ def test_ragged_faces_odd_grid_gradient(cuda_device):
     assert np.all(G[unused] == 0.0)
 
 
+@pytest.mark.parametrize("grid_n", [(24, 24, 24), (25, 19, 7)])
+def test_grid_gradient_face_pairs_mixed_orientation(cuda_device, grid_n):
+    """The grid adjoint walks edge-sharing face pairs (dv_build_face_pairs): with 30 % of the
+    faces reversed, pairs whose second face runs against (p2, p1, p3) occur beside consistent
+    ones, and on an even and an odd row length (packed and guarded paths) the gradient matches
+    the oracle's for the mesh as given."""
+    V, F = meshgen.jittered_torus(nu=40, nv=20, sigma=0.01, delete_frac=0.1, seed=2)
+    flip = np.random.default_rng(5).random(len(F)) < 0.3
+    F[flip] = F[flip][:, ::-1]
+    pairs, singles = dv.dv_build_face_pairs(F, len(V))
+    rev = (pairs[:, 6] >> 12) & 1
+    assert 0 < rev.sum() < len(pairs) and len(singles) > 0
+    grid = dv.Grid(grid_n, (-1.0, -0.9, -1.05), (1.0, 1.1, 0.95))
+    Q, _, d = oracle_grid(V, F, grid)
+    g = _masked_upstream(len(Q), d, seed=11)
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    mesh = make_mesh(V, F, cuda_device)
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    grad_close(G, G_ref, f"pairs mixed orientation {grid_n}", oracle.winding_grad_scale(V, F, Q, g))
+
+
+def test_grid_gradient_vertices_on_cell_centres(cuda_device):
+    """Mesh vertices placed exactly on voxel centres (as the kernels compute them in FP32): the
+    packed sums of those rows are not finite, so paired and single faces alike take the guarded
+    path for them; upstream is 0 within 1e-3 of the surface, so the oracle's gradient is the
+    reference."""
+    V, F = meshgen.jittered_torus(nu=30, nv=15, sigma=0.01, delete_frac=0.1, seed=9)
+    n, lo, hi = 24, -1.0, 1.0
+    h = np.float32((hi - lo) / n)
+    idx = np.clip(np.floor((V.astype(np.float64) - lo) / h), 0, n - 1)
+    centre = ((idx + 0.5) * np.float64(h) + lo).astype(np.float32)  # fmaf((float)i + 0.5f, h, lo)
+    pick = np.random.default_rng(3).choice(len(V), size=40, replace=False)
+    V = V.copy()
+    V[pick] = centre[pick]
+    pairs, singles = dv.dv_build_face_pairs(F, len(V))
+    grid = dv.Grid.cube(n)
+    Q, _, d = oracle_grid(V, F, grid)
+    assert (d < 1e-6).sum() >= 40  # the oracle's FP64 centres sit within 1e-7 of the FP32 ones
+    g = _masked_upstream(len(Q), d, seed=12)
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    mesh = make_mesh(V, F, cuda_device)
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    assert np.all(np.isfinite(G))
+    grad_close(G, G_ref, "vertices on cell centres", oracle.winding_grad_scale(V, F, Q, g))
+
+
 def test_list_gradient(cuda_device):
     V, F = meshgen.jittered_torus(nu=40, nv=20, sigma=0.01, delete_frac=0.1, seed=2)
     rng = np.random.default_rng(31)

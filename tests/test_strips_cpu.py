@@ -71,3 +71,63 @@ def test_strip_order_deterministic():
     a = dv.dv_build_strips(F, len(V))
     b = dv.dv_build_strips(F, len(V))
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def _check_pairs(F, pairs, singles):
+    """Every face in exactly one pair or in singles; each pair's records describe its two faces:
+    A = (p0, p1, p2) is a rotation of fA's corners and the code maps its canonical corners onto
+    them; B = (p2, p1, p3) is fB's vertex set, its corners mapped by the code, with bit 12 set
+    exactly when (p2, p1, p3) is not a rotation of fB's corners."""
+    nf = len(F)
+    seen = np.concatenate([pairs[:, 4], pairs[:, 5], singles]) if len(pairs) else singles
+    assert np.array_equal(np.sort(seen), np.arange(nf)), "every face exactly once"
+    assert np.all(pairs[:, 7] == 0)
+    for p0, p1, p2, p3, fa, fb, code, _ in pairs.tolist():
+        assert len({p0, p1, p2, p3}) == 4
+        ca = [(code >> (2 * c)) & 3 for c in range(3)]
+        cb = [(code >> (6 + 2 * c)) & 3 for c in range(3)]
+        assert sorted(ca) == [0, 1, 2] and sorted(cb) == [0, 1, 2]
+        assert [F[fa][ca[c]] for c in range(3)] == [p0, p1, p2]
+        assert [F[fb][cb[c]] for c in range(3)] == [p2, p1, p3]
+        # canonical A keeps fA's orientation: its corner map is a rotation
+        assert ca in ([0, 1, 2], [1, 2, 0], [2, 0, 1])
+        rot_b = cb in ([0, 1, 2], [1, 2, 0], [2, 0, 1])
+        assert bool((code >> 12) & 1) == (not rot_b)
+        assert code >> 13 == 0
+
+
+@pytest.mark.parametrize("kind", ["torus", "icosphere", "odd"])
+def test_face_pairs_valid(kind):
+    if kind == "torus":
+        V, F = meshgen.jittered_torus()
+    elif kind == "icosphere":
+        V, F = meshgen.icosphere(3, 0.8)
+    else:
+        V = np.zeros((12, 3), np.float32)
+        F = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4], [5, 5, 6], [7, 8, 9], [2, 1, 10], [2, 10, 11],
+                      [1, 2, 10]], dtype=np.int32)
+    pairs, singles = dv.dv_build_face_pairs(F, len(V))
+    _check_pairs(F, pairs, singles)
+    if kind == "icosphere":
+        assert 2 * len(pairs) >= 0.9 * len(F)  # long strips: nearly every face paired
+    if kind == "torus":
+        assert 2 * len(pairs) >= 0.7 * len(F)
+    if kind == "odd":
+        # the degenerate face [5, 5, 6] and the isolated face [7, 8, 9] stay single
+        assert 3 in singles and 4 in singles
+
+
+def test_face_pairs_reversed_orientation():
+    """Two faces crossing their shared edge in the same direction (inconsistent orientation):
+    they still pair, with bit 12 of the code set; randomly flipped torus faces give both kinds."""
+    F = np.array([[0, 1, 2], [1, 2, 3]], dtype=np.int32)
+    pairs, singles = dv.dv_build_face_pairs(F, 4)
+    _check_pairs(F, pairs, singles)
+    assert len(pairs) == 1 and len(singles) == 0 and (pairs[0, 6] >> 12) & 1 == 1
+    V, F = meshgen.jittered_torus(nu=40, nv=20, sigma=0.01, delete_frac=0.1, seed=2)
+    flip = np.random.default_rng(5).random(len(F)) < 0.3
+    F[flip] = F[flip][:, ::-1]
+    pairs, singles = dv.dv_build_face_pairs(F, len(V))
+    _check_pairs(F, pairs, singles)
+    rev = (pairs[:, 6] >> 12) & 1
+    assert 0 < rev.sum() < len(pairs)
