@@ -39,6 +39,10 @@ UNIT = "pairs/s"
 # lengths, N, dots, D, atan2, accumulate) and for the adjoint (no atan2, ~2x the algebra).
 OPS_FWD = 59
 OPS_BWD = 120
+# FP32 lane operations the grid adjoint kernel executes per pair (counted from its code, FMA = 1):
+# 42 for a face alone, 38.5 for a face of an edge-sharing pair (distances and dots shared).
+EXEC_BWD_SINGLE = 42.0
+EXEC_BWD_PAIRED = 38.5
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the dominant kernel on the full workload, keyed by (workload, kernel). Each entry records the
@@ -343,6 +347,12 @@ def run_native(args):
             "unit": "Tlane-op/s (FP32, FMA=1)", "frac": achieved / fp32_peak if fp32_peak else None,
             "traffic": traffic, "ops_per_pair": ops,
             "peak_note": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_src} sm_max_mhz)"}
+    if dname == "bwd_grid" and avg_s > 0:
+        # the same rate on the basis of the operations the kernel executes (faces in pairs and alone)
+        pair_recs, singles = dv.dv_build_face_pairs(F, len(V))
+        exec_ops = (EXEC_BWD_PAIRED * 2 * len(pair_recs) + EXEC_BWD_SINGLE * len(singles)) / nf
+        roof["executed_ops_per_pair"] = exec_ops
+        roof["frac_executed"] = exec_ops * pairs / avg_s / fp32_peak
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
