@@ -14,6 +14,7 @@ namespace dv {
 
 constexpr float kInv2Pi = 0.15915494309189535f;  // w = (1/4pi) sum Omega = (1/2pi) sum ATAN2
 constexpr double kInv2PiD = 0.15915494309189533576888;
+constexpr double kTwoPiD = 6.283185307179586476925;
 constexpr float kNearDist = 1e-3f;    // re-evaluate queries within this distance of a triangle
 constexpr float kThreshBand = 1e-3f;  // ... or with |w - 0.5| below this
 constexpr unsigned kFull = 0xffffffffu;

@@ -1,4 +1,4 @@
-"""Fit the minimax polynomials used by the kernels' arctangent fast paths.
+"""Fit the minimax polynomial used by the FP32 kernels' arctangent fast path.
 
 The FP32 forward kernel evaluates ATAN2(N, D) for the common case |N| < D/8
 (a face seen under a solid angle below about 0.25 sr). It stores the face
@@ -8,14 +8,11 @@ normal pre-multiplied by 8, so it holds v = 8N/D in [-1, 1] and needs
 
 with a small *relative* error, so that the error of a sum over faces stays
 proportional to the sum of |terms| (the faces far from a query have tiny
-solid angles). The FP64 re-evaluation kernel uses the same idea on u = N/D,
-|u| < 1/8:
+solid angles).
 
-    atan(u) ~= u * Q(u^2),       Q of degree ``DEG64`` in s = u^2.
-
-Both are fitted by the Remez exchange algorithm (E. Remez, 1934) on the
-reduced variable in [0, 1] with weight 1/g (relative error), carried out in
-50-digit arithmetic with mpmath; the FP32 coefficients are then checked by
+P is fitted by the Remez exchange algorithm (E. Remez, 1934) on the reduced
+variable in [0, 1] with weight 1/g (relative error), carried out in 50-digit
+arithmetic with mpmath; the float32 coefficients are then checked by
 evaluating the float32 Horner scheme exactly as the kernel does.
 
 Run ``python gen_atan_poly.py`` to regenerate ``atan_poly.h``.
@@ -27,9 +24,8 @@ from pathlib import Path
 import mpmath as mp
 import numpy as np
 
-T = 0.125      # fast-path bound on |N/D| (both precisions)
+T = 0.125      # fast-path bound on |N/D|
 DEG32 = 2
-DEG64 = 6
 
 mp.mp.dps = 50
 
@@ -105,27 +101,18 @@ def main():
     v = v[v != 0]
     ref = np.arctan(T * v.astype(np.float64))
     rel32 = float((np.abs(eval_f32(c32f, v).astype(np.float64) - ref) / np.abs(ref)).max())
-    # FP64 path: fit P(t) ~ atan(T sqrt(t)) / sqrt(t) on t in [0, 1], then substitute t = u^2 / T^2:
-    # atan(u) = (u / T) P(u^2 / T^2), i.e. Q(s) = sum_k c_k / T^(2k+1) s^k.
-    c64t = remez(DEG64, T)
-    e64 = max_rel_err_mp(c64t, T)
-    c64 = [c / mp.mpf(T) ** (2 * k + 1) for k, c in enumerate(c64t)]
+    e32 = max_rel_err_mp(c32, T)
     lines = [
-        "// Generated by gen_atan_poly.py (Remez minimax fits, relative error). Do not edit.",
+        "// Generated by gen_atan_poly.py (Remez minimax fit, relative error). Do not edit.",
         f"// FP32: atan(v * {T}) ~= v * P(v*v) for |v| <= 1, P of degree {DEG32};",
-        f"//       max relative error of the float32 evaluation: {rel32:.3e}",
-        f"// FP64: atan(u) ~= u * Q(u*u) for |u| <= {T}, Q of degree {DEG64};",
-        f"//       max relative error of the polynomial itself: {float(e64):.3e}",
+        f"//       max relative error of the polynomial itself: {float(e32):.3e},",
+        f"//       of its float32 evaluation: {rel32:.3e}",
         "#pragma once",
         f"#define DV_ATAN_FAST_T {T}f",
         f"#define DV_ATAN_FAST_DEG {DEG32}",
     ]
     for k, c in enumerate(c32f):
         lines.append(f"#define DV_ATAN_C{k} {float(c)!r}f")
-    lines.append(f"#define DV_ATAN64_FAST_T {T}")
-    lines.append(f"#define DV_ATAN64_DEG {DEG64}")
-    for k, c in enumerate(c64):
-        lines.append(f"#define DV_ATAN64_C{k} {mp.nstr(c, 25)}")
     Path(__file__).with_name("atan_poly.h").write_text("\n".join(lines) + "\n")
     print("\n".join(lines))
 

@@ -637,8 +637,11 @@ BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g,
     // 3 to 5 CTAs of 128 threads are resident per SM; aim for >= 4 waves in total.
     const int64_t target = 20LL * num_sms;
     int64_t ns = (target + p.fblocks - 1) / p.fblocks;
+    // at least 16 rows (grid) or 512 queries (list) per split: on small problems more splits only
+    // lengthen the per-vertex gather over splits
+    const int64_t per_min = grid ? 16 : 512;
+    if (ns > units / per_min) ns = units / per_min;
     if (ns < 1) ns = 1;
-    if (ns > units) ns = units > 0 ? units : 1;
     if (ns > 4096) ns = 4096;
     p.rows_per_split = (units + ns - 1) / ns;
     p.nsplit = (int)((units + p.rows_per_split - 1) / p.rows_per_split);

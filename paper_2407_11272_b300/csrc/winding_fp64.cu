@@ -22,27 +22,49 @@ struct Slot64 {
     double ax[kRsQB], ay[kRsQB], az[kRsQB], l[kRsQB], e[kRsQB];
 };
 
-// ATAN2(N, D) of one strip face in FP64. Fast path for D > 8|N| (a face seen under less than
-// ~0.25 sr, almost every face): atan(u) = u Q(u^2), u = N/D, Q a degree-6 Remez fit with
-// relative error below 2e-18 (atan_poly.h). Otherwise CUDA's atan2 with Eq. (8)'s conventions
-// (-0 -> +0; ATAN2(0, 0) = 0); a query on one of the face's vertices (a distance of exactly 0,
-// where N and D vanish) contributes 0.
-__device__ __forceinline__ double strip_half_angle64(double N, double D, double lV, double l1, double l2) {
-    if (D > 8.0 * fabs(N)) {
-        const double u = N / D;
-        const double s = u * u;
-        double P = DV_ATAN64_C6;
-        P = fma(P, s, DV_ATAN64_C5);
-        P = fma(P, s, DV_ATAN64_C4);
-        P = fma(P, s, DV_ATAN64_C3);
-        P = fma(P, s, DV_ATAN64_C2);
-        P = fma(P, s, DV_ATAN64_C1);
-        P = fma(P, s, DV_ATAN64_C0);
-        return u * P;
-    }
+// Sum of the half angles ATAN2(N, D) of Eq. (7)/(8) without an arctangent per face. For a face
+// with D > 8|N| (seen under less than ~0.25 sr, almost every face) ATAN2(N, D) is the argument
+// of z = D + iN, |arg z| < atan(1/8), and a sum of arguments is the argument of the product of
+// the z, counted with its turns: the running product P of a thread's fast faces changes its
+// argument by less than 0.125 rad per factor, so it passes the negative real axis exactly when
+// Im P changes sign while Re P < 0, upwards (+1 turn) when Im P goes from >= +0 to <= -0 and
+// downwards otherwise (sign bits, matching atan2's +-pi on that axis). At the end
+// sum = ATAN2(Im P, Re P) + 2 pi turns. Each factor is scaled by the power of two that brings D
+// into [1, 2) (exact), so |P| only grows, by less than 2.01 per factor, and P is rescaled by a
+// power of two every kRenorm faces. Per fast face this costs a complex product instead of a
+// division and a polynomial; every other face (D <= 8|N|) adds ATAN2 with Eq. (8)'s
+// conventions: -0 -> +0, ATAN2(0, 0) = 0, and 0 for a query on one of the face's vertices
+// (a distance of exactly 0, where N and D vanish).
+constexpr int kRenorm = 64;
+
+__device__ __forceinline__ double slow_half_angle64(double N, double D, double lV, double l1, double l2) {
     if (lV == 0.0 || l1 == 0.0 || l2 == 0.0) return 0.0;
     if (N == 0.0 && D == 0.0) return 0.0;
     return atan2(N + 0.0, D);
+}
+
+// 2^-e for x in [2^e, 2^(e+1)), built from x's exponent field (x > 0; clamped to normal scales).
+__device__ __forceinline__ double inv_pow2_of(double x) {
+    const int e = (__double2hiint(x) >> 20) & 0x7ff;
+    int f = 2046 - e;
+    f = f < 1 ? 1 : (f > 2046 ? 2046 : f);
+    return __hiloint2double(f << 20, 0);
+}
+
+struct ArgProduct {
+    double re, im;
+    int turns;
+};
+
+__device__ __forceinline__ void arg_product_mul(ArgProduct &P, double D, double N) {
+    const double sc = inv_pow2_of(D);
+    const double dr = D * sc, di = N * sc;
+    const double nr = fma(P.re, dr, -P.im * di);
+    const double ni = fma(P.re, di, P.im * dr);
+    const bool so = __double2hiint(P.im) < 0, sn = __double2hiint(ni) < 0;
+    if (so != sn && nr < 0.0) P.turns += so ? -1 : 1;
+    P.re = nr;
+    P.im = ni;
 }
 
 __global__ void __launch_bounds__(kReThreads, 2)
@@ -59,6 +81,7 @@ __global__ void __launch_bounds__(kReThreads, 2)
     const int64_t es = eb < 2 ? 0 : eb - 2;  // warm-up start
     for (int b = blockIdx.x; b < nb; b += gridDim.x) {
         double qx[kRsQB], qy[kRsQB], qz[kRsQB], sum[kRsQB];
+        ArgProduct prod[kRsQB];
         int ids[kRsQB];
 #pragma unroll
         for (int j = 0; j < kRsQB; ++j) {
@@ -76,7 +99,9 @@ __global__ void __launch_bounds__(kReThreads, 2)
                 qz[j] = g.lo[2] + ((double)iz + 0.5) * g.h[2];
             }
             sum[j] = 0.0;
+            prod[j] = ArgProduct{1.0, 0.0, 0};
         }
+        int nfac = 0;
         Slot64 P1, P2;
 #pragma unroll
         for (int j = 0; j < kRsQB; ++j) {
@@ -101,7 +126,19 @@ __global__ void __launch_bounds__(kReThreads, 2)
                     const double d2 = V.ax[j] * P2.ax[j] + V.ay[j] * P2.ay[j] + V.az[j] * P2.az[j];
                     const double N = V.ax[j] * r.n[0] + V.ay[j] * r.n[1] + V.az[j] * r.n[2];
                     const double D = (V.l[j] * P1.l[j] + V.e[j]) * P2.l[j] + V.l[j] * P1.e[j] + P1.l[j] * d2;
-                    sum[j] += strip_half_angle64(N, D, V.l[j], P1.l[j], P2.l[j]);
+                    if (D > 8.0 * fabs(N))
+                        arg_product_mul(prod[j], D, N);
+                    else
+                        sum[j] += slow_half_angle64(N, D, V.l[j], P1.l[j], P2.l[j]);
+                }
+                if (++nfac == kRenorm) {
+#pragma unroll
+                    for (int j = 0; j < kRsQB; ++j) {
+                        const double sc = inv_pow2_of(fmax(fabs(prod[j].re), fabs(prod[j].im)));
+                        prod[j].re *= sc;
+                        prod[j].im *= sc;
+                    }
+                    nfac = 0;
                 }
             }
             P2 = P1;
@@ -109,7 +146,7 @@ __global__ void __launch_bounds__(kReThreads, 2)
         }
 #pragma unroll
         for (int j = 0; j < kRsQB; ++j) {
-            double v = sum[j];
+            double v = sum[j] + (atan2(prod[j].im, prod[j].re) + kTwoPiD * prod[j].turns);
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
             if (lane == 0) red[warp][j] = v;
         }
