@@ -146,9 +146,10 @@ const char *dv_last_error(void);
 /* Algorithm 1 input "Mesh (V, F)": validate the faces (every index in [0, nv))
  * and vertices (finite), then pack each face f into a per-face record
  * (v0, v1, v2 and the face normal (v1-v0)x(v2-v0), FP32 and FP64 copies),
- * build the vertex-to-face adjacency and the strip order of the faces
+ * build the vertex-to-face adjacency, the strip order of the faces
  * (dv_build_strips) with its per-event records, used by the grid forward
- * and the FP64 re-evaluation. d_verts float32 [nv][3], d_faces int32 [nf][3]
+ * and the FP64 re-evaluation, and the edge-sharing face pairs of the grid
+ * adjoint (dv_build_face_pairs). The mesh keeps a host copy of the faces. d_verts float32 [nv][3], d_faces int32 [nf][3]
  * are read only during this call (the mesh keeps its own copies).
  * SYNCHRONIZES `stream` once (validation result). nv >= 3, nf >= 1.
  * On success *out receives a new handle; release it with dv_mesh_destroy. */
@@ -169,7 +170,8 @@ dv_status dv_mesh_reserve(dv_mesh *mesh, const dv_grid *grid, int64_t max_list_q
 
 /* Number of vertices / faces / boundary edges (directed edges with nonzero net
  * multiplicity over the faces; 0 for a closed, consistently oriented mesh) of a
- * mesh (-1 if mesh is NULL). */
+ * mesh (-1 if mesh is NULL, or if the host memory to find the boundary edges,
+ * which the first call does, is missing). */
 int64_t dv_mesh_num_verts(const dv_mesh *mesh);
 int64_t dv_mesh_num_faces(const dv_mesh *mesh);
 int64_t dv_mesh_num_boundary_edges(const dv_mesh *mesh);
@@ -220,7 +222,8 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
  * query on a boundary edge (|a||b| + a.b = 0) contributes nothing. No
  * counterpart in the paper: an evaluation of the same derivative. FP32 pair
  * arithmetic, FP64 vertex gather in a fixed order (deterministic).
- * Stream-ordered, no sync. */
+ * Stream-ordered, no sync; the first call on a mesh also finds its boundary
+ * edges on the host and uploads them (pageable copies). */
 dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                                        const float *d_upstream, float *d_dverts, void *stream);
 

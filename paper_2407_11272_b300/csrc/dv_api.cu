@@ -105,7 +105,11 @@ struct dv_mesh {
     int32_t *ptopo = nullptr;             // [np][8]
     dv::PairRec *prec = nullptr;          // [np]
     int32_t *singles = nullptr;           // [nsingle]
-    int64_t nb = 0;                       // boundary edges (net multiplicity != 0)
+    // boundary edges (net multiplicity != 0), built on first use: host topology, then device copies
+    std::vector<int32_t> hfaces;          // host copy of the faces [nf][3]
+    bool bnd_host = false, bnd_dev = false;
+    std::vector<int32_t> hb_edges, hb_vptr, hb_vend;
+    int64_t nb = 0;
     int32_t *bnd_edges = nullptr;         // [nb][3]: u, v, m
     dv::BndRec *bnd_rec = nullptr;        // [nb]
     int32_t *bnd_vptr = nullptr;          // [nv + 1]
@@ -362,7 +366,8 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
     if (bad == 1) return bail(fail(DV_ERR_INVALID_MESH, "a face index is outside [0, %lld)", (long long)nv));
     if (bad == 2) return bail(fail(DV_ERR_INVALID_MESH, "a vertex coordinate is not finite"));
     // Host topology: the vertex -> (face, corner) CSR (deterministic gather), the strip order of
-    // the faces (forward passes) and the boundary edges (boundary form of the adjoint).
+    // the faces (forward passes) and the adjoint's face pairs. The boundary edges (boundary form
+    // of the adjoint) are built on first use from the host copy of the faces kept here.
     std::vector<int32_t> ptr((size_t)nv + 1, 0), corner((size_t)nf * 3);
     for (int64_t i = 0; i < 3 * nf; ++i) ptr[(size_t)hf[i] + 1]++;
     for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
@@ -371,8 +376,6 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
     std::vector<int32_t> ev_vert, ev_face, p_topo, p_singles;
     dv::build_strips(hf.data(), nf, nv, ev_vert, ev_face);
     dv::build_pairs(hf.data(), nf, ev_vert, ev_face, p_topo, p_singles);
-    std::vector<int32_t> b_edges, b_vptr, b_vend;
-    dv::build_boundary(hf.data(), nf, nv, b_edges, b_vptr, b_vend);
     m->ne = (int64_t)ev_vert.size();
     e = cudaMallocAsync((void **)&m->ev_vert, (size_t)m->ne * sizeof(int32_t), s);
     if (!e) e = cudaMallocAsync((void **)&m->ev_face, (size_t)m->ne * sizeof(int32_t), s);
@@ -390,20 +393,6 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
         (m->nsingle > 0 && (e = cudaMemcpyAsync(m->singles, p_singles.data(), p_singles.size() * sizeof(int32_t),
                                                 cudaMemcpyHostToDevice, s))))
         return bail(fail(DV_ERR_CUDA, "face pair upload: %s", cudaGetErrorString(e)));
-    m->nb = (int64_t)b_edges.size() / 3;
-    e = cudaMallocAsync((void **)&m->bnd_vptr, b_vptr.size() * sizeof(int32_t), s);
-    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_edges, b_edges.size() * sizeof(int32_t), s);
-    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_rec, (size_t)m->nb * sizeof(dv::BndRec), s);
-    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_vend, b_vend.size() * sizeof(int32_t), s);
-    if (e) return bail(fail(DV_ERR_OOM, "boundary storage: %s", cudaGetErrorString(e)));
-    if ((e = cudaMemcpyAsync(m->bnd_vptr, b_vptr.data(), b_vptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                             s)) ||
-        (m->nb > 0 && (e = cudaMemcpyAsync(m->bnd_edges, b_edges.data(), b_edges.size() * sizeof(int32_t),
-                                           cudaMemcpyHostToDevice, s))) ||
-        (m->nb > 0 && (e = cudaMemcpyAsync(m->bnd_vend, b_vend.data(), b_vend.size() * sizeof(int32_t),
-                                           cudaMemcpyHostToDevice, s))) ||
-        (e = dv::launch_pack_boundary(d_verts, m->bnd_edges, m->nb, m->bnd_rec, s)))
-        return bail(fail(DV_ERR_CUDA, "boundary upload: %s", cudaGetErrorString(e)));
     if ((e = cudaMemcpyAsync(m->vtx_ptr, ptr.data(), ptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(m->vtx_corner, corner.data(), corner.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                              s)) ||
@@ -419,6 +408,7 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
         return bail(fail(DV_ERR_CUDA, "pack: %s", cudaGetErrorString(e)));
     // the host vectors above must outlive the async uploads
     if ((e = cudaStreamSynchronize(s))) return bail(fail(DV_ERR_CUDA, "mesh create: %s", cudaGetErrorString(e)));
+    m->hfaces.swap(hf);
     *out = m;
     return DV_OK;
 }
@@ -446,7 +436,9 @@ dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
     DV_CUDA(dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64,
                                    (cudaStream_t)stream));
     DV_CUDA(dv::launch_pack_pairs(m->rec, m->ptopo, m->np, m->prec, (cudaStream_t)stream));
-    DV_CUDA(dv::launch_pack_boundary(d_verts, m->bnd_edges, m->nb, m->bnd_rec, (cudaStream_t)stream));
+    if (m->bnd_dev)
+        DV_CUDA(dv::launch_pack_boundary(m->rec, m->vtx_ptr, m->vtx_corner, m->bnd_edges, m->nb, m->bnd_rec,
+                                         (cudaStream_t)stream));
     return DV_OK;
 }
 
@@ -546,6 +538,55 @@ dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64
     return DV_OK;
 }
 
+namespace {
+// Boundary edges of the mesh on the host (once).
+dv_status boundary_host(dv_mesh *m) {
+    if (m->bnd_host) return DV_OK;
+    try {
+        dv::build_boundary(m->hfaces.data(), m->nf, m->nv, m->hb_edges, m->hb_vptr, m->hb_vend);
+    } catch (const std::bad_alloc &) {
+        return fail(DV_ERR_OOM, "host memory while building the boundary edges");
+    }
+    m->nb = (int64_t)m->hb_edges.size() / 3;
+    m->bnd_host = true;
+    return DV_OK;
+}
+
+// ... and on the device, packed from the current face records (once; dv_mesh_update_verts
+// repacks them from then on).
+dv_status boundary_device(dv_mesh *m, cudaStream_t s) {
+    dv_status st = boundary_host(m);
+    if (st || m->bnd_dev) return st;
+    cudaError_t e = cudaMallocAsync((void **)&m->bnd_vptr, m->hb_vptr.size() * sizeof(int32_t), s);
+    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_edges, m->hb_edges.size() * sizeof(int32_t), s);
+    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_rec, (size_t)m->nb * sizeof(dv::BndRec), s);
+    if (!e && m->nb > 0) e = cudaMallocAsync((void **)&m->bnd_vend, m->hb_vend.size() * sizeof(int32_t), s);
+    auto release = [&] {  // a later call starts over
+        for (void **p : {(void **)&m->bnd_vptr, (void **)&m->bnd_edges, (void **)&m->bnd_rec, (void **)&m->bnd_vend})
+            if (*p) {
+                cudaFreeAsync(*p, s);
+                *p = nullptr;
+            }
+    };
+    if (e) {
+        release();
+        return fail(DV_ERR_OOM, "boundary storage: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpyAsync(m->bnd_vptr, m->hb_vptr.data(), m->hb_vptr.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s)) ||
+        (m->nb > 0 && (e = cudaMemcpyAsync(m->bnd_edges, m->hb_edges.data(), m->hb_edges.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s))) ||
+        (m->nb > 0 && (e = cudaMemcpyAsync(m->bnd_vend, m->hb_vend.data(), m->hb_vend.size() * sizeof(int32_t),
+                                           cudaMemcpyHostToDevice, s))) ||
+        (e = dv::launch_pack_boundary(m->rec, m->vtx_ptr, m->vtx_corner, m->bnd_edges, m->nb, m->bnd_rec, s))) {
+        release();
+        return fail(DV_ERR_CUDA, "boundary upload: %s", cudaGetErrorString(e));
+    }
+    m->bnd_dev = true;
+    return DV_OK;
+}
+}  // namespace
+
 dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                                        const float *d_upstream, float *d_dverts, void *stream) {
     int64_t n = 0;
@@ -557,8 +598,9 @@ dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queri
     cudaStream_t s = (cudaStream_t)stream;
     dv::GridF gf{};
     if (grid) gf = to_gridf(grid);
-    const dv::BndPlan plan = dv::plan_boundary(n, m->nb, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
     m->last_stream = s;
+    if ((st = boundary_device(m, s))) return st;
+    const dv::BndPlan plan = dv::plan_boundary(n, m->nb, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
     if (m->nb > 0 && (st = grow(m->ws_bpart, m->cap_bpart, (int64_t)plan.nsplit * m->nb * 8, s))) return st;
     DV_CUDA(dv::launch_boundary_backward(plan, m->bnd_rec, m->nb, grid ? &gf : nullptr, d_queries, n, d_upstream,
                                          m->ws_bpart, s));
@@ -567,7 +609,11 @@ dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queri
     return DV_OK;
 }
 
-int64_t dv_mesh_num_boundary_edges(const dv_mesh *mesh) { return mesh ? mesh->nb : -1; }
+int64_t dv_mesh_num_boundary_edges(const dv_mesh *mesh) {
+    if (!mesh) return -1;
+    dv_mesh *m = const_cast<dv_mesh *>(mesh);
+    return boundary_host(m) == DV_OK ? m->nb : -1;
+}
 
 // ------------------------------------------------------------------------------------------
 // Batches of independent requests as one CUDA graph (request server).

@@ -210,7 +210,9 @@ struct BndPlan {
     int64_t per_split;  // grid: rows per split; list: queries per split
 };
 BndPlan plan_boundary(int64_t nq, int64_t nb, bool grid, const GridF *g, int num_sms);
-cudaError_t launch_pack_boundary(const float *verts, const int32_t *edges, int64_t nb, BndRec *rec, cudaStream_t s);
+// Boundary records from the packed face records (vertex coordinates through the vertex CSR).
+cudaError_t launch_pack_boundary(const FaceRec *frec, const int32_t *vptr, const int32_t *vcorner,
+                                 const int32_t *edges, int64_t nb, BndRec *rec, cudaStream_t s);
 // Per-split edge sums into part [nsplit][nb][8]; nothing to do when nb == 0.
 cudaError_t launch_boundary_backward(const BndPlan &p, const BndRec *rec, int64_t nb, const GridF *g,
                                      const float *queries, int64_t nq, const float *upstream, float *part,

@@ -210,28 +210,44 @@ void build_pairs(const int32_t *faces, int64_t nf, const std::vector<int32_t> &e
 
 void build_boundary(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int32_t> &edges,
                     std::vector<int32_t> &vptr, std::vector<int32_t> &vend) {
-    // net multiplicity of every undirected edge {u < v}: +1 per face traversing u -> v, -1 per v -> u
-    std::vector<std::pair<uint64_t, int32_t>> he;
-    he.reserve((size_t)nf * 3);
+    // net multiplicity of every undirected edge {u < v}: +1 per face traversing u -> v, -1 per
+    // v -> u. The directed edges are bucketed by their lower endpoint (CSR), each short bucket is
+    // sorted by the upper endpoint and equal entries are merged, so the edges come out ordered
+    // by (u, v).
+    std::vector<int32_t> lptr((size_t)nv + 1, 0);
     for (int64_t f = 0; f < nf; ++f)
         for (int k = 0; k < 3; ++k) {
             const int32_t u = faces[3 * f + k], v = faces[3 * f + (k + 1) % 3];
-            if (u == v) continue;  // a zero-length edge of a degenerate face contributes nothing
-            const uint64_t lo = (uint32_t)(u < v ? u : v), hi = (uint32_t)(u < v ? v : u);
-            he.push_back({lo * (uint64_t)nv + hi, u < v ? 1 : -1});
+            if (u != v) lptr[(size_t)(u < v ? u : v) + 1]++;  // a zero-length edge contributes nothing
         }
-    std::sort(he.begin(), he.end());
+    for (int64_t v = 0; v < nv; ++v) lptr[v + 1] += lptr[v];
+    std::vector<std::pair<int32_t, int32_t>> he((size_t)lptr[nv]);  // (upper endpoint, +-1)
+    {
+        std::vector<int32_t> fill(lptr.begin(), lptr.end() - 1);
+        for (int64_t f = 0; f < nf; ++f)
+            for (int k = 0; k < 3; ++k) {
+                const int32_t u = faces[3 * f + k], v = faces[3 * f + (k + 1) % 3];
+                if (u == v) continue;
+                he[(size_t)fill[u < v ? u : v]++] = {u < v ? v : u, u < v ? 1 : -1};
+            }
+    }
     edges.clear();
-    for (size_t i = 0; i < he.size();) {
-        size_t j = i;
-        int32_t m = 0;
-        while (j < he.size() && he[j].first == he[i].first) m += he[j++].second;
-        if (m != 0) {
-            edges.push_back((int32_t)(he[i].first / (uint64_t)nv));
-            edges.push_back((int32_t)(he[i].first % (uint64_t)nv));
-            edges.push_back(m);
+    for (int64_t lo = 0; lo < nv; ++lo) {
+        auto b = he.begin() + lptr[lo], e = he.begin() + lptr[lo + 1];
+        std::sort(b, e, [](const std::pair<int32_t, int32_t> &x, const std::pair<int32_t, int32_t> &y) {
+            return x.first < y.first;
+        });
+        for (auto i = b; i != e;) {
+            auto j = i;
+            int32_t m = 0;
+            while (j != e && j->first == i->first) m += (j++)->second;
+            if (m != 0) {
+                edges.push_back((int32_t)lo);
+                edges.push_back(i->first);
+                edges.push_back(m);
+            }
+            i = j;
         }
-        i = j;
     }
     const int64_t nb = (int64_t)edges.size() / 3;
     vptr.assign((size_t)nv + 1, 0);

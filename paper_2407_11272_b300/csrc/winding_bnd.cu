@@ -274,13 +274,25 @@ __global__ void bnd_gather_kernel(int64_t nv, const BndRec *__restrict__ rec, in
     }
 }
 
-__global__ void pack_bnd_kernel(const float *__restrict__ verts, const int32_t *__restrict__ edges, int64_t nb,
+// Endpoint coordinates come from the packed face records (the first (face, corner) of each
+// vertex in the vertex CSR): the same FP32 values as the vertex array they were packed from.
+__device__ __forceinline__ float4 vertex_from_rec(const FaceRec *__restrict__ frec, const int32_t *__restrict__ vptr,
+                                                  const int32_t *__restrict__ vcorner, int64_t v) {
+    const int32_t c = vcorner[vptr[v]];
+    const FaceRec r = frec[c / 3];
+    const int k = c - 3 * (c / 3);
+    return k == 0 ? r.r0 : (k == 1 ? r.r1 : r.r2);
+}
+
+__global__ void pack_bnd_kernel(const FaceRec *__restrict__ frec, const int32_t *__restrict__ vptr,
+                                const int32_t *__restrict__ vcorner, const int32_t *__restrict__ edges, int64_t nb,
                                 BndRec *__restrict__ rec) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nb; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ip = edges[3 * e], ir = edges[3 * e + 1];
+        const float4 p = vertex_from_rec(frec, vptr, vcorner, edges[3 * e]);
+        const float4 r = vertex_from_rec(frec, vptr, vcorner, edges[3 * e + 1]);
         BndRec b;
-        b.p = make_float4(verts[3 * ip], verts[3 * ip + 1], verts[3 * ip + 2], (float)edges[3 * e + 2]);
-        b.r = make_float4(verts[3 * ir], verts[3 * ir + 1], verts[3 * ir + 2], 0.f);
+        b.p = make_float4(p.x, p.y, p.z, (float)edges[3 * e + 2]);
+        b.r = make_float4(r.x, r.y, r.z, 0.f);
         rec[e] = b;
     }
 }
@@ -292,10 +304,11 @@ static int grid_blocks(int64_t n, int threads) {
     return (int)b;
 }
 
-cudaError_t launch_pack_boundary(const float *verts, const int32_t *edges, int64_t nb, BndRec *rec, cudaStream_t s) {
+cudaError_t launch_pack_boundary(const FaceRec *frec, const int32_t *vptr, const int32_t *vcorner,
+                                 const int32_t *edges, int64_t nb, BndRec *rec, cudaStream_t s) {
     if (nb == 0) return cudaSuccess;
     prof_begin("pack_boundary", s);
-    pack_bnd_kernel<<<grid_blocks(nb, 256), 256, 0, s>>>(verts, edges, nb, rec);
+    pack_bnd_kernel<<<grid_blocks(nb, 256), 256, 0, s>>>(frec, vptr, vcorner, edges, nb, rec);
     count_launch();
     prof_end("pack_boundary", s);
     return cudaGetLastError();
