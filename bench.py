@@ -50,7 +50,7 @@ EXEC_BWD_PAIRED = 38.5
 # counters no longer describe the kernel and the bench line reports traffic as null.
 TRAFFIC = {
     ("torus_128", "bwd_grid"): (10864640, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "87dc27a6ad37abc3c81459fb34671aaf6b91564dfda9fcdfa9e85f1036165b0d"),
+                                "81f84345211f3a0dc5eb1093e769185cc6675de8e62ea0c64c58df9236ed0bb9"),
 }
 
 WORKLOADS = {

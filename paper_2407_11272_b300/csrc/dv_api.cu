@@ -402,6 +402,8 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
                              s)) ||
         (e = cudaMemcpyAsync(m->faces, d_faces, (size_t)nf * 3 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s)))
         return bail(fail(DV_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e)));
+    if ((e = dv::prepare_backward_kernels()))
+        return bail(fail(DV_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e)));
     if ((e = dv::launch_pack(d_verts, m->faces, nf, m->rec, m->rec64, s)) ||
         (e = dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64, s)) ||
         (e = dv::launch_pack_pairs(m->rec, m->ptopo, m->np, m->prec, s)))

@@ -302,6 +302,8 @@ struct BwdPlan {
     int nsplit;
     int64_t rows_per_split;  // grid: rows (z,y) per split; list: queries per split
 };
+// Kernel attributes of the adjoint on the current device (once; outside stream capture).
+cudaError_t prepare_backward_kernels();
 BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g, int num_sms);
 cudaError_t launch_backward(const BwdPlan &p, const BwdFaces &fc, const GridF *g, const float *queries, int64_t nq,
                             const float *upstream, float *face_grad, const LaunchCtx &ctx);

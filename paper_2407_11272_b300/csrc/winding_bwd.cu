@@ -623,6 +623,20 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_list_kernel(const BwdArgs 
     if (f < a.nf) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
+// Once per device (mesh creation calls it, outside any stream capture): the grid kernel's
+// dynamic shared memory exceeds the 48 KB default.
+cudaError_t prepare_backward_kernels() {
+    static std::atomic<uint64_t> smem_set{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (smem_set.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(bwd_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdGridSmem);
+    if (e == cudaSuccess) smem_set.fetch_or(bit);
+    return e;
+}
+
 BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g, int num_sms) {
     BwdPlan p{};
     p.threads = kBwdThreads;
@@ -672,17 +686,8 @@ cudaError_t launch_backward(const BwdPlan &p, const BwdFaces &fc, const GridF *g
     dim3 grid((unsigned)p.fblocks, (unsigned)p.nsplit);
     const char *name = queries ? "bwd_list" : "bwd_grid";
     if (!queries) {
-        // once per device: the grid kernel's dynamic shared memory exceeds the 48 KB default
-        static std::atomic<uint64_t> smem_set{0};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+        const cudaError_t e = prepare_backward_kernels();
         if (e != cudaSuccess) return e;
-        const uint64_t bit = 1ull << (dev & 63);
-        if (!(smem_set.load() & bit)) {
-            e = cudaFuncSetAttribute(bwd_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdGridSmem);
-            if (e != cudaSuccess) return e;
-            smem_set.fetch_or(bit);
-        }
     }
     prof_begin(name, ctx.stream);
     if (queries)
