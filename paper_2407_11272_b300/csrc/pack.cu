@@ -73,6 +73,41 @@ __global__ void gather_dverts_kernel(const float *__restrict__ face_grad, int ns
     dverts[3 * v + 2] = (float)s2;
 }
 
+// The same sum with a warp per vertex when there are many splits (small meshes on many row
+// splits): lane l takes splits l, l + 32, ... of every incident (face, corner) in CSR order, then
+// a fixed butterfly over the lanes; deterministic for a given split count.
+__global__ void gather_dverts_warp_kernel(const float *__restrict__ face_grad, int nsplit, int64_t nf,
+                                          const int32_t *__restrict__ vtx_ptr,
+                                          const int32_t *__restrict__ vtx_corner, int64_t nv,
+                                          float *__restrict__ dverts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {  // whole warps
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int32_t c = vtx_ptr[v]; c < vtx_ptr[v + 1]; ++c) {
+            const int32_t corner = vtx_corner[c];
+            const int64_t f = corner / 3;
+            const int k = corner - 3 * (int)f;
+            for (int s = lane; s < nsplit; s += 32) {
+                const float *g = face_grad + ((int64_t)s * nf + f) * 9 + 3 * k;
+                s0 += (double)g[0];
+                s1 += (double)g[1];
+                s2 += (double)g[2];
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            dverts[3 * v + 0] = (float)s0;
+            dverts[3 * v + 1] = (float)s1;
+            dverts[3 * v + 2] = (float)s2;
+        }
+    }
+}
+
 static int blocks_for(int64_t n, int threads, int64_t cap = 1 << 20) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -185,7 +220,12 @@ cudaError_t launch_gather_dverts(const double *, const float *face_grad, int nsp
                                  const int32_t *vtx_ptr, const int32_t *vtx_corner, int64_t nv, float *dverts,
                                  cudaStream_t s) {
     prof_begin("gather_dverts", s);
-    gather_dverts_kernel<<<blocks_for(nv, 256), 256, 0, s>>>(face_grad, nsplit, nf, vtx_ptr, vtx_corner, nv, dverts);
+    if (nsplit > 32)
+        gather_dverts_warp_kernel<<<blocks_for(nv * 32, 256), 256, 0, s>>>(face_grad, nsplit, nf, vtx_ptr, vtx_corner,
+                                                                         nv, dverts);
+    else
+        gather_dverts_kernel<<<blocks_for(nv, 256), 256, 0, s>>>(face_grad, nsplit, nf, vtx_ptr, vtx_corner, nv,
+                                                                 dverts);
     count_launch();
     prof_end("gather_dverts", s);
     return cudaGetLastError();
