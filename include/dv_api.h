@@ -36,7 +36,9 @@
  *     and so must backward calls; a forward and a backward on the same mesh use
  *     separate scratch and may run concurrently on two streams once the mesh
  *     is packed and its scratch reserved (dv_mesh_reserve). Different meshes are
- *     independent.
+ *     independent. Calls on one mesh come from one host thread at a time (the
+ *     mesh's host state, such as grown scratch or the boundary edges built on
+ *     first use, is not locked).
  */
 #ifndef DV_API_H
 #define DV_API_H

@@ -69,6 +69,20 @@ def test_grid_gradient_face_pairs_mixed_orientation(cuda_device, grid_n):
     grad_close(G, G_ref, f"pairs mixed orientation {grid_n}", oracle.winding_grad_scale(V, F, Q, g))
 
 
+def test_grid_gradient_rows_longer_than_the_window(cuda_device):
+    """Rows of 2101 and 4100 voxels (longer than the 2048-query staging window): they go through
+    the kernel in pieces on the guarded path, for paired and single faces alike."""
+    V, F = meshgen.jittered_torus(nu=24, nv=12, sigma=0.01, delete_frac=0.1, seed=3)
+    for n in ((2101, 3, 2), (4100, 2, 1)):
+        grid = dv.Grid(n, (-1.0, -0.3, -0.05), (1.0, 0.3, 0.05))
+        Q, _, d = oracle_grid(V, F, grid)
+        g = _masked_upstream(len(Q), d, seed=13)
+        G_ref = oracle.winding_grad(V, F, Q, g)
+        mesh = make_mesh(V, F, cuda_device)
+        G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+        grad_close(G, G_ref, f"long rows {n}", oracle.winding_grad_scale(V, F, Q, g))
+
+
 def test_grid_gradient_vertices_on_cell_centres(cuda_device):
     """Mesh vertices placed exactly on voxel centres (as the kernels compute them in FP32): the
     packed sums of those rows are not finite, so paired and single faces alike take the guarded
