@@ -50,7 +50,7 @@ EXEC_BWD_PAIRED = 38.5
 # counters no longer describe the kernel and the bench line reports traffic as null.
 TRAFFIC = {
     ("torus_128", "bwd_grid"): (10864640, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "81f84345211f3a0dc5eb1093e769185cc6675de8e62ea0c64c58df9236ed0bb9"),
+                                "30415bb40333c29cd5621d74789d30ce4e0652007c4d5eec2ab888465c347e9a"),
 }
 
 WORKLOADS = {

@@ -19,9 +19,9 @@
 //   dL/dv2 = k [-e1 x U_cD - T_P e1 - T_ac e2 - U_c],   k = 1/(2 pi).
 // On a grid row (fixed y, z) the y and z parts of a are constant, so the sums over a row are
 // kept as 7 scalars and their x-weighted versions (14 FMAs per pair) and folded per row.
-// On the grid, a thread owns two faces that share an edge (consecutive faces of a strip, paired
-// on the host): per query the four vertex distances (one MUFU reciprocal square root each) and
-// the five edge dots serve both faces; the faces left unpaired run one per thread.
+// A thread owns two faces that share an edge (consecutive faces of a strip, paired on the host):
+// per query the four vertex distances (one MUFU reciprocal square root each) and the five edge
+// dots serve both faces; the faces left unpaired run one per thread (grid and list paths).
 // Per-face sums are FP32 with Kahan compensation; per-split face gradients are summed over
 // splits and incident faces in FP64 by the gather kernel (pack.cu), in a fixed order.
 #include <math.h>
@@ -512,25 +512,11 @@ struct FaceL2 {
     float2 v0x, v0y, v0z, v1x, v1y, v1z, v2x, v2y, v2z, nx, ny, nz;
 };
 
-__device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float4 q1, float2 (&T)[6],
-                                               float2 (&U)[4][3]) {
-    // window entries are (-x, -y, -z, g)
-    const float2 nqx = make_float2(q0.x, q1.x), nqy = make_float2(q0.y, q1.y), nqz = make_float2(q0.z, q1.z);
-    const float2 g = make_float2(q0.w, q1.w);
-    const float2 ax = __fadd2_rn(F.v0x, nqx), ay = __fadd2_rn(F.v0y, nqy), az = __fadd2_rn(F.v0z, nqz);
-    const float2 bx = __fadd2_rn(F.v1x, nqx), by = __fadd2_rn(F.v1y, nqy), bz = __fadd2_rn(F.v1z, nqz);
-    const float2 cx = __fadd2_rn(F.v2x, nqx), cy = __fadd2_rn(F.v2y, nqy), cz = __fadd2_rn(F.v2z, nqz);
-    const float2 la2 = __ffma2_rn(az, az, __ffma2_rn(ay, ay, __fmul2_rn(ax, ax)));
-    const float2 lb2 = __ffma2_rn(bz, bz, __ffma2_rn(by, by, __fmul2_rn(bx, bx)));
-    const float2 lc2 = __ffma2_rn(cz, cz, __ffma2_rn(cy, cy, __fmul2_rn(cx, cx)));
-    const float2 ia = make_float2(rsqrt_approx(la2.x), rsqrt_approx(la2.y));
-    const float2 ib = make_float2(rsqrt_approx(lb2.x), rsqrt_approx(lb2.y));
-    const float2 ic = make_float2(rsqrt_approx(lc2.x), rsqrt_approx(lc2.y));
-    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
-    const float2 ab = __ffma2_rn(az, bz, __ffma2_rn(ay, by, __fmul2_rn(ax, bx)));
-    const float2 bcd = __ffma2_rn(bz, cz, __ffma2_rn(by, cy, __fmul2_rn(bx, cx)));
-    const float2 ca = __ffma2_rn(cz, az, __ffma2_rn(cy, ay, __fmul2_rn(cx, ax)));
-    const float2 N = __ffma2_rn(az, F.nz, __ffma2_rn(ay, F.ny, __fmul2_rn(ax, F.nx)));
+// The list-path adjoint terms of one face for two queries, from the distances, their reciprocals,
+// the edge dots, N and the offsets (ax, ay, az) of the face's first vertex.
+__device__ __forceinline__ void list_face2(float2 la, float2 lb, float2 lc, float2 ia, float2 ib, float2 ic,
+                                           float2 ab, float2 bcd, float2 ca, float2 N, float2 ax, float2 ay,
+                                           float2 az, float2 g, float2 (&T)[6], float2 (&U)[4][3]) {
     const float2 tc = __ffma2_rn(la, lb, ab);
     float2 D = __fmul2_rn(tc, lc);
     D = __ffma2_rn(la, bcd, D);
@@ -559,20 +545,86 @@ __device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float
     }
 }
 
-__global__ void __launch_bounds__(kBwdThreads, 4) bwd_list_kernel(const BwdArgs a) {
-    __shared__ float4 win[kBwdWin / 2];  // (-x, -y, -z, g), padded to an even count with g = 0
-    __shared__ float2 ks[kFaceSlots][kBwdThreads];
-    const int64_t f = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    const FaceF F = load_face(a.rec, f < a.nf ? f : a.nf - 1);
-    FaceL2 F2;
-    F2.v0x = bc2(F.v0x); F2.v0y = bc2(F.v0y); F2.v0z = bc2(F.v0z);
-    F2.v1x = bc2(F.v1x); F2.v1y = bc2(F.v1y); F2.v1z = bc2(F.v1z);
-    F2.v2x = bc2(F.v2x); F2.v2y = bc2(F.v2y); F2.v2z = bc2(F.v2z);
-    F2.nx = bc2(F.nx); F2.ny = bc2(F.ny); F2.nz = bc2(F.nz);
+__device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float4 q1, float2 (&T)[6],
+                                               float2 (&U)[4][3]) {
+    // window entries are (-x, -y, -z, g)
+    const float2 nqx = make_float2(q0.x, q1.x), nqy = make_float2(q0.y, q1.y), nqz = make_float2(q0.z, q1.z);
+    const float2 g = make_float2(q0.w, q1.w);
+    const float2 ax = __fadd2_rn(F.v0x, nqx), ay = __fadd2_rn(F.v0y, nqy), az = __fadd2_rn(F.v0z, nqz);
+    const float2 bx = __fadd2_rn(F.v1x, nqx), by = __fadd2_rn(F.v1y, nqy), bz = __fadd2_rn(F.v1z, nqz);
+    const float2 cx = __fadd2_rn(F.v2x, nqx), cy = __fadd2_rn(F.v2y, nqy), cz = __fadd2_rn(F.v2z, nqz);
+    const float2 la2 = __ffma2_rn(az, az, __ffma2_rn(ay, ay, __fmul2_rn(ax, ax)));
+    const float2 lb2 = __ffma2_rn(bz, bz, __ffma2_rn(by, by, __fmul2_rn(bx, bx)));
+    const float2 lc2 = __ffma2_rn(cz, cz, __ffma2_rn(cy, cy, __fmul2_rn(cx, cx)));
+    const float2 ia = rsqrt2(la2), ib = rsqrt2(lb2), ic = rsqrt2(lc2);
+    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
+    const float2 ab = __ffma2_rn(az, bz, __ffma2_rn(ay, by, __fmul2_rn(ax, bx)));
+    const float2 bcd = __ffma2_rn(bz, cz, __ffma2_rn(by, cy, __fmul2_rn(bx, cx)));
+    const float2 ca = __ffma2_rn(cz, az, __ffma2_rn(cy, ay, __fmul2_rn(cx, ax)));
+    const float2 N = __ffma2_rn(az, F.nz, __ffma2_rn(ay, F.ny, __fmul2_rn(ax, F.nx)));
+    list_face2(la, lb, lc, ia, ib, ic, ab, bcd, ca, N, ax, ay, az, g, T, U);
+}
+
+// Two edge-sharing faces (A = (p0, p1, p2), B = (p2, p1, p3)) against two queries: four distances
+// and five dots for both faces.
+struct PairL2 {
+    float2 x[4], y[4], z[4];
+    float2 nA[3], nB[3];
+};
+
+__device__ __forceinline__ PairL2 pair_l2(const PairRec &P) {
+    PairL2 Q;
+    const float4 r[4] = {P.r0, P.r1, P.r2, P.r3};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        Q.x[i] = bc2(r[i].x);
+        Q.y[i] = bc2(r[i].y);
+        Q.z[i] = bc2(r[i].z);
+    }
+    Q.nA[0] = bc2(P.r0.w);
+    Q.nA[1] = bc2(P.r1.w);
+    Q.nA[2] = bc2(P.r2.w);
+    Q.nB[0] = bc2(P.r3.w);
+    Q.nB[1] = bc2(P.r4.x);
+    Q.nB[2] = bc2(P.r4.y);
+    return Q;
+}
+
+__device__ __forceinline__ float2 dot2(float2 ax, float2 ay, float2 az, float2 bx, float2 by, float2 bz) {
+    return __ffma2_rn(az, bz, __ffma2_rn(ay, by, __fmul2_rn(ax, bx)));
+}
+
+__device__ __forceinline__ void bwd_list_quad2(const PairL2 &P, float4 q0, float4 q1, float2 (&TA)[6],
+                                               float2 (&UA)[4][3], float2 (&TB)[6], float2 (&UB)[4][3]) {
+    const float2 nqx = make_float2(q0.x, q1.x), nqy = make_float2(q0.y, q1.y), nqz = make_float2(q0.z, q1.z);
+    const float2 g = make_float2(q0.w, q1.w);
+    float2 x[4], y[4], z[4], l[4], r[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        x[i] = __fadd2_rn(P.x[i], nqx);
+        y[i] = __fadd2_rn(P.y[i], nqy);
+        z[i] = __fadd2_rn(P.z[i], nqz);
+        const float2 m = dot2(x[i], y[i], z[i], x[i], y[i], z[i]);
+        r[i] = rsqrt2(m);
+        l[i] = __fmul2_rn(m, r[i]);
+    }
+    const float2 d01 = dot2(x[0], y[0], z[0], x[1], y[1], z[1]);
+    const float2 d12 = dot2(x[1], y[1], z[1], x[2], y[2], z[2]);
+    const float2 d20 = dot2(x[2], y[2], z[2], x[0], y[0], z[0]);
+    const float2 d13 = dot2(x[1], y[1], z[1], x[3], y[3], z[3]);
+    const float2 d32 = dot2(x[3], y[3], z[3], x[2], y[2], z[2]);
+    const float2 NA = dot2(x[0], y[0], z[0], P.nA[0], P.nA[1], P.nA[2]);
+    const float2 NB = dot2(x[2], y[2], z[2], P.nB[0], P.nB[1], P.nB[2]);
+    list_face2(l[0], l[1], l[2], r[0], r[1], r[2], d01, d12, d20, NA, x[0], y[0], z[0], g, TA, UA);
+    list_face2(l[2], l[1], l[3], r[2], r[1], r[3], d12, d13, d32, NB, x[2], y[2], z[2], g, TB, UB);
+}
+
+// Query windows of a split (padded to an even count with g = 0), in chunks of kListChunk
+// queries: visit(c0, c1, len) for window entries c0 .. c1 - 1 (entries >= len are padding).
+template <typename ChunkFn>
+__device__ __forceinline__ void for_each_chunk(const BwdArgs &a, float4 *win, ChunkFn &&visit) {
     const int64_t q0 = (int64_t)blockIdx.y * a.rows_per_split;
     const int64_t q1 = q0 + a.rows_per_split < a.nq ? q0 + a.rows_per_split : a.nq;
-#pragma unroll
-    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
     for (int64_t w0 = q0; w0 < q1; w0 += kBwdWin / 2) {
         const int len = (int)(q1 - w0 < kBwdWin / 2 ? q1 - w0 : kBwdWin / 2);
         const int len2 = (len + 1) & ~1;
@@ -583,47 +635,124 @@ __global__ void __launch_bounds__(kBwdThreads, 4) bwd_list_kernel(const BwdArgs 
                                  i < len ? a.upstream[k] : 0.0f);
         }
         __syncthreads();
-        for (int c0 = 0; c0 < len2; c0 += kListChunk) {
-            const int c1 = c0 + kListChunk < len2 ? c0 + kListChunk : len2;
-            float2 T[6], U[4][3];
-#pragma unroll
-            for (int k = 0; k < 6; ++k) T[k] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) U[i][0] = U[i][1] = U[i][2] = make_float2(0.f, 0.f);
-#pragma unroll 2
-            for (int i = c0; i < c1; i += 2) bwd_list_pair2(F2, win[i], win[i + 1], T, U);
-            float t = 0.f;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) t += T[k].x + T[k].y;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) t += U[i][0].x + U[i][0].y + U[i][1].x + U[i][1].y + U[i][2].x + U[i][2].y;
-            if (isfinite(t)) {
-                const int th = threadIdx.x;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) kahan_sm(&ks[k][th], T[k].x + T[k].y);
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) kahan_sm(&ks[6 + 3 * i + j][th], U[i][j].x + U[i][j].y);
-            } else {
-                // guarded scalar recompute of this chunk, one query at a time
-                const int ce = c1 < len ? c1 : len;
-                for (int i = c0; i < ce; ++i) {
-                    const float4 q = win[i];
-                    const RowB R = row_b(F, -q.y, -q.z);
-                    float S[7], X[7];
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-                    bwd_pair<true>(F, R, -q.x, q.w, S, X);
-                    fold_sm(ks, S, X, R.ay, R.az);
-                }
-            }
-        }
+        for (int c0 = 0; c0 < len2; c0 += kListChunk)
+            visit(c0, c0 + kListChunk < len2 ? c0 + kListChunk : len2, len);
     }
-    if (f < a.nf) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
-// Once per device (mesh creation calls it, outside any stream capture): the grid kernel's
+__device__ __forceinline__ bool finite_tu(const float2 (&T)[6], const float2 (&U)[4][3]) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) t += T[k].x + T[k].y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t += U[i][0].x + U[i][0].y + U[i][1].x + U[i][1].y + U[i][2].x + U[i][2].y;
+    return isfinite(t);
+}
+
+__device__ __forceinline__ void fold_list(float2 (*ks)[kBwdThreads], const float2 (&T)[6], const float2 (&U)[4][3]) {
+    const int th = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) kahan_sm(&ks[k][th], T[k].x + T[k].y);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) kahan_sm(&ks[6 + 3 * i + j][th], U[i][j].x + U[i][j].y);
+}
+
+// Guarded scalar recompute of one chunk for one face, one query at a time (a chunk whose packed
+// sums are not finite: a query on a vertex or an edge line).
+__device__ __noinline__ void list_guarded(const FaceF F, const float4 *win, int c0, int ce,
+                                          float2 (*ks)[kBwdThreads]) {
+    for (int i = c0; i < ce; ++i) {
+        const float4 q = win[i];
+        const RowB R = row_b(F, -q.y, -q.z);
+        float S[7], X[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
+        bwd_pair<true>(F, R, -q.x, q.w, S, X);
+        fold_sm(ks, S, X, R.ay, R.az);
+    }
+}
+
+__device__ __forceinline__ void bwd_list_singles(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads]) {
+    const int64_t count = a.singles ? a.nsingle : a.nf;
+    const int64_t idx = ((int64_t)blockIdx.x - a.pblocks) * kBwdThreads + threadIdx.x;
+    const int64_t ic = idx < count ? idx : count - 1;
+    const int64_t f = a.singles ? (int64_t)a.singles[ic] : ic;
+    const FaceF F = load_face(a.rec, f);
+    FaceL2 F2;
+    F2.v0x = bc2(F.v0x); F2.v0y = bc2(F.v0y); F2.v0z = bc2(F.v0z);
+    F2.v1x = bc2(F.v1x); F2.v1y = bc2(F.v1y); F2.v1z = bc2(F.v1z);
+    F2.v2x = bc2(F.v2x); F2.v2y = bc2(F.v2y); F2.v2z = bc2(F.v2z);
+    F2.nx = bc2(F.nx); F2.ny = bc2(F.ny); F2.nz = bc2(F.nz);
+#pragma unroll
+    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
+    for_each_chunk(a, win, [&](int c0, int c1, int len) {
+        float2 T[6], U[4][3];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) T[k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) U[i][0] = U[i][1] = U[i][2] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int i = c0; i < c1; i += 2) bwd_list_pair2(F2, win[i], win[i + 1], T, U);
+        if (finite_tu(T, U))
+            fold_list(ks, T, U);
+        else
+            list_guarded(F, win, c0, c1 < len ? c1 : len, ks);
+    });
+    if (idx < count) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+}
+
+__device__ __forceinline__ void bwd_list_pairs(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads]) {
+    const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    const int64_t ic = idx < a.np ? idx : a.np - 1;
+    const PairRec P = a.prec[ic];
+    const PairL2 P2 = pair_l2(P);
+    float2(*ksB)[kBwdThreads] = ks + kFaceSlots;
+#pragma unroll
+    for (int k = 0; k < 2 * kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
+    for_each_chunk(a, win, [&](int c0, int c1, int len) {
+        float2 TA[6], UA[4][3], TB[6], UB[4][3];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) TA[k] = TB[k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) UA[i][0] = UA[i][1] = UA[i][2] = UB[i][0] = UB[i][1] = UB[i][2] = make_float2(0.f, 0.f);
+        for (int i = c0; i < c1; i += 2) bwd_list_quad2(P2, win[i], win[i + 1], TA, UA, TB, UB);
+        const int ce = c1 < len ? c1 : len;
+        if (finite_tu(TA, UA))
+            fold_list(ks, TA, UA);
+        else
+            list_guarded(pair_face(P, 0), win, c0, ce, ks);
+        if (finite_tu(TB, UB))
+            fold_list(ksB, TB, UB);
+        else
+            list_guarded(pair_face(P, 1), win, c0, ce, ksB);
+    });
+    if (idx < a.np) {
+        const int32_t *t = a.ptopo + 8 * idx;
+        const int code = t[6];
+        float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
+        write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
+        write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
+                           (code >> 12) & 1 ? -1.0 : 1.0);
+    }
+}
+
+// List adjoint: CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces. Dynamic
+// shared memory: the query window, then 2 x 18 face-sum slots per thread.
+constexpr size_t kBwdListSmem = sizeof(float4) * (kBwdWin / 2) + sizeof(float2) * 2 * kFaceSlots * kBwdThreads;
+
+__global__ void __launch_bounds__(kBwdThreads, 3) bwd_list_kernel(const BwdArgs a) {
+    extern __shared__ __align__(16) float4 bwd_list_smem[];
+    float4 *win = bwd_list_smem;
+    float2(*ks)[kBwdThreads] = reinterpret_cast<float2(*)[kBwdThreads]>(bwd_list_smem + kBwdWin / 2);
+    if ((int64_t)blockIdx.x < a.pblocks)
+        bwd_list_pairs(a, win, ks);
+    else
+        bwd_list_singles(a, win, ks);
+}
+
+// Once per device (mesh creation calls it, outside any stream capture): the adjoint kernels'
 // dynamic shared memory exceeds the 48 KB default.
 cudaError_t prepare_backward_kernels() {
     static std::atomic<uint64_t> smem_set{0};
@@ -633,6 +762,8 @@ cudaError_t prepare_backward_kernels() {
     const uint64_t bit = 1ull << (dev & 63);
     if (smem_set.load() & bit) return cudaSuccess;
     e = cudaFuncSetAttribute(bwd_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdGridSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(bwd_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdListSmem);
     if (e == cudaSuccess) smem_set.fetch_or(bit);
     return e;
 }
@@ -640,7 +771,7 @@ cudaError_t prepare_backward_kernels() {
 BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g, int num_sms) {
     BwdPlan p{};
     p.threads = kBwdThreads;
-    if (grid && fc.prec) {
+    if (fc.prec) {
         p.pblocks = (fc.np + kBwdThreads - 1) / kBwdThreads;
         p.fblocks = p.pblocks + (fc.nsingle + kBwdThreads - 1) / kBwdThreads;
     } else {
@@ -685,13 +816,11 @@ cudaError_t launch_backward(const BwdPlan &p, const BwdFaces &fc, const GridF *g
     }
     dim3 grid((unsigned)p.fblocks, (unsigned)p.nsplit);
     const char *name = queries ? "bwd_list" : "bwd_grid";
-    if (!queries) {
-        const cudaError_t e = prepare_backward_kernels();
-        if (e != cudaSuccess) return e;
-    }
+    const cudaError_t e = prepare_backward_kernels();
+    if (e != cudaSuccess) return e;
     prof_begin(name, ctx.stream);
     if (queries)
-        bwd_list_kernel<<<grid, kBwdThreads, 0, ctx.stream>>>(a);
+        bwd_list_kernel<<<grid, kBwdThreads, kBwdListSmem, ctx.stream>>>(a);
     else
         bwd_grid_kernel<<<grid, kBwdThreads, kBwdGridSmem, ctx.stream>>>(a);
     count_launch();
