@@ -745,13 +745,11 @@ __device__ __forceinline__ void list_nd(const StripRec &r, const ListSlot<QP> &P
     D = __ffma2_rn(P1.l[j], d2, D);
 }
 
-template <int QP, bool FACE>
-__device__ __forceinline__ void list_event(const StripRec &r, const float2 (&nq)[QP][3], const ListSlot<QP> &P2,
-                                           const ListSlot<QP> &P1, ListSlot<QP> &V, float2 (&acc)[QP]) {
+// Vertex part of a list event (offsets, |V - q|, dot with the previous vertex P1).
+template <int QP>
+__device__ __forceinline__ void list_vertex(const StripRec &r, const float2 (&nq)[QP][3], const ListSlot<QP> &P1,
+                                            ListSlot<QP> &V) {
     const float2 vx = make_float2(r.p.x, r.p.x), vy = make_float2(r.p.y, r.p.y), vz = make_float2(r.p.z, r.p.z);
-    const float2 C0 = make_float2(DV_ATAN_C0, DV_ATAN_C0), C1 = make_float2(DV_ATAN_C1, DV_ATAN_C1);
-    const float2 C2 = make_float2(DV_ATAN_C2, DV_ATAN_C2);
-    bool ok = true;
 #pragma unroll
     for (int j = 0; j < QP; ++j) {
         V.ax[j] = __fadd2_rn(vx, nq[j][0]);
@@ -764,20 +762,30 @@ __device__ __forceinline__ void list_event(const StripRec &r, const float2 (&nq)
         float2 e = __fmul2_rn(V.ax[j], P1.ax[j]);
         e = __ffma2_rn(V.ay[j], P1.ay[j], e);
         V.e[j] = __ffma2_rn(V.az[j], P1.az[j], e);
-        if (FACE) {
-            float2 N8, D;
-            list_nd<QP>(r, P2, P1, V, j, N8, D);
-            const bool p0 = D.x > fabsf(N8.x), p1 = D.y > fabsf(N8.y);
-            ok = ok && p0 && p1;
-            float2 v = __fmul2_rn(N8, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
-            v.x = p0 ? v.x : 0.0f;
-            v.y = p1 ? v.y : 0.0f;
-            const float2 sq = __fmul2_rn(v, v);
-            const float2 P = __ffma2_rn(__ffma2_rn(C2, sq, C1), sq, C0);
-            acc[j] = __ffma2_rn(v, P, acc[j]);
-        }
     }
-    if (FACE && __any_sync(kFull, !ok)) {
+}
+
+// Face part of a list event: fast path, and the slow path when any lane needs it.
+template <int QP>
+__device__ __forceinline__ void list_face(const StripRec &r, const ListSlot<QP> &P2, const ListSlot<QP> &P1,
+                                          const ListSlot<QP> &V, float2 (&acc)[QP]) {
+    const float2 C0 = make_float2(DV_ATAN_C0, DV_ATAN_C0), C1 = make_float2(DV_ATAN_C1, DV_ATAN_C1);
+    const float2 C2 = make_float2(DV_ATAN_C2, DV_ATAN_C2);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < QP; ++j) {
+        float2 N8, D;
+        list_nd<QP>(r, P2, P1, V, j, N8, D);
+        const bool p0 = D.x > fabsf(N8.x), p1 = D.y > fabsf(N8.y);
+        ok = ok && p0 && p1;
+        float2 v = __fmul2_rn(N8, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
+        v.x = p0 ? v.x : 0.0f;
+        v.y = p1 ? v.y : 0.0f;
+        const float2 sq = __fmul2_rn(v, v);
+        const float2 P = __ffma2_rn(__ffma2_rn(C2, sq, C1), sq, C0);
+        acc[j] = __ffma2_rn(v, P, acc[j]);
+    }
+    if (__any_sync(kFull, !ok)) {
 #pragma unroll
         for (int j = 0; j < QP; ++j) {
             float2 N8, D;
@@ -790,14 +798,18 @@ __device__ __forceinline__ void list_event(const StripRec &r, const float2 (&nq)
     }
 }
 
+// Software-pipelined step: face part of event r (if it completes a face), then the vertex part
+// of the next event rn into P2's slot.
 template <int QP>
-__device__ __forceinline__ void list_step(const StripRec &r, bool face, const float2 (&nq)[QP][3],
-                                          const ListSlot<QP> &P2, const ListSlot<QP> &P1, ListSlot<QP> &V,
-                                          float2 (&acc)[QP]) {
-    if (face)
-        list_event<QP, true>(r, nq, P2, P1, V, acc);
-    else
-        list_event<QP, false>(r, nq, P2, P1, V, acc);
+__device__ __forceinline__ void list_pstep(const StripRec &r, bool face, const StripRec &rn,
+                                           const float2 (&nq)[QP][3], ListSlot<QP> &P2, const ListSlot<QP> &P1,
+                                           const ListSlot<QP> &V, float2 (&acc)[QP]) {
+    if (face) {
+        list_face<QP>(r, P2, P1, V, acc);
+        list_vertex<QP>(rn, nq, V, P2);
+    } else {
+        list_vertex<QP>(rn, nq, V, P2);
+    }
 }
 
 template <int QP, bool KAHAN>
@@ -846,21 +858,36 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_list_strip_kernel(const 
     run_face_tiles(
         pp, a.err,
         [&](const StripRec *tilep, int cnt) {
-            // roles on entry: S1 = P2, S2 = P1 (the two most recent vertices)
+            // roles on entry: S1 = P2, S2 = P1 (the two most recent vertices); event k goes to
+            // slot k mod 3, and step k finishes event k's face and computes event k + 1's vertex
+            list_vertex<QP>(tilep[0], nq, S2, S0);
+            int k = 0;
 #pragma unroll 1
-            for (int k = 0; k < cnt; k += 3) {
-                {
-                    const StripRec r = tilep[k];
-                    list_step<QP>(r, r.q.z != 0.0f && k >= first, nq, S1, S2, S0, acc);
-                }
-                if (k + 1 < cnt) {
-                    const StripRec r = tilep[k + 1];
-                    list_step<QP>(r, r.q.z != 0.0f && k + 1 >= first, nq, S2, S0, S1, acc);
-                }
-                if (k + 2 < cnt) {
-                    const StripRec r = tilep[k + 2];
-                    list_step<QP>(r, r.q.z != 0.0f, nq, S0, S1, S2, acc);
-                }
+            for (; k + 3 < cnt; k += 3) {
+                list_pstep<QP>(tilep[k], tilep[k].q.z != 0.0f && k >= first, tilep[k + 1], nq, S1, S2, S0, acc);
+                list_pstep<QP>(tilep[k + 1], tilep[k + 1].q.z != 0.0f && k + 1 >= first, tilep[k + 2], nq, S2, S0,
+                               S1, acc);
+                list_pstep<QP>(tilep[k + 2], tilep[k + 2].q.z != 0.0f, tilep[k + 3], nq, S0, S1, S2, acc);
+            }
+            {
+                const StripRec r = tilep[k];
+                const bool face = r.q.z != 0.0f && k >= first;
+                if (k + 1 < cnt)
+                    list_pstep<QP>(r, face, tilep[k + 1], nq, S1, S2, S0, acc);
+                else if (face)
+                    list_face<QP>(r, S1, S2, S0, acc);
+            }
+            if (k + 1 < cnt) {
+                const StripRec r = tilep[k + 1];
+                const bool face = r.q.z != 0.0f && k + 1 >= first;
+                if (k + 2 < cnt)
+                    list_pstep<QP>(r, face, tilep[k + 2], nq, S2, S0, S1, acc);
+                else if (face)
+                    list_face<QP>(r, S2, S0, S1, acc);
+            }
+            if (k + 2 < cnt) {
+                const StripRec r = tilep[k + 2];
+                if (r.q.z != 0.0f) list_face<QP>(r, S0, S1, S2, acc);
             }
             first = 0;
         },
