@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from _util import NEAR, check_forward, make_mesh, oracle_grid, to_dev
+from _util import NEAR, check_forward, grad_close, make_mesh, oracle_grid, to_dev
 from paper_2407_11272_b300 import dv, meshgen
 
 pytestmark = pytest.mark.gpu
@@ -58,6 +58,27 @@ def test_ragged_face_counts_and_odd_grid(cuda_device, nfaces):
     for prec in ("fp32", "mixed"):
         w, occ, _ = dv.dv_voxelize_grid(mesh, grid, precision=prec)
         check_forward(w.cpu().numpy(), w64, d, prec, occ.cpu().numpy(), f"ragged{nfaces}")
+
+
+@pytest.mark.parametrize("nfaces", [1, 2, 63, 65, 129])
+def test_ragged_face_counts_list_path(cuda_device, nfaces):
+    """Query lists (odd count) against meshes whose strip events end mid-tile and mid-step of the
+    software-pipelined event loop, and the list adjoint on the same inputs."""
+    V, F = meshgen.jittered_torus(nu=20, nv=10, sigma=0.01, delete_frac=0.0, seed=1)
+    F = F[:nfaces]
+    rng = np.random.default_rng(nfaces)
+    Q = rng.uniform(-1, 1, size=(1001, 3)).astype(np.float32)
+    w64 = oracle.winding(V, F, Q)
+    d = oracle.point_mesh_distance(V, F, Q)
+    mesh = make_mesh(V, F, cuda_device)
+    for prec in ("fp32", "kahan", "mixed"):
+        w = dv.dv_winding(mesh, queries=to_dev(Q, cuda_device), precision=prec)
+        check_forward(w.cpu().numpy(), w64, d, prec, None, f"list ragged{nfaces}")
+    g = meshgen.upstream_gradient(len(Q), seed=3).astype(np.float64)
+    g[d <= NEAR] = 0.0
+    G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), queries=to_dev(Q, cuda_device))
+    grad_close(G.cpu().numpy(), oracle.winding_grad(V, F, Q, g), f"list ragged{nfaces} adjoint",
+               oracle.winding_grad_scale(V, F, Q, g))
 
 
 @pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 5), (9, 1, 7), (130, 3, 2)])
