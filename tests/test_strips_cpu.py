@@ -131,3 +131,21 @@ def test_face_pairs_reversed_orientation():
     _check_pairs(F, pairs, singles)
     rev = (pairs[:, 6] >> 12) & 1
     assert 0 < rev.sum() < len(pairs)
+
+
+def test_face_pairs_random_meshes():
+    """Random face sets over small vertex sets (shared, non-manifold, repeated and degenerate
+    faces, both orientations): the pairing invariants hold on every one."""
+    rng = np.random.default_rng(123)
+    for trial in range(60):
+        nv = int(rng.integers(3, 40))
+        nf = int(rng.integers(1, 120))
+        F = rng.integers(0, nv, size=(nf, 3)).astype(np.int32)
+        pairs, singles = dv.dv_build_face_pairs(F, nv)
+        _check_pairs(F, pairs, singles)
+        ev_vert, ev_face = dv.dv_build_strips(F, nv)
+        _check_order(F, ev_vert, ev_face)
+    # a closed surface with consistently oriented faces: every pair is consistent (no bit 12)
+    V, F = meshgen.icosphere(2, 0.7)
+    pairs, _ = dv.dv_build_face_pairs(F, len(V))
+    assert np.all(((pairs[:, 6] >> 12) & 1) == 0)
