@@ -141,7 +141,9 @@ __device__ __forceinline__ float2 rsqrt2(float2 v) { return make_float2(rsqrt_ap
 __device__ __forceinline__ void bwd_face2(float2 la, float2 lb, float2 lc, float2 ia, float2 ib, float2 ic,
                                           float2 ab, float2 bc, float2 ca, float2 N, float2 ax, float2 g,
                                           float2 (&S)[7], float2 (&X)[7]) {
-    const float2 tc = __ffma2_rn(la, lb, ab);
+    // |a||b| + a.b, written lb * la so that for two faces sharing the edge (a, b) = (c', b') it is
+    // the same expression as the other face's lb * lc + b.c (one computation after CSE)
+    const float2 tc = __ffma2_rn(lb, la, ab);
     float2 D = __fmul2_rn(tc, lc);
     D = __ffma2_rn(la, bc, D);
     D = __ffma2_rn(lb, ca, D);
@@ -517,7 +519,7 @@ struct FaceL2 {
 __device__ __forceinline__ void list_face2(float2 la, float2 lb, float2 lc, float2 ia, float2 ib, float2 ic,
                                            float2 ab, float2 bcd, float2 ca, float2 N, float2 ax, float2 ay,
                                            float2 az, float2 g, float2 (&T)[6], float2 (&U)[4][3]) {
-    const float2 tc = __ffma2_rn(la, lb, ab);
+    const float2 tc = __ffma2_rn(lb, la, ab);  // operand order as in bwd_face2
     float2 D = __fmul2_rn(tc, lc);
     D = __ffma2_rn(la, bcd, D);
     D = __ffma2_rn(lb, ca, D);
