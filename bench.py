@@ -50,7 +50,7 @@ EXEC_BWD_PAIRED = 38.5
 # counters no longer describe the kernel and the bench line reports traffic as null.
 TRAFFIC = {
     ("torus_128", "bwd_grid"): (11298304, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "f74e90245e1b477f07fad29c46ae397c06daa77ce4b77020957563dad8674595"),
+                                "c75ae620f598367491587bd20ef3b3ef0a233ce033780af048394ae4808abe03"),
 }
 
 WORKLOADS = {

@@ -5,8 +5,8 @@
 //   dw = (1/2pi) (D dN - N dD) / (N^2 + D^2)
 //   dN/da = b x c,  dN/db = c x a,  dN/dc = a x b
 //   dD/da = (a/|a|)(|b||c| + b.c) + b|c| + c|b|   (and cyclically)
-// No arctangent is needed. The kernel is face-parallel: each thread owns one face, streams the
-// queries (uniform across the warp), and keeps the per-face gradient as a few scalar sums.
+// No arctangent is needed. The kernels are face-parallel: a thread owns its faces (below), streams
+// the queries (uniform across the warp), and keeps each face's gradient as a few scalar sums.
 // Writing b = e1 + a, c = e2 + a (e1 = v1 - v0, e2 = v2 - v0), every per-query vector term is
 // (scalar) x a or a constant vector, so per face only these sums are needed:
 //   T_cD = sum cD, T_P = sum cN|a|, T_Q = sum cN|b|, T_R = sum cN|c|,
