@@ -221,3 +221,31 @@ def test_shsphere256_full_size_open_adjoint_sampled(cuda_device):
     G_ref = oracle.vertex_grad_subset(V, F, Q, g, ids)
     assert np.linalg.norm(G_ref[:6], axis=1).min() > 0.0
     grad_close(G, G_ref, "shsphere256 open, analytic")
+
+
+def test_forward_and_adjoint_concurrently_on_two_streams(cuda_device):
+    """A forward (mixed precision) and an adjoint of the same mesh, reserved, launched on two
+    streams at once (the header allows it): both equal the same calls made one after the other,
+    bit for bit."""
+    import torch
+
+    V, F = meshgen.jittered_torus(nu=60, nv=30, sigma=0.01, delete_frac=0.1, seed=0)
+    grid = dv.Grid.cube(40)
+    mesh = make_mesh(V, F, cuda_device)
+    dv.dv_mesh_reserve(mesh, grid)
+    g = to_dev(meshgen.upstream_gradient(grid.num_queries, seed=4), cuda_device)
+    w0, occ0, _ = dv.dv_voxelize_grid(mesh, grid, precision="mixed")
+    G0 = dv.dv_winding_backward(mesh, g, grid=grid)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = torch.cuda.Event()
+    ev.record()
+    s1.wait_event(ev)
+    s2.wait_event(ev)
+    with torch.cuda.stream(s1):
+        w1, occ1, _ = dv.dv_voxelize_grid(mesh, grid, precision="mixed", stream=s1)
+    with torch.cuda.stream(s2):
+        G1 = dv.dv_winding_backward(mesh, g, grid=grid, stream=s2)
+    torch.cuda.synchronize()
+    assert torch.equal(w0, w1) and torch.equal(occ0, occ1)
+    assert torch.equal(G0, G1)
