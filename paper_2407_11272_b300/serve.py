@@ -278,6 +278,8 @@ def main(argv=None):
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--max-inflight", type=int, default=3)
     ap.add_argument("--sub-capacity", type=float, default=0.7)
+    ap.add_argument("--sweep", type=str, default="",
+                    help="extra comma-separated fractions of the measured capacity to offer as Poisson loads")
     a = ap.parse_args(argv)
     t = time.perf_counter()
     reqs = make_workload(a.requests, a.rate, a.seed)
@@ -291,12 +293,17 @@ def main(argv=None):
     sub_rate = a.sub_capacity * cap["pairs_per_s"] / mean_pairs
     sub = make_workload(a.requests, sub_rate, a.seed)
     _, slow = srv.run(sub, realtime=True)
+    sweep = []
+    for frac in [float(x) for x in a.sweep.split(",") if x.strip()]:
+        rate = frac * cap["pairs_per_s"] / mean_pairs
+        _, st = srv.run(make_workload(a.requests, rate, a.seed), realtime=True)
+        sweep.append(dict(st, rate=rate, fraction=frac))
     offered = a.rate * mean_pairs
     print(json.dumps({"workload": f"{a.requests} requests, Poisson {a.rate} req/s (seed {a.seed}), ellipsoid unions "
                                   "F log-uniform [500, 1e5], grids {32..192}^3, 30% with dL/dV",
                       "generation_s": gen_s, "mean_pairs_per_request": mean_pairs,
                       "offered_pairs_per_s": offered, "capacity": cap, "at_rate": live,
-                      "sub_capacity": dict(slow, rate=sub_rate, fraction=a.sub_capacity)}))
+                      "sub_capacity": dict(slow, rate=sub_rate, fraction=a.sub_capacity), "sweep": sweep}))
 
 
 if __name__ == "__main__":
