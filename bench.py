@@ -50,7 +50,7 @@ EXEC_BWD_PAIRED = 38.5
 # counters no longer describe the kernel and the bench line reports traffic as null.
 TRAFFIC = {
     ("torus_128", "bwd_grid"): (11298304, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "c75ae620f598367491587bd20ef3b3ef0a233ce033780af048394ae4808abe03"),
+                                "b6c3d3a58e597cc97d82f06b22944d858cd3bc9d5611dd9cbd4ca087a86631da"),
 }
 
 WORKLOADS = {

@@ -549,9 +549,9 @@ __device__ __forceinline__ void list_face2(float2 la, float2 lb, float2 lc, floa
 
 __device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float4 q1, float2 (&T)[6],
                                                float2 (&U)[4][3]) {
-    // window entries are (-x, -y, -z, g)
-    const float2 nqx = make_float2(q0.x, q1.x), nqy = make_float2(q0.y, q1.y), nqz = make_float2(q0.z, q1.z);
-    const float2 g = make_float2(q0.w, q1.w);
+    // window entries of a pair of queries: (-x0, -x1, -y0, -y1), (-z0, -z1, g0, g1)
+    const float2 nqx = make_float2(q0.x, q0.y), nqy = make_float2(q0.z, q0.w), nqz = make_float2(q1.x, q1.y);
+    const float2 g = make_float2(q1.z, q1.w);
     const float2 ax = __fadd2_rn(F.v0x, nqx), ay = __fadd2_rn(F.v0y, nqy), az = __fadd2_rn(F.v0z, nqz);
     const float2 bx = __fadd2_rn(F.v1x, nqx), by = __fadd2_rn(F.v1y, nqy), bz = __fadd2_rn(F.v1z, nqz);
     const float2 cx = __fadd2_rn(F.v2x, nqx), cy = __fadd2_rn(F.v2y, nqy), cz = __fadd2_rn(F.v2z, nqz);
@@ -598,8 +598,8 @@ __device__ __forceinline__ float2 dot2(float2 ax, float2 ay, float2 az, float2 b
 
 __device__ __forceinline__ void bwd_list_quad2(const PairL2 &P, float4 q0, float4 q1, float2 (&TA)[6],
                                                float2 (&UA)[4][3], float2 (&TB)[6], float2 (&UB)[4][3]) {
-    const float2 nqx = make_float2(q0.x, q1.x), nqy = make_float2(q0.y, q1.y), nqz = make_float2(q0.z, q1.z);
-    const float2 g = make_float2(q0.w, q1.w);
+    const float2 nqx = make_float2(q0.x, q0.y), nqy = make_float2(q0.z, q0.w), nqz = make_float2(q1.x, q1.y);
+    const float2 g = make_float2(q1.z, q1.w);
     float2 x[4], y[4], z[4], l[4], r[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -621,6 +621,12 @@ __device__ __forceinline__ void bwd_list_quad2(const PairL2 &P, float4 q0, float
     list_face2(l[2], l[1], l[3], r[2], r[1], r[3], d12, d13, d32, NB, x[2], y[2], z[2], g, TB, UB);
 }
 
+// Query i of a window laid out in pairs: (-x, -y, -z, g).
+__device__ __forceinline__ float4 list_query(const float4 *win, int i) {
+    const float *wf = reinterpret_cast<const float *>(win) + 8 * (i >> 1) + (i & 1);
+    return make_float4(wf[0], wf[2], wf[4], wf[6]);
+}
+
 // Query windows of a split (padded to an even count with g = 0), in chunks of kListChunk
 // queries: visit(c0, c1, len) for window entries c0 .. c1 - 1 (entries >= len are padding).
 template <typename ChunkFn>
@@ -633,8 +639,11 @@ __device__ __forceinline__ void for_each_chunk(const BwdArgs &a, float4 *win, Ch
         __syncthreads();
         for (int i = threadIdx.x; i < len2; i += kBwdThreads) {
             const int64_t k = w0 + (i < len ? i : len - 1);
-            win[i] = make_float4(-a.queries[3 * k], -a.queries[3 * k + 1], -a.queries[3 * k + 2],
-                                 i < len ? a.upstream[k] : 0.0f);
+            float *wf = reinterpret_cast<float *>(win) + 8 * (i >> 1) + (i & 1);
+            wf[0] = -a.queries[3 * k];
+            wf[2] = -a.queries[3 * k + 1];
+            wf[4] = -a.queries[3 * k + 2];
+            wf[6] = i < len ? a.upstream[k] : 0.0f;
         }
         __syncthreads();
         for (int c0 = 0; c0 < len2; c0 += kListChunk)
@@ -666,7 +675,7 @@ __device__ __forceinline__ void fold_list(float2 (*ks)[kBwdThreads], const float
 __device__ __noinline__ void list_guarded(const FaceF F, const float4 *win, int c0, int ce,
                                           float2 (*ks)[kBwdThreads]) {
     for (int i = c0; i < ce; ++i) {
-        const float4 q = win[i];
+        const float4 q = list_query(win, i);
         const RowB R = row_b(F, -q.y, -q.z);
         float S[7], X[7];
 #pragma unroll
@@ -696,7 +705,7 @@ __device__ __forceinline__ void bwd_list_singles(const BwdArgs &a, float4 *win, 
 #pragma unroll
         for (int i = 0; i < 4; ++i) U[i][0] = U[i][1] = U[i][2] = make_float2(0.f, 0.f);
 #pragma unroll 2
-        for (int i = c0; i < c1; i += 2) bwd_list_pair2(F2, win[i], win[i + 1], T, U);
+        for (int i = c0; i < c1; i += 2) bwd_list_pair2(F2, win[i], win[i + 1], T, U);  // i even: one pair
         if (finite_tu(T, U))
             fold_list(ks, T, U);
         else
@@ -741,7 +750,9 @@ __device__ __forceinline__ void bwd_list_pairs(const BwdArgs &a, float4 *win, fl
 }
 
 // List adjoint: CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces. Dynamic
-// shared memory: the query window, then 2 x 18 face-sum slots per thread.
+// shared memory: the query window (consecutive queries in pairs, each pair as (-x0, -x1, -y0,
+// -y1), (-z0, -z1, g0, g1), so two 16-byte loads give the packed operands), then 2 x 18
+// face-sum slots per thread.
 constexpr size_t kBwdListSmem = sizeof(float4) * (kBwdWin / 2) + sizeof(float2) * 2 * kFaceSlots * kBwdThreads;
 
 __global__ void __launch_bounds__(kBwdThreads, 3) bwd_list_kernel(const BwdArgs a) {
