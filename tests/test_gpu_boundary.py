@@ -127,3 +127,21 @@ def test_autograd_boundary_adjoint_matches_face_adjoint(cuda_device):
     Q64, gq = Q, g.cpu().numpy().astype(np.float64)
     grad_close(grads["boundary"], grads["faces"], "autograd boundary vs faces",
                oracle.winding_grad_scale(V, F, Q64, gq))
+
+
+def test_boundary_adjoint_repacked_after_first_use(cuda_device):
+    """The boundary records are built on the first call; a later dv_mesh_update_verts repacks
+    them, so a second call sees the new vertices."""
+    V, F = meshgen.jittered_torus(nu=30, nv=15, sigma=0.0, delete_frac=0.2, seed=8)
+    V2 = (V * 0.9 + np.array([-0.01, 0.02, 0.03], dtype=np.float32)).astype(np.float32)
+    grid = dv.Grid.cube(16)
+    mesh = make_mesh(V, F, cuda_device)
+    Q, _, d1 = oracle_grid(V, F, grid)
+    g1 = _masked(len(Q), d1, seed=9)
+    G1 = dv.dv_winding_backward_boundary(mesh, to_dev(g1.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    grad_close(G1, oracle.winding_grad(V, F, Q, g1), "boundary first use", oracle.winding_grad_scale(V, F, Q, g1))
+    dv.dv_mesh_update_verts(mesh, to_dev(V2, cuda_device))
+    _, _, d2 = oracle_grid(V2, F, grid)
+    g2 = _masked(len(Q), d2, seed=10)
+    G2 = dv.dv_winding_backward_boundary(mesh, to_dev(g2.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    grad_close(G2, oracle.winding_grad(V2, F, Q, g2), "boundary after repack", oracle.winding_grad_scale(V2, F, Q, g2))

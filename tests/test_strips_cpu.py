@@ -149,3 +149,25 @@ def test_face_pairs_random_meshes():
     V, F = meshgen.icosphere(2, 0.7)
     pairs, _ = dv.dv_build_face_pairs(F, len(V))
     assert np.all(((pairs[:, 6] >> 12) & 1) == 0)
+
+
+def test_face_pairs_argument_errors():
+    """Host entry points reject bad arguments with the documented status codes."""
+    import ctypes
+
+    lib = dv.load()
+    F = np.array([[0, 1, 2], [1, 2, 3]], dtype=np.int32)
+    n_p, n_s = ctypes.c_int64(0), ctypes.c_int64(0)
+    ptr = ctypes.c_void_p(F.ctypes.data)
+    assert lib.dv_build_face_pairs(ptr, 2, 2, None, None, 0, 0, ctypes.byref(n_p), ctypes.byref(n_s)) == 1  # nv < 3
+    assert lib.dv_build_face_pairs(None, 2, 4, None, None, 0, 0, ctypes.byref(n_p), ctypes.byref(n_s)) == 1
+    bad = np.array([[0, 1, 9]], dtype=np.int32)
+    assert lib.dv_build_face_pairs(ctypes.c_void_p(bad.ctypes.data), 1, 4, None, None, 0, 0, ctypes.byref(n_p),
+                                   ctypes.byref(n_s)) == 2  # index outside [0, nv)
+    assert lib.dv_build_face_pairs(ptr, 2, 4, None, None, 0, 0, ctypes.byref(n_p), ctypes.byref(n_s)) == 0
+    assert (n_p.value, n_s.value) == (1, 0)
+    out_p = np.zeros((1, 8), np.int32)
+    out_s = np.zeros(1, np.int32)
+    # a capacity below the count
+    assert lib.dv_build_face_pairs(ptr, 2, 4, ctypes.c_void_p(out_p.ctypes.data), ctypes.c_void_p(out_s.ctypes.data),
+                                   0, 1, ctypes.byref(n_p), ctypes.byref(n_s)) == 1
