@@ -13,6 +13,8 @@
 // FP32x2 instructions.
 #include <math.h>
 
+#include <type_traits>
+
 #include "dv_internal.cuh"
 
 namespace dv {
@@ -157,9 +159,10 @@ __global__ void __launch_bounds__(kDipBwdThreads) dipole_bwd_kernel(const FaceRe
             const float rx = d.c.x - q.x, ry = d.c.y - q.y, rz = d.c.z - q.z;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             const float ir = rsqrt_approx(r2);
-            const float ir2 = r2 > 0.f ? ir * ir : 0.f;
-            const float gi3 = q.w * ir2 * ir;
-            const float t = gi3 * fmaf(d.m.x, rx, fmaf(d.m.y, ry, d.m.z * rz)) * ir2;
+            const float ir2 = ir * ir;
+            const bool at_c = !(r2 > 0.f);  // a query at the centroid contributes 0 (not 0 * inf)
+            const float gi3 = at_c ? 0.f : q.w * ir2 * ir;
+            const float t = at_c ? 0.f : gi3 * fmaf(d.m.x, rx, fmaf(d.m.y, ry, d.m.z * rz)) * ir2;
             p[0] += gi3;
             p[1] = fmaf(gi3, rx, p[1]);
             p[2] = fmaf(gi3, ry, p[2]);
@@ -226,15 +229,15 @@ __global__ void __launch_bounds__(kDipThreads, 2) dipole_fwd_grid_kernel(const F
 #pragma unroll
             for (int i = 0; i < kDipGY; ++i) {
                 const float ry = d.c.y - qy[i];
-                const float Lyz = fmaf(ry, ry, rz2), Myz = fmaf(d.m.y, ry, mzrz);
+                // + 1e-24 keeps |r|^2 > 0 at the centroid itself, where m.r = 0 exactly and
+                // |r|^-3 = 1e36 stays finite, so the term is 0 as before
+                const float Lyz = fmaf(ry, ry, rz2) + 1e-24f, Myz = fmaf(d.m.y, ry, mzrz);
 #pragma unroll
                 for (int j = 0; j < kDipGX / 2; ++j) {
                     const float2 rx = __fadd2_rn(cx, nqx[j]);
                     const float2 r2 = __ffma2_rn(rx, rx, make_float2(Lyz, Lyz));
                     const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-                    float2 ir3 = __fmul2_rn(__fmul2_rn(ir, ir), ir);
-                    ir3.x = r2.x > 0.f ? ir3.x : 0.f;  // a query at the centroid gets 0
-                    ir3.y = r2.y > 0.f ? ir3.y : 0.f;
+                    const float2 ir3 = __fmul2_rn(__fmul2_rn(ir, ir), ir);
                     const float2 mr = __ffma2_rn(mx, rx, make_float2(Myz, Myz));
                     acc[i][j] = __ffma2_rn(mr, ir3, acc[i][j]);
                 }
@@ -318,25 +321,40 @@ __global__ void __launch_bounds__(kDipBwdThreads) dipole_bwd_grid_kernel(const F
                 const float2 L2 = make_float2(fmaf(ry, ry, rz * rz), fmaf(ry, ry, rz * rz));
                 const float myz = fmaf(d.m.y, ry, d.m.z * rz);
                 const float2 M2 = make_float2(myz, myz);
-                float2 A = make_float2(0.f, 0.f), B = A, T = A, E = A;  // sum gi3, gi3 rx, t, t rx
                 const int64_t p0 = whole ? rr * nx / 2 : 0;
                 const int np = whole ? nx / 2 : (int)((len + 1) / 2);
+                // sums of gi3, gi3 rx, t, t rx over the row: unguarded first; a query exactly at the
+                // centroid (|r| = 0) makes them non-finite, and then the row is summed again with
+                // that query's term set to 0
+                auto row_sums = [&](auto guard, float2 &A, float2 &B, float2 &T, float2 &E) {
+                    A = B = T = E = make_float2(0.f, 0.f);
 #pragma unroll 2
-                for (int p = 0; p < np; ++p) {
-                    const float4 q = win[p0 + p];
-                    const float2 rx = __fadd2_rn(cx, make_float2(q.x, q.y));
-                    const float2 r2 = __ffma2_rn(rx, rx, L2);
-                    const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-                    float2 ir2 = __fmul2_rn(ir, ir);
-                    ir2.x = r2.x > 0.f ? ir2.x : 0.f;  // a query at the centroid contributes 0
-                    ir2.y = r2.y > 0.f ? ir2.y : 0.f;
-                    const float2 gi3 = __fmul2_rn(__fmul2_rn(make_float2(q.z, q.w), ir2), ir);
-                    const float2 tt = __fmul2_rn(__fmul2_rn(gi3, __ffma2_rn(mx, rx, M2)), ir2);
-                    A = __fadd2_rn(A, gi3);
-                    B = __ffma2_rn(gi3, rx, B);
-                    T = __fadd2_rn(T, tt);
-                    E = __ffma2_rn(tt, rx, E);
-                }
+                    for (int p = 0; p < np; ++p) {
+                        const float4 q = win[p0 + p];
+                        const float2 rx = __fadd2_rn(cx, make_float2(q.x, q.y));
+                        const float2 r2 = __ffma2_rn(rx, rx, L2);
+                        const float2 ir = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                        const float2 ir2 = __fmul2_rn(ir, ir);
+                        float2 gi3 = __fmul2_rn(__fmul2_rn(make_float2(q.z, q.w), ir2), ir);
+                        if (decltype(guard)::value) {  // |r| = 0: the term is 0 (not 0 * inf)
+                            gi3.x = r2.x > 0.f ? gi3.x : 0.f;
+                            gi3.y = r2.y > 0.f ? gi3.y : 0.f;
+                        }
+                        float2 tt = __fmul2_rn(__fmul2_rn(gi3, __ffma2_rn(mx, rx, M2)), ir2);
+                        if (decltype(guard)::value) {
+                            tt.x = r2.x > 0.f ? tt.x : 0.f;
+                            tt.y = r2.y > 0.f ? tt.y : 0.f;
+                        }
+                        A = __fadd2_rn(A, gi3);
+                        B = __ffma2_rn(gi3, rx, B);
+                        T = __fadd2_rn(T, tt);
+                        E = __ffma2_rn(tt, rx, E);
+                    }
+                };
+                float2 A, B, T, E;
+                row_sums(std::false_type{}, A, B, T, E);
+                if (!isfinite((A.x + A.y) + (B.x + B.y) + (T.x + T.y) + (E.x + E.y)))
+                    row_sums(std::true_type{}, A, B, T, E);
                 const float a = A.x + A.y, b = B.x + B.y, t = T.x + T.y, e = E.x + E.y;
                 kahan(0, a);
                 kahan(1, b);

@@ -115,3 +115,4 @@ def test_small_morph_dipole_improves_iou(cuda_device):
     assert res["final_iou"] > res["initial_iou"] + 0.02, res
     ex = morph(V0, F, target, grid, steps=10, lr=5e-3, surrogate="exact", device=cuda_device)
     assert np.isfinite(ex["final_loss"])
+
