@@ -356,10 +356,16 @@ def run_native(args):
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
+    # end to end through the public API on every rank at once; the job time is the slowest rank's
+    e2e = None
+    if not args.no_e2e:
+        e2e = _e2e(args, V, F, grid, dev)
+        e2e_ms, e2e_value = aggregate_ranks(e2e["ms_per_step"], pairs, 1, ws, dev)
+        e2e.update(value=e2e_value, ms_per_step=e2e_ms, h2d_bytes_per_step=ws * e2e["h2d_bytes_per_step"],
+                   d2h_bytes_per_step=ws * e2e["d2h_bytes_per_step"])
     line = None
     if rank == 0:
         cpu = None if args.no_cpu_baseline else _cpu_baseline(V, F, n)
-        e2e = None if args.no_e2e else _e2e(args, V, F, grid, dev)
         ck = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
