@@ -121,7 +121,7 @@ dv_status dv_selftest_bounded_wait(int64_t limit_us, int arrive, void *stream);
 dv_status dv_build_strips(const int32_t *faces, int64_t nf, int64_t nv, int32_t *ev_vert, int32_t *ev_face,
                           int64_t capacity, int64_t *n_events);
 
-/* Edge-sharing face pairs of the grid adjoint: consecutive faces of the strip
+/* Edge-sharing face pairs of the adjoint (grid and query lists): consecutive faces of the strip
  * order (dv_build_strips) taken two at a time, so that per (query, pair) four
  * vertex distances and five edge dots of the derivative of Eq. (7) serve two
  * faces. HOST function, no GPU needed. faces int32 [nf][3] (host), indices in

@@ -157,7 +157,7 @@ void build_strips(const int32_t *faces, int64_t nf, int64_t nv, std::vector<int3
     }
 }
 
-// Pairs of faces that share an edge, for the grid adjoint (winding_bwd.cu): two consecutive
+// Pairs of faces that share an edge, for the adjoint (winding_bwd.cu): two consecutive
 // faces of a strip share the edge formed by the two events between them, so per (query, pair)
 // four vertex distances and five edge dots serve both faces instead of six and six. Faces of a
 // strip are paired front to back; what is left (odd strip ends, singletons) is listed in
