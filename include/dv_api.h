@@ -150,9 +150,10 @@ const char *dv_last_error(void);
  * (v0, v1, v2 and the face normal (v1-v0)x(v2-v0), FP32 and FP64 copies),
  * build the vertex-to-face adjacency, the strip order of the faces
  * (dv_build_strips) with its per-event records, used by the grid forward
- * and the FP64 re-evaluation, and the edge-sharing face pairs of the grid
- * adjoint (dv_build_face_pairs). The mesh keeps a host copy of the faces. d_verts float32 [nv][3], d_faces int32 [nf][3]
- * are read only during this call (the mesh keeps its own copies).
+ * and the FP64 re-evaluation, and the edge-sharing face pairs of the
+ * adjoint (dv_build_face_pairs). The mesh keeps a host copy of the faces (for
+ * the boundary edges, found on first use). d_verts float32 [nv][3], d_faces
+ * int32 [nf][3] are read only during this call (the mesh keeps its own copies).
  * SYNCHRONIZES `stream` once (validation result). nv >= 3, nf >= 1.
  * On success *out receives a new handle; release it with dv_mesh_destroy. */
 dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,

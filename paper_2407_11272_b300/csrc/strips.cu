@@ -1,5 +1,5 @@
 // Mesh topology on the host, once per mesh at creation: the vertex-sharing strip order of the
-// faces (below), the edge-sharing face pairs of the grid adjoint (build_pairs) and the boundary
+// faces (below), the edge-sharing face pairs of the adjoint (build_pairs) and the boundary
 // edges used by the boundary form of the adjoint (build_boundary).
 //
 // Vertex-sharing triangle strips.

@@ -410,7 +410,7 @@ def dv_build_strips(faces, nv: int):
 
 
 def dv_build_face_pairs(faces, nv: int):
-    """Edge-sharing face pairs of the grid adjoint (host call, no GPU): returns (pairs [n, 8],
+    """Edge-sharing face pairs of the adjoint (host call, no GPU): returns (pairs [n, 8],
     singles [m]) int32 numpy arrays; see dv_build_face_pairs in dv_api.h for the record layout."""
     import numpy as np
 
