@@ -154,8 +154,9 @@ const char *dv_last_error(void);
  * adjoint (dv_build_face_pairs). The mesh keeps a host copy of the faces (for
  * the boundary edges, found on first use). d_verts float32 [nv][3], d_faces
  * int32 [nf][3] are read only during this call (the mesh keeps its own copies).
- * SYNCHRONIZES `stream` once (validation result). nv >= 3, nf >= 1.
- * On success *out receives a new handle; release it with dv_mesh_destroy. */
+ * SYNCHRONIZES `stream` (for the validation result, and once the uploads are
+ * done). nv >= 3, nf >= 1. On success *out receives a new handle; release it
+ * with dv_mesh_destroy. */
 dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,
                          dv_mesh **out);
 
