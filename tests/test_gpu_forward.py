@@ -196,3 +196,20 @@ def test_shsphere256_full_size_sampled(cuda_device):
     stats = check_forward(w[idx], w64, d, "mixed", occ[idx], "shsphere256")
     assert rep["n_flagged"] > 10000
     print(stats, rep)
+
+
+@pytest.mark.parametrize("scale", [1e-3, 1e3])
+def test_scaled_meshes_mixed_precision(cuda_device, scale):
+    """The winding number is scale invariant; meshes and grids scaled by 1e-3 and 1e3 exercise the
+    FP32 fast path and the FP64 pass (whose running product of small-angle factors is rescaled by
+    exact powers of two) far from unit size. At 1e-3 every voxel centre lies within the absolute
+    1e-3 band and goes through FP64."""
+    V, F = meshgen.jittered_torus(nu=30, nv=15, sigma=0.01, delete_frac=0.1, seed=5)
+    V = (V.astype(np.float64) * scale).astype(np.float32)
+    grid = dv.Grid((20, 17, 9), tuple(-scale * x for x in (1.0, 0.9, 0.4)), tuple(scale * x for x in (1.0, 0.9, 0.4)))
+    Q, w64, d = oracle_grid(V, F, grid)
+    mesh = make_mesh(V, F, cuda_device)
+    w, occ, rep = dv.dv_voxelize_grid(mesh, grid, precision="mixed", report=True)
+    check_forward(w.cpu().numpy(), w64, d, "mixed", occ.cpu().numpy(), f"scale {scale}")
+    if scale < 1:
+        assert rep["n_flagged"] == grid.num_queries
