@@ -30,6 +30,12 @@ MUTANTS = {
     "grad_len": ("/ len[j];\n    }\n}", "/ (len[j] * len[j]);\n    }\n}"),
     "grid_corner": ("((double)ix + 0.5)", "((double)ix)"),
     "grid_points_index": ("(c / n[0]) % n[1], c / ((int64_t)n[0] * n[1])", "(c / n[0]) % n[1], c / n[1]"),
+    # Eq. (4): the dipole evaluated at a vertex instead of the face centre, an unnormalized face
+    # normal (2 x area), and the field's denominator |r - q|^2 instead of |r - q|^3
+    "dipole_centroid_to_v0": ("x[k] = (a[k] + b[k] + c[k]) / 3.0 - Q[3 * i + k];", "x[k] = a[k] - Q[3 * i + k];"),
+    "dipole_unnormalized_normal": ("double nrm[3] = {m[0] / (2 * area), m[1] / (2 * area), m[2] / (2 * area)};",
+                                   "double nrm[3] = {m[0], m[1], m[2]};"),
+    "dipole_r_squared": ("/ (r * r * r) * area", "/ (r * r) * area"),
 }
 
 _d = ctypes.POINTER(ctypes.c_double)
@@ -70,6 +76,17 @@ def _grad(lib, V, F, Q, g):
                          F.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.c_int64(len(F)),
                          Q.ctypes.data_as(_d), ctypes.c_int64(len(Q)), g.ctypes.data_as(_d), out.ctypes.data_as(_d),
                          ctypes.c_int(1))
+    return out
+
+
+def _dipole(lib, V, F, Q):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    out = np.empty(len(Q))
+    lib.orc_dipole_winding(V.ctypes.data_as(_d), ctypes.c_int64(len(V)),
+                           F.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.c_int64(len(F)),
+                           Q.ctypes.data_as(_d), ctypes.c_int64(len(Q)), out.ctypes.data_as(_d), ctypes.c_int(1))
     return out
 
 
@@ -116,6 +133,15 @@ def _pins_pass(lib) -> bool:
             b[i, k] -= h
             fd[i, k] = (g @ _winding(lib, a, Fp, Qp) - g @ _winding(lib, b, Fp, Qp)) / (2 * h)
     ok &= np.allclose(G, fd, rtol=1e-5, atol=1e-7)
+    # Eq. (4) on one face: q at distance d behind the centroid along the unit normal gives
+    # area / (4 pi d^2), and shifted by t inside the plane area d / (4 pi (d^2 + t^2)^1.5)
+    Vt = np.array([[0.1, -0.2, 0.05], [0.8, -0.2, 0.05], [0.1, 0.71, 0.05]])
+    area, d, t = 0.5 * 0.7 * 0.91, 0.37, 0.23
+    ct = Vt.mean(axis=0)
+    Qt = np.array([ct - [0, 0, d], ct - [0, 0, d] + [t, 0, 0]])
+    ok &= np.allclose(_dipole(lib, Vt, np.array([[0, 1, 2]]), Qt),
+                      [area / (4 * math.pi * d * d), area * d / (4 * math.pi * (d * d + t * t) ** 1.5)],
+                      rtol=1e-12, atol=0)
     ok &= np.allclose(_grid(lib, 4)[0], [-0.75, -0.75, -0.75])
     ok &= np.allclose(_grid_points(lib, (4, 2, 8), [4 * 2 * 8 - 1]), [[0.75, 0.5, 0.875]])
     return bool(ok)

@@ -346,6 +346,55 @@ def test_dipole_discretization_converges_far_from_surface():
     assert errs[2] < 5e-3
 
 
+def _rotated_face(scale, seed):
+    """One triangle (0,0,0), (s,0,0), (0,1.3s,0) under a seeded rotation and shift, with its exact
+    area, unit normal (counter-clockwise side) and centroid, and an in-plane unit vector."""
+    rng = np.random.default_rng(seed)
+    R, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(R) < 0:
+        R[:, 0] = -R[:, 0]
+    shift = rng.uniform(-0.3, 0.3, size=3)
+    P = np.array([[0.0, 0, 0], [scale, 0, 0], [0, 1.3 * scale, 0]])
+    V = P @ R.T + shift
+    area = 0.5 * 1.3 * scale * scale
+    n = R @ np.array([0.0, 0, 1])
+    u = R @ np.array([0.6, 0.8, 0.0])
+    return V, np.array([[0, 1, 2]], dtype=np.int32), area, n, V.mean(axis=0), u
+
+
+def test_dipole_single_face_closed_forms():
+    # Eq. (4) for one face: W = (1/4pi) <n, E_q(c)> area with E_q(r) = (r - q)/|r - q|^3. For q at
+    # distance d behind the centroid along the normal, c - q = d n, so W = area / (4 pi d^2); moved
+    # by t inside the plane, W = area d / (4 pi (d^2 + t^2)^(3/2)); in front of the face the sign
+    # flips. The area is not 1/2, d is not 1 and the evaluation point matters, so dropping the
+    # area, an unnormalized normal, a wrong power of |r - q| or evaluating at a vertex all fail.
+    for seed, s, d, t in ((0, 0.7, 0.37, 0.23), (1, 1.6, 2.5, -1.1), (2, 0.05, 0.011, 0.004)):
+        V, F, area, n, c, u = _rotated_face(s, seed)
+        Q = np.stack([c - d * n, c - d * n + t * u, c + d * n])
+        want = np.array([area / (4 * math.pi * d * d),
+                         area * d / (4 * math.pi * (d * d + t * t) ** 1.5),
+                         -area / (4 * math.pi * d * d)])
+        got = oracle.dipole_winding(V, F, Q)
+        assert np.allclose(got, want, rtol=1e-12, atol=0), (seed, got, want)
+
+
+def test_dipole_sums_faces_and_skips_degenerate_ones():
+    # Eq. (4) is a plain sum over faces: two separate faces give the sum of their single-face
+    # closed forms, and a zero-area face adds nothing.
+    V1, F1, a1, n1, c1, _ = _rotated_face(0.4, 5)
+    V2, F2, a2, n2, c2, _ = _rotated_face(0.9, 6)
+    V2 = V2 + np.array([1.5, 0.0, 0.0])
+    c2 = c2 + np.array([1.5, 0.0, 0.0])
+    Vd = np.array([[0.2, 0.2, 0.2], [0.4, 0.4, 0.4], [0.8, 0.8, 0.8]])  # collinear: zero area
+    V = np.concatenate([V1, V2, Vd])
+    F = np.concatenate([F1, F2 + 3, np.array([[6, 7, 8]], dtype=np.int32)])
+    q = c1 - 0.3 * n1
+    r = c2 - q
+    want = (a1 / (4 * math.pi * 0.09)
+            + a2 * float(np.dot(n2, r)) / (4 * math.pi * float(np.linalg.norm(r)) ** 3))
+    assert abs(oracle.dipole_winding(V, F, q[None])[0] - want) <= 1e-13 * abs(want)
+
+
 def test_flipped_duplication_closes_open_cap():
     V, F = meshgen.open_cap(freq=6, radius=0.5, max_polar=1.0)
     V2, F2 = oracle.flipped_duplication(V, F, eps=0.01)
