@@ -106,6 +106,22 @@ int dv_abi_version(void);
  * DV_ERR_TIMEOUT, and the CUDA context stays usable. Synchronizes `stream`. */
 dv_status dv_selftest_bounded_wait(int64_t limit_us, int arrive, void *stream);
 
+/* Self-test of the give-up path of the forward's shared-memory copy pipeline
+ * (no counterpart in the paper). Runs the grid forward of dv_winding (strip
+ * order, Kahan FP32) on `mesh` over `grid` into d_out_w (float32, caller-owned
+ * device memory, nx*ny*nz values), except that in every CTA the copy of tile
+ * `skip_tile` (an index into the CTA's own run of 96-event tiles, >= 0) is
+ * never issued and every wait is limited to limit_us microseconds (1 .. 1e7).
+ * A CTA that reaches that tile waits for the limit, stops issuing copies, waits
+ * (bounded) for the copies it has in flight, records DV_ERR_TIMEOUT in the
+ * mesh's sticky error word and finishes; its values in d_out_w are then not
+ * meaningful. With skip_tile beyond every CTA's last tile the call is an
+ * ordinary forward. Synchronizes `stream` and returns the error word without
+ * clearing it (DV_ERR_TIMEOUT, or DV_OK); dv_mesh_check then reports it once.
+ * No fault, trap or unbounded wait is involved. */
+dv_status dv_selftest_forward_timeout(dv_mesh *mesh, const dv_grid *grid, float *d_out_w, int64_t skip_tile,
+                                      int64_t limit_us, void *stream);
+
 /* Strip order of a mesh's faces, the visiting order of the forward passes
  * (the sum of Eq. (5) is order-free; this order lets consecutive faces share
  * the per-vertex |v - q| and per-edge dot terms of Eq. (7)). HOST function, no
@@ -179,6 +195,10 @@ dv_status dv_mesh_reserve(dv_mesh *mesh, const dv_grid *grid, int64_t max_list_q
 int64_t dv_mesh_num_verts(const dv_mesh *mesh);
 int64_t dv_mesh_num_faces(const dv_mesh *mesh);
 int64_t dv_mesh_num_boundary_edges(const dv_mesh *mesh);
+/* Number of strip events of the mesh's visiting order (dv_build_strips; nf
+ * <= events <= 3 nf), the unit the forward and FP64 passes walk per query; -1
+ * if mesh is NULL. */
+int64_t dv_mesh_num_strip_events(const dv_mesh *mesh);
 
 /* Synchronize `stream` and report (then clear) the sticky device error word
  * of the mesh: DV_ERR_TIMEOUT if a kernel's bounded wait ran out. */

@@ -496,6 +496,37 @@ dv_status dv_mesh_check(dv_mesh *m, void *stream) {
     return DV_OK;
 }
 
+dv_status dv_selftest_forward_timeout(dv_mesh *m, const dv_grid *grid, float *d_out_w, int64_t skip_tile,
+                                      int64_t limit_us, void *stream) {
+    int64_t n = 0;
+    if (!grid) return fail(DV_ERR_INVALID_ARG, "grid is NULL");
+    dv_status st = check_queries(m, nullptr, 0, grid, &n);
+    if (st) return st;
+    if (!d_out_w) return fail(DV_ERR_INVALID_ARG, "d_out_w is NULL");
+    if (skip_tile < 0 || skip_tile > (int64_t)INT32_MAX)
+        return fail(DV_ERR_INVALID_ARG, "skip_tile = %lld outside [0, 2^31-1]", (long long)skip_tile);
+    if (limit_us < 1 || limit_us > 10000000)
+        return fail(DV_ERR_INVALID_ARG, "limit_us = %lld outside [1, 1e7]", (long long)limit_us);
+    DeviceGuard dg(m->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const dv::GridF gf = to_gridf(grid);
+    const dv::FwdPlan plan = dv::plan_forward(n, m->nf, true, &gf, m->num_sms, m->ne);
+    m->last_stream = s;
+    if (plan.nsplit > 1 && (st = grow(m->ws_partial, m->cap_partial, (int64_t)plan.nsplit * n, s))) return st;
+    dv::LaunchCtx ctx{s, m->err};
+    ctx.test_skip_tile = (int)skip_tile;
+    ctx.wait_ns = (uint64_t)limit_us * 1000ull;
+    DV_CUDA(dv::launch_forward(plan, m->rec, m->nf, m->srec, m->ne, &gf, nullptr, n, dv::kArithKahan, m->ws_partial,
+                               d_out_w, nullptr, nullptr, nullptr, nullptr, ctx));
+    if (plan.nsplit > 1)
+        DV_CUDA(dv::launch_split_reduce(plan, m->ws_partial, n, d_out_w, nullptr, nullptr, nullptr, nullptr, s));
+    int code = 0;
+    DV_CUDA(cudaMemcpyAsync(&code, m->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DV_CUDA(cudaStreamSynchronize(s));
+    if (code) return fail((dv_status)code, "device error word is %d after the self-test forward", code);
+    return DV_OK;
+}
+
 dv_status dv_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid, float *d_out_w,
                      dv_precision prec, void *stream) {
     int64_t n = 0;
@@ -610,6 +641,8 @@ dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queri
                                        d_dverts, s));
     return DV_OK;
 }
+
+int64_t dv_mesh_num_strip_events(const dv_mesh *mesh) { return mesh ? mesh->ne : -1; }
 
 int64_t dv_mesh_num_boundary_edges(const dv_mesh *mesh) {
     if (!mesh) return -1;

@@ -183,6 +183,10 @@ namespace dv {
 struct LaunchCtx {
     cudaStream_t stream;
     int *d_err;  // sticky device error word (may be null)
+    // Self-test hooks of the forward's copy pipeline (dv_selftest_forward_timeout): a tile index
+    // that no CTA issues (-1: none) and the limit of every bounded wait.
+    int test_skip_tile = -1;
+    uint64_t wait_ns = kWaitLimitNs;
 };
 
 // Kernel-profiling hooks (dv_api.cu): bracket one launch with events when enabled.

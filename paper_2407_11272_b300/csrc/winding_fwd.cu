@@ -59,6 +59,8 @@ struct FwdArgs {
     int *flag_list;
     int *flag_count;
     int *err;
+    int skip_tile;     // self-test: tile (per CTA) that thread 0 never issues; -1 = none
+    uint64_t wait_ns;  // limit of each bounded wait
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -310,12 +312,15 @@ struct TilePipe {
     int64_t f0;
     int64_t nfaces;
     int ntiles;
+    int skip_tile;     // self-test hook: this tile is never issued (-1: none)
+    uint64_t wait_ns;  // limit of each bounded wait
 
     __device__ __forceinline__ int tile_count(int t) const {
         const int64_t left = nfaces - (int64_t)t * kT;
         return left < kT ? (int)left : kT;
     }
     __device__ __forceinline__ void issue(int t) const {
+        if (t == skip_tile) return;
         const int s = t % kStages;
         const uint32_t bytes = (uint32_t)tile_count(t) * (uint32_t)sizeof(Rec);
         mbar_arrive_expect_tx(&full[s], bytes);
@@ -323,6 +328,12 @@ struct TilePipe {
     }
 };
 
+// Every thread waits (bounded) for tile t, processes it, and the barrier that ends the tile
+// combines the threads' verdicts, so the CTA decides as one whether a wait ran out. On a timeout
+// the CTA stops: no further copies are issued, the sticky error word gets DV_ERR_TIMEOUT, and
+// thread 0 waits (bounded again) for the copies already issued and not yet seen complete, tiles
+// t .. min(ntiles, t + kStages) - 1, before the CTA leaves. The results of such a CTA are not
+// meaningful; the error word says so.
 template <typename Rec, int kT, typename Body, typename TileEnd>
 __device__ __forceinline__ bool run_face_tiles(TilePipe<Rec, kT> &pp, int *err, Body &&body, TileEnd &&tile_end) {
     if (threadIdx.x == 0) {
@@ -334,25 +345,29 @@ __device__ __forceinline__ bool run_face_tiles(TilePipe<Rec, kT> &pp, int *err, 
         const int pre = pp.ntiles < kStages ? pp.ntiles : kStages;
         for (int t = 0; t < pre; ++t) pp.issue(t);
     }
+    int t = 0;
     bool timed_out = false;
-    for (int t = 0; t < pp.ntiles; ++t) {
+    for (; t < pp.ntiles; ++t) {
         const int s = t % kStages;
-        // after a first timeout, stop waiting: finish the loop on whatever is in shared memory
-        if (!timed_out && !mbar_wait_bounded(&pp.full[s], (uint32_t)((t / kStages) & 1))) timed_out = true;
+        const bool ok = mbar_wait_bounded(&pp.full[s], (uint32_t)((t / kStages) & 1), pp.wait_ns);
         body(&pp.sm[s][0], pp.tile_count(t));
         tile_end();
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
         if (threadIdx.x == 0 && t + kStages < pp.ntiles) {
             fence_proxy_async_smem();
             pp.issue(t + kStages);
         }
     }
-    if (timed_out) {
-        set_error(err, 5);
-        // Drain: give any copy still in flight a bounded chance to land before the CTA exits.
-        if (threadIdx.x == 0)
-            for (int t = pp.ntiles - kStages < 0 ? 0 : pp.ntiles - kStages; t < pp.ntiles; ++t)
-                mbar_wait_bounded(&pp.full[t % kStages], (uint32_t)((t / kStages) & 1));
+    if (timed_out) {  // the same value in every thread of the CTA
+        if (threadIdx.x == 0) {
+            set_error(err, 5);
+            const int last = t + kStages < pp.ntiles ? t + kStages : pp.ntiles;
+            for (int u = t; u < last; ++u)
+                if (u != pp.skip_tile) mbar_wait_bounded(&pp.full[u % kStages], (uint32_t)((u / kStages) & 1), pp.wait_ns);
+        }
         __syncthreads();
     }
     return !timed_out;
@@ -407,6 +422,8 @@ __global__ void __launch_bounds__(kFwdThreads, 3) fwd_grid_kernel(const FwdArgs 
     const int64_t f1 = pp.f0 + a.faces_per_split < a.nf ? pp.f0 + a.faces_per_split : a.nf;
     pp.nfaces = f1 - pp.f0;
     pp.ntiles = (int)((pp.nfaces + kTileFaces - 1) / kTileFaces);
+    pp.skip_tile = a.skip_tile;
+    pp.wait_ns = a.wait_ns;
 
     run_face_tiles(
         pp, a.err,
@@ -642,6 +659,8 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_grid_strip_kernel(const 
     pp.f0 = e0 - warm;
     pp.nfaces = e1 - pp.f0;
     pp.ntiles = (int)((pp.nfaces + kTileEvents - 1) / kTileEvents);
+    pp.skip_tile = a.skip_tile;
+    pp.wait_ns = a.wait_ns;
 
     int first = warm;  // leading events of the current tile that are warm-up only
     run_face_tiles(
@@ -853,6 +872,8 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_list_strip_kernel(const 
     pp.f0 = e0 - warm;
     pp.nfaces = e1 - pp.f0;
     pp.ntiles = (int)((pp.nfaces + kTileEvents - 1) / kTileEvents);
+    pp.skip_tile = a.skip_tile;
+    pp.wait_ns = a.wait_ns;
 
     int first = warm;
     run_face_tiles(
@@ -999,6 +1020,8 @@ cudaError_t launch_forward(const FwdPlan &p, const FaceRec *rec, int64_t nf, con
     a.flag_list = flag_list;
     a.flag_count = flag_count;
     a.err = ctx.d_err;
+    a.skip_tile = ctx.test_skip_tile;
+    a.wait_ns = ctx.wait_ns;
     dim3 grid((unsigned)p.qblocks, (unsigned)p.nsplit);
     const bool kahan = arith != kArithFP32;
     if (arith == kArithFP16 && queries) return cudaErrorNotSupported;

@@ -16,8 +16,8 @@ from . import build as _build
 __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
-    "dv_winding_backward_boundary", "dv_mesh_num_boundary_edges",
-    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_build_face_pairs", "dv_selftest_bounded_wait", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_winding_backward_boundary", "dv_mesh_num_boundary_edges", "dv_mesh_num_strip_events",
+    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_build_face_pairs", "dv_selftest_bounded_wait", "dv_selftest_forward_timeout", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2, "fp16": 3}
@@ -113,6 +113,8 @@ def load():
     lib.dv_winding_backward_boundary.restype = ctypes.c_int
     lib.dv_mesh_num_boundary_edges.argtypes = [_P]
     lib.dv_mesh_num_boundary_edges.restype = _I64
+    lib.dv_mesh_num_strip_events.argtypes = [_P]
+    lib.dv_mesh_num_strip_events.restype = _I64
     lib.dv_run_batch.argtypes = [ctypes.POINTER(_Request), ctypes.c_int, ctypes.c_int, _P]
     lib.dv_run_batch.restype = ctypes.c_int
     lib.dv_dipole_winding.argtypes = [_P, _P, _I64, ctypes.POINTER(_Grid), _P, _P]
@@ -123,6 +125,8 @@ def load():
     lib.dv_flipped_duplication.restype = ctypes.c_int
     lib.dv_selftest_bounded_wait.argtypes = [_I64, ctypes.c_int, _P]
     lib.dv_selftest_bounded_wait.restype = ctypes.c_int
+    lib.dv_selftest_forward_timeout.argtypes = [_P, ctypes.POINTER(_Grid), _P, _I64, _I64, _P]
+    lib.dv_selftest_forward_timeout.restype = ctypes.c_int
     lib.dv_build_strips.argtypes = [_P, _I64, _I64, _P, _P, _I64, ctypes.POINTER(_I64)]
     lib.dv_build_strips.restype = ctypes.c_int
     lib.dv_build_face_pairs.argtypes = [_P, _I64, _I64, _P, _P, _I64, _I64, ctypes.POINTER(_I64),
@@ -325,6 +329,11 @@ def dv_winding_backward_boundary(mesh: Mesh, upstream, queries=None, grid: Grid 
     return out
 
 
+def dv_mesh_num_strip_events(mesh: Mesh) -> int:
+    """Number of strip events of the mesh's face visiting order."""
+    return int(load().dv_mesh_num_strip_events(mesh.handle))
+
+
 def dv_mesh_num_boundary_edges(mesh: Mesh) -> int:
     return int(load().dv_mesh_num_boundary_edges(mesh.handle))
 
@@ -390,6 +399,19 @@ def dv_dipole_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = N
 def dv_selftest_bounded_wait(limit_us: int, arrive: bool, stream=None) -> int:
     """Status code of one bounded wait on the GPU (0 = DV_OK, 5 = DV_ERR_TIMEOUT); no exception."""
     return int(load().dv_selftest_bounded_wait(int(limit_us), 1 if arrive else 0, _stream(stream)))
+
+
+def dv_selftest_forward_timeout(mesh: Mesh, grid: Grid, out, skip_tile: int, limit_us: int, stream=None) -> int:
+    """Status code of the grid forward run with tile `skip_tile` of every CTA never issued and
+    every wait limited to limit_us (0 = DV_OK, 5 = DV_ERR_TIMEOUT); no exception."""
+    import torch
+
+    out = _tensor(out, torch.float32, None, "out")
+    if out.numel() != grid.num_queries:
+        raise ValueError("out must have one value per grid cell")
+    g = grid._c()
+    return int(load().dv_selftest_forward_timeout(mesh.handle, ctypes.byref(g), ctypes.c_void_p(out.data_ptr()),
+                                                  int(skip_tile), int(limit_us), _stream(stream)))
 
 
 def dv_build_strips(faces, nv: int):
