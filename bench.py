@@ -8,10 +8,25 @@ One step = the whole hot path on one synthetic mesh and grid:
   selected queries, occupancy (dv_voxelize_grid, mixed precision), and the
   adjoint dL/dV for an N(0,1) upstream (dv_winding_backward).
 Metric: query x face pairs per second, counting each pair once for its forward
-and backward evaluation (pairs = queries x faces per step).
+and backward evaluation (pairs = queries x faces per step); the forward and the
+adjoint rates are reported beside it.
 
-Default workload ``torus_128``: jittered torus R=0.6, r=0.25, 200x100 grid, 10 %
-faces deleted (36 000 faces, open), 128^3 cell-centred grid on [-1,1]^3.
+Default workload ``shsphere_256``: a sphere of radius 0.7 displaced by a seeded
+spherical-harmonic field (degrees <= 8), as a frequency-101 geodesic mesh with
+204 020 faces, on a 256^3 cell-centred grid over [-1,1]^3 (3.42e12 pairs per
+step). ``torus_128`` (jittered open torus, 36 000 faces, 128^3) and the small
+cases remain selectable with --workload.
+
+Beside the timed steps, outside the timed region, the line carries
+  * ``accuracy``: plain FP32, Kahan FP32 and mixed precision against the FP64
+    oracle on a seeded sample of 100 000 voxel centres (max |dw| farther than
+    1e-3 from the surface, occupancy mismatches outside ties);
+  * ``served``: the served mixed stream (512 requests, Poisson 200 req/s, and
+    again at 0.7 x the measured capacity) with p50/p99 latency and pairs/s;
+  * ``cpu_baseline``: the oracle on the host's cores on a bounded sample.
+The oracle runs in a separate process started before the first CUDA call: the
+CPU baseline is timed while the GPU is idle, and the accuracy sample's oracle
+values are computed while the GPU steps run.
 Under torchrun each rank runs its own replica of the workload (the queries of
 different meshes are independent; there is no data-path collective): the
 value is the work of all ranks over the slowest rank's time.
@@ -35,64 +50,89 @@ if ROOT not in sys.path:
 
 METRIC = "query×face solid-angle pairs/s fwd & fwd+bwd, served p50/p99 ms, |Δw|≤1e-4"
 UNIT = "pairs/s"
-# FP32 lane operations per pair (FMA = 1): the direct formula's count for the forward (offsets,
-# lengths, N, dots, D, atan2, accumulate) and for the adjoint (no atan2, ~2x the algebra).
+# FP32 lane operations per pair (FMA = 1) of the direct formula: offsets, lengths, N, dots, D,
+# arctangent and accumulation for the forward; about twice that algebra (no arctangent) for the
+# adjoint. The kernels share distances and dots between consecutive faces and execute fewer, so
+# a rate on this basis is an algorithmic-equivalent rate that can exceed the FP32 peak.
 OPS_FWD = 59
 OPS_BWD = 120
-# FP32 lane operations the grid adjoint kernel executes per pair (counted from its code, FMA = 1):
-# 42 for a face alone, 38.5 for a face of an edge-sharing pair (distances and dots shared).
+# FP32 lane operations the grid adjoint kernel executes per pair, counted from its code (FMA = 1):
+# 42 for a face alone, 38.5 for a face of an edge-sharing pair (distances and dots shared). Used
+# when no measured count (EXECUTED) matches the kernel's current source.
 EXEC_BWD_SINGLE = 42.0
 EXEC_BWD_PAIRED = 38.5
 
+# Executed operations per unit, measured by ncu thread-instruction counters on the same mesh over
+# a 64^3 grid: FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2) per query x face pair for the
+# FP32 kernels, DFMA + DADD + DMUL per re-evaluated query x strip event for the FP64 pass. Keyed
+# by (mesh, kernel); each entry records the SHA-256 of the kernel's source file at capture time
+# and is ignored once that file changes.
+EXECUTED = {}
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the dominant kernel on the full workload, keyed by (workload, kernel). Each entry records the
-# SHA-256 of the kernel's source file at capture time: if that file has changed since, the
-# counters no longer describe the kernel and the bench line reports traffic as null.
+# the dominant kernel on the full workload, keyed by (workload, kernel), with the same source
+# digest rule as EXECUTED.
 TRAFFIC = {
     ("torus_128", "bwd_grid"): (11298304, "paper_2407_11272_b300/csrc/winding_bwd.cu",
                                 "b6c3d3a58e597cc97d82f06b22944d858cd3bc9d5611dd9cbd4ca087a86631da"),
 }
 
+ACC_QUERIES = 100_000  # seeded voxel-centre sample of the accuracy block
+ACC_SEED = 4
+
 WORKLOADS = {
+    "shsphere_256": dict(desc="SH-displaced geodesic sphere r=0.7 (l<=8, c~N(0,0.02^2), seed 3; 204020 faces), "
+                              "256^3 grid on [-1,1]^3, fwd(mixed: Kahan FP32 + FP64 re-eval) + bwd",
+                         n=256, mesh="sh_sphere"),
     "torus_128": dict(desc="jittered open torus R=0.6 r=0.25 200x100, 10% faces deleted (36000 faces), "
                            "128^3 grid on [-1,1]^3, fwd(mixed: Kahan FP32 + FP64 re-eval) + bwd",
-                      n=128),
-    "shsphere_256": dict(desc="SH-displaced geodesic sphere r=0.7 (204020 faces), 256^3 grid on [-1,1]^3, "
-                              "fwd(mixed) + bwd", n=256),
+                      n=128, mesh="torus"),
+    "shsphere_64": dict(desc="the shsphere_256 mesh (204020 faces) on a 64^3 grid on [-1,1]^3, fwd(mixed) + bwd; "
+                             "the small case for profiler captures", n=64, mesh="sh_sphere"),
     "torus_64": dict(desc="the torus_128 mesh (36000 faces) on a 64^3 grid on [-1,1]^3, fwd(mixed) + bwd; "
-                          "the small case for profiler captures", n=64),
-    "icosphere_32": dict(desc="icosphere k=3 r=0.8 (1280 faces), 32^3 grid on [-1,1]^3, fwd(mixed) + bwd", n=32),
+                          "the small case for profiler captures", n=64, mesh="torus"),
+    "icosphere_32": dict(desc="icosphere k=3 r=0.8 (1280 faces), 32^3 grid on [-1,1]^3, fwd(mixed) + bwd", n=32,
+                         mesh="icosphere"),
 }
+DEFAULT_WORKLOAD = "shsphere_256"
 
 
 def _mesh_for(name):
     from paper_2407_11272_b300 import meshgen
 
-    if name in ("torus_128", "torus_64"):
+    kind = WORKLOADS[name]["mesh"]
+    if kind == "torus":
         return meshgen.jittered_torus()
-    if name == "shsphere_256":
+    if kind == "sh_sphere":
         return meshgen.sh_sphere()
-    if name == "icosphere_32":
-        return meshgen.icosphere(3, 0.8)
-    raise SystemExit(f"unknown workload {name}")
+    return meshgen.icosphere(3, 0.8)
+
+
+def _source_matches(src, digest):
+    import hashlib
+
+    path = os.path.join(ROOT, src)
+    if not os.path.exists(path):
+        return False
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest() == digest
 
 
 def _traffic(workload, kernel):
     """Captured DRAM bytes per launch of `kernel` on `workload`, or None if not captured or if the
     kernel's source changed after the capture."""
-    import hashlib
-
     ent = TRAFFIC.get((workload, kernel))
-    if not ent:
+    if not ent or not _source_matches(ent[1], ent[2]):
         return None
-    nbytes, src, digest = ent
-    path = os.path.join(ROOT, src)
-    if not os.path.exists(path):
+    return ent[0]
+
+
+def _executed(workload, kernel):
+    """Measured executed operations per unit of `kernel` on `workload`'s mesh, or None."""
+    ent = EXECUTED.get((WORKLOADS[workload]["mesh"], kernel))
+    if not ent or not _source_matches(ent[1], ent[2]):
         return None
-    with open(path, "rb") as fh:
-        if hashlib.sha256(fh.read()).hexdigest() != digest:
-            return None
-    return nbytes
+    return ent[0]
 
 
 def _dist_env():
@@ -189,6 +229,64 @@ def _cpu_baseline(V, F, grid_n, budget_s=12.0, seed=4):
                       f"{dt:.1f} s"}
 
 
+def _oracle_leg_main(conn, workload, acc_queries, budget_s):
+    """Body of the spawned oracle process: on "go" the CPU baseline (the GPU side waits meanwhile),
+    then the oracle's w and distance to the surface at the accuracy sample's voxel centres."""
+    import oracle
+    from paper_2407_11272_b300 import meshgen
+
+    n = WORKLOADS[workload]["n"]
+    V, F = _mesh_for(workload)
+    oracle.build()
+    if conn.recv() != "go":
+        return
+    conn.send(("baseline", _cpu_baseline(V, F, n, budget_s) if budget_s > 0 else None))
+    if acc_queries <= 0:
+        return
+    idx = meshgen.query_subsample(n ** 3, acc_queries, seed=ACC_SEED)
+    Q = oracle.grid_points([-1.0] * 3, [1.0] * 3, [n] * 3, idx)
+    t0 = time.perf_counter()
+    w64 = oracle.winding(V, F, Q)
+    t1 = time.perf_counter()
+    d = oracle.point_mesh_distance(V, F, Q)
+    t2 = time.perf_counter()
+    conn.send(("accuracy", {"idx": idx, "w64": w64, "d": d, "winding_s": t1 - t0, "distance_s": t2 - t1,
+                            "threads": oracle.max_threads()}))
+
+
+class OracleLeg:
+    """The oracle's share of the bench in a process of its own (spawned, so it is started before
+    and independent of any CUDA context): the CPU baseline, timed while the GPU is idle, then the
+    accuracy sample's reference values, computed while the GPU steps run."""
+
+    def __init__(self, workload, acc_queries, budget_s=12.0):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        self.conn, child = ctx.Pipe()
+        self.proc = ctx.Process(target=_oracle_leg_main, args=(child, workload, acc_queries, budget_s), daemon=True)
+        self.proc.start()
+        child.close()
+
+    def baseline(self):
+        self.conn.send("go")
+        tag, val = self.conn.recv()
+        assert tag == "baseline"
+        return val
+
+    def accuracy(self, timeout_s=1800.0):
+        if not self.conn.poll(timeout_s):
+            return None
+        tag, val = self.conn.recv()
+        assert tag == "accuracy"
+        return val
+
+    def close(self):
+        if self.proc.is_alive():
+            self.proc.terminate()
+        self.proc.join(timeout=10)
+
+
 def aggregate_ranks(local_ms: float, pairs_per_step: int, steps: int, ws: int, device=None):
     """Whole-job throughput: every rank ran its own replica of `steps` steps; the job time is the
     slowest rank's (max over ranks), and the value counts the pairs of all ranks.
@@ -252,12 +350,120 @@ def run_reference(args):
     return 0
 
 
+def _kernel_rooflines(args, prof, pairs, nflagged, ne, F, nv, fp32_peak, fp64_peak):
+    """Per hot kernel: the rate on the survey's algorithmic basis (FP32 lane operations of the direct
+    formula per pair; exceeds 1 by operation sharing) and on the executed basis (operations the
+    kernel executes per unit, measured by ncu counters, else counted from the code), both against
+    the peak of the pipe that bounds it."""
+    out = {}
+    for name, alg in (("fwd_strip_kahan", OPS_FWD), ("fwd_strip", OPS_FWD), ("bwd_grid", OPS_BWD)):
+        if name not in prof:
+            continue
+        ms, cnt = prof[name]
+        avg_s = ms / max(cnt, 1) * 1e-3
+        rate = pairs / avg_s
+        ent = {"ms_per_launch": avg_s * 1e3, "units": "query x face pairs", "units_per_launch": pairs,
+               "pairs_per_s": rate, "peak": fp32_peak / 1e12, "peak_unit": "Tlane-op/s (FP32, FMA=1)",
+               "alg_ops_per_pair": alg, "frac_alg_equivalent": alg * rate / fp32_peak}
+        ex = _executed(args.workload, name)
+        basis = "ncu thread-instruction counters on the same mesh at 64^3"
+        if ex is None and name == "bwd_grid":
+            pair_recs, singles = __import__("paper_2407_11272_b300.dv", fromlist=["dv"]).dv_build_face_pairs(F, nv)
+            ex = (EXEC_BWD_PAIRED * 2 * len(pair_recs) + EXEC_BWD_SINGLE * len(singles)) / len(F)
+            basis = "counted from the kernel's code (38.5 per paired face, 42 per single face)"
+        if ex is not None:
+            ent.update(executed_ops_per_pair=ex, frac_executed=ex * rate / fp32_peak, executed_basis=basis)
+        out[name] = ent
+    if "reeval_fp64" in prof and nflagged:
+        ms, cnt = prof["reeval_fp64"]
+        avg_s = ms / max(cnt, 1) * 1e-3
+        units = nflagged * ne
+        ent = {"ms_per_launch": avg_s * 1e3, "units": "re-evaluated query x strip event",
+               "units_per_launch": units, "units_per_s": units / avg_s, "peak": fp64_peak / 1e12,
+               "peak_unit": "T DFMA-lane-op/s (FP64)"}
+        ex = _executed(args.workload, "reeval_fp64")
+        if ex is not None:
+            ent.update(executed_ops_per_unit=ex, frac_executed=ex * units / avg_s / fp64_peak,
+                       executed_basis="ncu thread-instruction counters on the same mesh at 64^3")
+        out["reeval_fp64"] = ent
+    return out
+
+
+def _accuracy_gpu(mesh, grid, w, occ, idx, stream, dev):
+    """Forward outputs at the accuracy sample in plain FP32, Kahan FP32 and mixed precision (each a
+    whole-grid dv_voxelize_grid, timed with CUDA events), outside the timed region."""
+    import torch
+
+    from paper_2407_11272_b300 import dv
+
+    idx_t = torch.from_numpy(idx).to(dev)
+    out = {}
+    for prec in ("fp32", "kahan", "mixed"):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision=prec, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        out[prec] = (w[idx_t].cpu().numpy(), occ[idx_t].cpu().numpy(), a.elapsed_time(b))
+    return out
+
+
+def _accuracy(gpu, ref, n_flagged, pairs):
+    """Errors of each precision against the oracle at the sample: max and mean |dw| farther than
+    1e-3 from the surface (the parity bar is 1e-4), max |dw| nearer, and occupancy mismatches
+    among queries that are not ties (|w64 - 0.5| > 1e-9)."""
+    w64, d = ref["w64"], ref["d"]
+    far = d > 1e-3
+    tie = np.abs(w64 - 0.5) <= 1e-9
+    occ64 = w64 > 0.5
+    out = {"queries": int(len(w64)), "seed": ACC_SEED, "n_far": int(far.sum()), "n_near": int((~far).sum()),
+           "ties": int(tie.sum()),
+           "oracle": f"FP64 winding + exact point-triangle distance, {ref['threads']} threads, "
+                     f"{ref['winding_s']:.1f} s + {ref['distance_s']:.1f} s"}
+    for prec, (wg, og, ms) in gpu.items():
+        err = np.abs(wg.astype(np.float64) - w64)
+        mism = (og.astype(bool) != occ64) & ~tie
+        ent = {"fwd_ms": ms, "fwd_pairs_per_s": pairs / (ms * 1e-3),
+               "max_abs_dw_far": float(err[far].max()) if far.any() else None,
+               "mean_abs_dw_far": float(err[far].mean()) if far.any() else None,
+               "max_abs_dw_near": float(err[~far].max()) if (~far).any() else None,
+               "occ_mismatch": int(mism.sum()), "occ_mismatch_far": int((mism & far).sum()),
+               "occ_mismatch_near": int((mism & ~far).sum())}
+        ent["meets_1e-4_far"] = ent["max_abs_dw_far"] is None or ent["max_abs_dw_far"] <= 1e-4
+        if prec == "mixed":
+            ent["n_flagged_grid"] = int(n_flagged)
+        out[prec] = ent
+    return out
+
+
+def _served(dev):
+    """The served mixed stream (512 requests, Poisson 200 req/s, seed 5), then the same stream at
+    0.7 x the capacity that run shows (its offered load exceeds capacity), through serve.Server."""
+    from paper_2407_11272_b300 import serve
+
+    sv = serve.served_runs(capacity_run=False, device=dev)
+    keep = ("p50_ms", "p99_ms", "mean_ms", "pairs_per_s", "requests_per_s", "makespan_s", "requests", "batches",
+            "mean_batch", "batch_host_ms_mean", "batch_host_ms_p50", "batch_host_ms_max", "batch_host_s_total",
+            "rate", "fraction")
+    out = {"workload": sv["workload"], "mean_pairs_per_request": sv["mean_pairs_per_request"],
+           "offered_pairs_per_s": sv["offered_pairs_per_s"], "capacity_from": sv["capacity_from"]}
+    for k in ("at_rate", "sub_capacity"):
+        out[k] = {x: sv[k][x] for x in keep if x in sv[k]}
+    return out
+
+
 def run_native(args):
+    ws, rank, local = _dist_env()
+    n = WORKLOADS[args.workload]["n"]
+    leg = None
+    if rank == 0 and not (args.no_cpu_baseline and args.no_accuracy):
+        # before the first CUDA call: the oracle's process is spawned, not forked from a CUDA context
+        leg = OracleLeg(args.workload, 0 if args.no_accuracy else ACC_QUERIES, 0.0 if args.no_cpu_baseline else 12.0)
+
     import torch
 
     from paper_2407_11272_b300 import build, dv, meshgen
 
-    ws, rank, local = _dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
     torch.cuda.set_device(local)
@@ -268,7 +474,6 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=dev)
     build.build()
     V, F = _mesh_for(args.workload)
-    n = WORKLOADS[args.workload]["n"]
     grid = dv.Grid.cube(n)
     nq, nf = grid.num_queries, len(F)
     pairs = nq * nf
@@ -301,6 +506,9 @@ def run_native(args):
         stream.wait_stream(s_fwd)
         stream.wait_stream(s_bwd)
 
+    torch.cuda.synchronize()
+    cpu = leg.baseline() if leg is not None else None  # the oracle timed while the GPU is idle
+
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()
@@ -329,43 +537,66 @@ def run_native(args):
     times_ms = [a.elapsed_time(b) for a, b in evs]
     prof = dv.dv_profile_read()
     total_ms, value = aggregate_ranks(float(sum(times_ms)), pairs, args.steps, ws, dev)
-    bnd = _boundary_adjoint(mesh, g, grid, dV, prof, stream, dev)
+    dv.dv_mesh_check(mesh)  # no bounded wait ran out during the timed steps
+
+    # forward (near-surface flags, FP32 pass, split reduction, FP64 pass) and adjoint (face-parallel
+    # kernel, vertex gather) rates from the per-kernel event times of the timed steps
+    fwd_k = ("near_surface_grid", "fwd_strip_kahan", "fwd_strip", "split_reduce", "reeval_fp64")
+    bwd_k = ("bwd_grid", "gather_dverts")
+    fwd_ms = sum(prof[k][0] for k in fwd_k if k in prof) / args.steps
+    bwd_ms = sum(prof[k][0] for k in bwd_k if k in prof) / args.steps
 
     # roofline of the dominant kernel: algorithmic FP32 lane operations per launch / measured duration
     peaks, peak_src = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = sms * 128 * sm_mhz * 1e6  # lane-ops/s, FMA counted once
+    fp64_peak = sms * 2 * sm_mhz * 1e6    # FP64 lanes: 1/64 of the FP32 lanes
     dom = max(prof.items(), key=lambda kv: kv[1][0]) if prof else ("none", (0.0, 1))
     dname, (dms, dn) = dom
-    ops = {"fwd_grid_kahan": OPS_FWD, "fwd_grid": OPS_FWD, "fwd_grid_fp16": OPS_FWD, "fwd_strip_kahan": OPS_FWD,
-           "fwd_strip": OPS_FWD, "bwd_grid": OPS_BWD}.get(dname, OPS_FWD)
+    kr = _kernel_rooflines(args, prof, pairs, rep["n_flagged"], dv.dv_mesh_num_strip_events(mesh), F, len(V),
+                           fp32_peak, fp64_peak)
+    ops = {"fwd_strip_kahan": OPS_FWD, "fwd_strip": OPS_FWD, "bwd_grid": OPS_BWD}.get(dname, OPS_FWD)
     avg_s = dms / max(dn, 1) * 1e-3
     achieved = ops * pairs / avg_s if avg_s > 0 else 0.0
-    traffic = _traffic(args.workload, dname)
     roof = {"bound": "alu", "kernel": dname, "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
             "unit": "Tlane-op/s (FP32, FMA=1)", "frac": achieved / fp32_peak if fp32_peak else None,
-            "traffic": traffic, "ops_per_pair": ops,
+            "frac_basis": f"algorithmic-equivalent: {ops} FP32 lane-ops per pair of the direct formula; above 1 "
+                          "because the kernel shares distances and dots between faces",
+            "traffic": _traffic(args.workload, dname), "ops_per_pair": ops,
             "peak_note": f"{sms} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz ({peak_src} sm_max_mhz)"}
-    if dname == "bwd_grid" and avg_s > 0:
-        # the same rate on the basis of the operations the kernel executes (faces in pairs and alone)
-        pair_recs, singles = dv.dv_build_face_pairs(F, len(V))
-        exec_ops = (EXEC_BWD_PAIRED * 2 * len(pair_recs) + EXEC_BWD_SINGLE * len(singles)) / nf
-        roof["executed_ops_per_pair"] = exec_ops
-        roof["frac_executed"] = exec_ops * pairs / avg_s / fp32_peak
+    if dname in kr and "frac_executed" in kr[dname]:
+        roof.update(executed_ops_per_pair=kr[dname]["executed_ops_per_pair"],
+                    frac_executed=kr[dname]["frac_executed"], executed_basis=kr[dname]["executed_basis"])
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    bnd = _boundary_adjoint(mesh, g, grid, dV, prof, stream, dev)
+
+    acc_gpu = None
+    if leg is not None and not args.no_accuracy:
+        acc_gpu = _accuracy_gpu(mesh, grid, w, occ, meshgen.query_subsample(nq, ACC_QUERIES, seed=ACC_SEED),
+                                stream, dev)
 
     # end to end through the public API on every rank at once; the job time is the slowest rank's
     e2e = None
     if not args.no_e2e:
-        e2e = _e2e(args, V, F, grid, dev)
+        e2e = _e2e(args, V, F, grid, dev, total_ms / args.steps)
         e2e_ms, e2e_value = aggregate_ranks(e2e["ms_per_step"], pairs, 1, ws, dev)
         e2e.update(value=e2e_value, ms_per_step=e2e_ms, h2d_bytes_per_step=ws * e2e["h2d_bytes_per_step"],
                    d2h_bytes_per_step=ws * e2e["d2h_bytes_per_step"])
+    mesh.close()
+    del flush, w, occ, g, dV
+    torch.cuda.empty_cache()
+
     line = None
     if rank == 0:
-        cpu = None if args.no_cpu_baseline else _cpu_baseline(V, F, n)
+        acc = None
+        if acc_gpu is not None:
+            ref = leg.accuracy()
+            acc = _accuracy(acc_gpu, ref, rep["n_flagged"], pairs) if ref is not None else {"error": "oracle timed out"}
+        if leg is not None:
+            leg.close()
+        served = None if args.no_served else _served(dev)
         ck = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -376,19 +607,25 @@ def run_native(args):
                        "l2": "flushed between timed steps (256 MB write)", "streams": args.streams,
                        "precision": args.precision,
                        "fp64_reevaluated_queries": rep["n_flagged"]},
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "fwd_pairs_per_s": ws * pairs / (fwd_ms * 1e-3) if fwd_ms > 0 else None,
+            "bwd_pairs_per_s": ws * pairs / (bwd_ms * 1e-3) if bwd_ms > 0 else None,
+            "fwd_ms_per_step": fwd_ms, "bwd_ms_per_step": bwd_ms,
+            "roofline": roof, "roofline_kernels": kr, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
+            "accuracy": acc,
+            "served": served,
             "adjoint_boundary": bnd,
             "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"],
                        "samples": ck["samples"]},
         }
         print(json.dumps(line))
+    elif leg is not None:
+        leg.close()
     if ws > 1:
         import torch.distributed as dist
 
         dist.barrier()
         dist.destroy_process_group()
-    mesh.close()
     return 0
 
 
@@ -421,7 +658,7 @@ def _boundary_adjoint(mesh, g, grid, dV_faces, prof, stream, dev):
             "face_adjoint_norm": float(torch.linalg.norm(ref)), "note": note}
 
 
-def _e2e(args, V, F, grid, dev):
+def _e2e(args, V, F, grid, dev, step_ms):
     """Same step through the public API from pinned host buffers: H2D of the mesh and upstream,
     mesh creation (validation + packing), voxelization, adjoint, D2H of w, occupancy and dL/dV."""
     import torch
@@ -452,23 +689,26 @@ def _e2e(args, V, F, grid, dev):
         mesh.close()
 
     one()
-    k = max(1, min(args.steps, 3))
+    k = max(1, min(args.steps, 2 if step_ms > 2000 else 3))
     t0 = time.perf_counter()
     for _ in range(k):
         one()
     dt = (time.perf_counter() - t0) / k
     return {"value": grid.num_queries * len(F) / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3, "steps": k}
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--gpus", type=int, default=1,
+                    help="number of GPUs (ranks); N > 1 must be launched with torchrun --nproc-per-node N")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="torus_128")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the 1e5-query accuracy block")
+    ap.add_argument("--no-served", action="store_true", help="skip the served mixed stream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["mixed", "kahan", "fp32", "fp16"], default="mixed",
                     help="forward arithmetic (mixed = Kahan FP32 + FP64 re-evaluation, the default)")
@@ -476,6 +716,12 @@ def main(argv=None):
                     help="1: one stream (default); 2: forward and adjoint on two streams")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps, whatever was asked
+    ws = _dist_env()[0]
+    if args.gpus != ws:
+        print(f"bench.py: --gpus {args.gpus} but {ws} rank(s) were started (WORLD_SIZE={ws}); run N GPUs as "
+              f"python -m torch.distributed.run --nproc-per-node {args.gpus} --master-addr 127.0.0.1 bench.py "
+              f"--gpus {args.gpus}", file=sys.stderr)
+        return 2
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

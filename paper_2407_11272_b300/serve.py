@@ -198,7 +198,9 @@ class Server:
                     a.dverts = torch.empty((len(a.req.verts), 3), dtype=torch.float32, device=self.dev)
                     d.update(upstream=a.up, dverts=a.dverts)
                 reqs.append(d)
+            th = time.perf_counter()
             dv.dv_run_batch(reqs, precision=self.precision, stream=stream)
+            self._batch_host_s.append(time.perf_counter() - th)  # scratch, capture, instantiate, launch
             for a in items:
                 a.host_occ = torch.empty(a.req.queries, dtype=torch.uint8, pin_memory=True)
                 a.host_occ.copy_(a.occ, non_blocking=True)
@@ -225,6 +227,7 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         admitted = collections.deque()
         self._inflight = []
+        self._batch_host_s = []
         results, batch_sizes = [], []
         bid = 0
         torch.cuda.synchronize(self.dev)
@@ -267,7 +270,50 @@ class Server:
                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                  "mean_ms": float(lat.mean()), "batches": bid,
                  "mean_batch": float(np.mean(batch_sizes)) if batch_sizes else 0.0}
+        hs = np.array(self._batch_host_s) * 1e3
+        if len(hs):
+            # host time of dv_run_batch per batch: scratch reservation, graph capture, instantiation
+            # and launch (the call returns before the GPU work ends)
+            stats.update(batch_host_ms_mean=float(hs.mean()), batch_host_ms_p50=float(np.percentile(hs, 50)),
+                         batch_host_ms_max=float(hs.max()), batch_host_s_total=float(hs.sum() * 1e-3))
         return results, stats
+
+
+def served_runs(n_requests: int = 512, rate: float = 200.0, seed: int = 5, sub_capacity: float = 0.7,
+                max_batch: int = 16, max_inflight: int = 3, capacity_run: bool = True, sweep=(), device="cuda"):
+    """The served mixed stream at ``rate`` (arrivals in real time), optionally the same requests
+    all queued at t = 0 (capacity), and the stream again at ``sub_capacity`` x the measured
+    capacity (from the queued run, else from the run at ``rate`` when that rate exceeds it).
+    Returns a dict of the runs' statistics (p50/p99 latency, pairs/s, requests/s, batches)."""
+    t = time.perf_counter()
+    reqs = make_workload(n_requests, rate, seed)
+    gen_s = time.perf_counter() - t
+    srv = Server(device=device, max_batch=max_batch, max_inflight=max_inflight)
+    warm = make_workload(8, 0.0, seed=seed + 100, f_hi=5000, grids=(32,))
+    srv.run(warm, realtime=False)
+    cap = None
+    if capacity_run:
+        _, cap = srv.run(reqs, realtime=False)
+    _, live = srv.run(reqs, realtime=True)
+    mean_pairs = float(np.mean([r.pairs for r in reqs]))
+    capacity = cap["pairs_per_s"] if cap else live["pairs_per_s"]
+    sub_rate = sub_capacity * capacity / mean_pairs
+    _, slow = srv.run(make_workload(n_requests, sub_rate, seed), realtime=True)
+    out_sweep = []
+    for frac in sweep:
+        r = frac * capacity / mean_pairs
+        _, st = srv.run(make_workload(n_requests, r, seed), realtime=True)
+        out_sweep.append(dict(st, rate=r, fraction=frac))
+    out = {"workload": f"{n_requests} requests, Poisson {rate} req/s (seed {seed}), ellipsoid unions "
+                       "F log-uniform [500, 1e5], grids {32..192}^3, 30% with dL/dV",
+           "generation_s": gen_s, "mean_pairs_per_request": mean_pairs, "offered_pairs_per_s": rate * mean_pairs,
+           "capacity_from": "all queued at t=0" if cap else f"the run at {rate} req/s (offered load above capacity)",
+           "at_rate": live, "sub_capacity": dict(slow, rate=sub_rate, fraction=sub_capacity)}
+    if cap:
+        out["capacity"] = cap
+    if out_sweep:
+        out["sweep"] = out_sweep
+    return out
 
 
 def main(argv=None):
@@ -281,29 +327,8 @@ def main(argv=None):
     ap.add_argument("--sweep", type=str, default="",
                     help="extra comma-separated fractions of the measured capacity to offer as Poisson loads")
     a = ap.parse_args(argv)
-    t = time.perf_counter()
-    reqs = make_workload(a.requests, a.rate, a.seed)
-    gen_s = time.perf_counter() - t
-    srv = Server(max_batch=a.max_batch, max_inflight=a.max_inflight)
-    warm = make_workload(8, 0.0, seed=a.seed + 100, f_hi=5000, grids=(32,))
-    srv.run(warm, realtime=False)
-    _, cap = srv.run(reqs, realtime=False)
-    _, live = srv.run(reqs, realtime=True)
-    mean_pairs = float(np.mean([r.pairs for r in reqs]))
-    sub_rate = a.sub_capacity * cap["pairs_per_s"] / mean_pairs
-    sub = make_workload(a.requests, sub_rate, a.seed)
-    _, slow = srv.run(sub, realtime=True)
-    sweep = []
-    for frac in [float(x) for x in a.sweep.split(",") if x.strip()]:
-        rate = frac * cap["pairs_per_s"] / mean_pairs
-        _, st = srv.run(make_workload(a.requests, rate, a.seed), realtime=True)
-        sweep.append(dict(st, rate=rate, fraction=frac))
-    offered = a.rate * mean_pairs
-    print(json.dumps({"workload": f"{a.requests} requests, Poisson {a.rate} req/s (seed {a.seed}), ellipsoid unions "
-                                  "F log-uniform [500, 1e5], grids {32..192}^3, 30% with dL/dV",
-                      "generation_s": gen_s, "mean_pairs_per_request": mean_pairs,
-                      "offered_pairs_per_s": offered, "capacity": cap, "at_rate": live,
-                      "sub_capacity": dict(slow, rate=sub_rate, fraction=a.sub_capacity), "sweep": sweep}))
+    print(json.dumps(served_runs(a.requests, a.rate, a.seed, a.sub_capacity, a.max_batch, a.max_inflight,
+                                 sweep=[float(x) for x in a.sweep.split(",") if x.strip()])))
 
 
 if __name__ == "__main__":
