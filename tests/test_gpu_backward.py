@@ -172,22 +172,29 @@ def test_torus128_full_size_64_vertices(cuda_device):
     mesh = make_mesh(V, F, cuda_device)
     Q = oracle.grid_queries(grid.lo, grid.hi, grid.n)
     g32 = meshgen.upstream_gradient(len(Q), seed=1)
-    # mask the near-surface queries using the GPU-independent conservative rule: the oracle distance
-    # is too slow at this size, so mask by a bounding distance to the vertices instead (a superset)
+    # Only the faces incident to the 64 vertices enter their gradient, so the upstream is masked to
+    # 0 within 1e-3 of those faces (the near-surface radius of the gradient bar), by the oracle's
+    # exact distance to them.
     ids = meshgen.random_vertex_ids(len(V), 64, seed=2)
     used = np.isin(ids, np.unique(F))
     ids = ids[used]
     inc = np.isin(F, ids).any(axis=1)
     sub_d = oracle.point_mesh_distance(V, F[inc], Q)
     g = g32.astype(np.float64)
-    g[sub_d <= 2e-2] = 0.0
+    g[sub_d <= 1e-3] = 0.0
     G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()[ids]
     G_ref = oracle.vertex_grad_subset(V, F, Q, g, ids)
-    grad_close(G, G_ref, "torus128 analytic")
-    # finite differences on a query subsample (list path)
+    # per-vertex cancellation scale (sum of |face contributions|) from the incident faces, which are
+    # all the faces the 64 vertices have: vertices away from the holes have an exact gradient of 0
+    # that FP32 reaches only up to a fraction of the terms that cancel
+    scale = oracle.winding_grad_scale(V, F[inc], Q, g)[ids]
+    grad_close(G, G_ref, "torus128 analytic", scale)
+    # finite differences on a query subsample (list path); central differences with h = 1e-4 have a
+    # truncation error ~ (h/d)^2, so here the upstream is masked within 1e-2 of the incident faces
     sub = meshgen.query_subsample(len(Q), 20000, seed=5)
     Qs = Q[sub].astype(np.float32)
-    gs = g[sub]
+    gs = g[sub].copy()
+    gs[sub_d[sub] <= 1e-2] = 0.0
     Gs = dv.dv_winding_backward(mesh, to_dev(gs.astype(np.float32), cuda_device),
                                 queries=to_dev(Qs, cuda_device)).cpu().numpy()[ids]
     fd = oracle.fd_vertex_grad(V, F, Qs, gs, ids, h=1e-4)
@@ -216,11 +223,12 @@ def test_shsphere256_full_size_open_adjoint_sampled(cuda_device):
     Q = oracle.grid_queries(grid.lo, grid.hi, grid.n)
     g = meshgen.upstream_gradient(len(Q), seed=1).astype(np.float64)
     inc = np.isin(F, ids).any(axis=1)
-    g[oracle.point_mesh_distance(V, F[inc], Q) <= 2e-2] = 0.0  # a superset of the 1e-3 band
+    g[oracle.point_mesh_distance(V, F[inc], Q) <= 1e-3] = 0.0  # the gradient bar's near-surface radius
     G = dv.dv_winding_backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()[ids]
     G_ref = oracle.vertex_grad_subset(V, F, Q, g, ids)
     assert np.linalg.norm(G_ref[:6], axis=1).min() > 0.0
-    grad_close(G, G_ref, "shsphere256 open, analytic")
+    scale = oracle.winding_grad_scale(V, F[inc], Q, g)[ids]  # exact for these vertices (all their faces)
+    grad_close(G, G_ref, "shsphere256 open, analytic", scale)
 
 
 def test_forward_and_adjoint_concurrently_on_two_streams(cuda_device):

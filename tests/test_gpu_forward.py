@@ -190,7 +190,7 @@ def test_shsphere256_full_size_sampled(cuda_device):
     w, occ, rep = dv.dv_voxelize_grid(mesh, grid, precision="mixed", report=True)
     w, occ = w.cpu().numpy(), occ.cpu().numpy()
     Q = oracle.grid_queries(grid.lo, grid.hi, grid.n)
-    idx = _sample_with_near(V, F, Q, 600, 150, 4000, seed=4)
+    idx = _sample_with_near(V, F, Q, 3000, 1000, 20000, seed=4)
     w64 = oracle.winding(V, F, Q[idx])
     d = oracle.point_mesh_distance(V, F, Q[idx])
     stats = check_forward(w[idx], w64, d, "mixed", occ[idx], "shsphere256")
