@@ -13,6 +13,7 @@ paper's remedy, the Eq. (4) dipole discretization, for w in the loss. Quality is
 with the exact voxelization (mixed precision): IoU of occupancy against the target.
 
     python -m paper_2407_11272_b300.morph [--steps 200] [--surrogate dipole|exact]
+                                          [--checkpoint FILE --checkpoint-every K [--resume]]
 
 runs the full configuration (icosphere with 40 962 vertices / 81 920 faces, radius 0.5; target a
 seeded union of 4 ellipsoids with semi-axes U[0.2, 0.5] on a 128^3 grid; lr 1e-3; sharpness 20;
@@ -107,8 +108,65 @@ def iou(occ: torch.Tensor, target: torch.Tensor) -> float:
     return float((a & b).sum().item()) / max(float((a | b).sum().item()), 1.0)
 
 
+def save_checkpoint(path: str, step: int, offsets: torch.Tensor, opt: torch.optim.Optimizer, losses: list) -> None:
+    """Write the optimization state after `step` completed steps: the offsets, the optimizer's
+    state (Adam moments and step counts) and the loss history. The file is written under a
+    temporary name and renamed, so an interrupted write leaves the previous checkpoint intact."""
+    import os
+
+    def to_cpu(x):
+        if isinstance(x, torch.Tensor):
+            return x.detach().cpu()
+        if isinstance(x, dict):
+            return {k: to_cpu(v) for k, v in x.items()}
+        if isinstance(x, list):
+            return [to_cpu(v) for v in x]
+        return x
+
+    state = {"step": int(step), "offsets": offsets.detach().cpu(), "opt": to_cpu(opt.state_dict()),
+             "losses": list(losses)}
+    tmp = f"{path}.tmp{os.getpid()}"
+    torch.save(state, tmp)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, offsets: torch.Tensor, opt: torch.optim.Optimizer):
+    """Restore a checkpoint written by save_checkpoint into `offsets` (in place) and `opt`;
+    returns (completed steps, loss history)."""
+    state = torch.load(path, map_location="cpu", weights_only=True)
+    with torch.no_grad():
+        offsets.copy_(state["offsets"].to(offsets.device))
+    opt.load_state_dict(state["opt"])  # moves the moments to the parameter's device
+    return int(state["step"]), list(state["losses"])
+
+
+def optimize(loss_of, offsets: torch.Tensor, opt: torch.optim.Optimizer, steps: int, checkpoint: str | None = None,
+             every: int = 0, resume: bool = False):
+    """Run `steps` optimizer steps on loss_of(offsets) in total. With `checkpoint`, the state is
+    saved every `every` steps and at the end; with `resume` and an existing checkpoint the loop
+    continues from the saved step, so an interrupted run resumed this way follows the same
+    trajectory as one that was never interrupted. Returns (loss history, steps run here)."""
+    import os
+
+    start, losses = 0, []
+    if checkpoint and resume and os.path.exists(checkpoint):
+        start, losses = load_checkpoint(checkpoint, offsets, opt)
+    for step in range(start, steps):
+        opt.zero_grad(set_to_none=True)
+        loss = loss_of(offsets)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+        if checkpoint and every > 0 and (step + 1) % every == 0 and step + 1 < steps:
+            save_checkpoint(checkpoint, step + 1, offsets, opt, losses)
+    if checkpoint:
+        save_checkpoint(checkpoint, steps, offsets, opt, losses)
+    return losses, steps - start
+
+
 def morph(V0: np.ndarray, F: np.ndarray, target: np.ndarray, grid: dv.Grid, steps: int = 200, lr: float = 1e-3,
-          sharpness: float = 20.0, lap_weight: float = 0.1, surrogate: str = "dipole", device="cuda"):
+          sharpness: float = 20.0, lap_weight: float = 0.1, surrogate: str = "dipole", device="cuda",
+          checkpoint: str | None = None, checkpoint_every: int = 0, resume: bool = False):
     dev = torch.device(device)
     V0d = torch.from_numpy(V0).to(dev)
     Fd = torch.from_numpy(F).to(dev)
@@ -139,20 +197,15 @@ def morph(V0: np.ndarray, F: np.ndarray, target: np.ndarray, grid: dv.Grid, step
     warm_opt = torch.optim.Adam([warm], lr=lr)
     loss_of(V0d + warm).backward()
     warm_opt.step()
-    losses = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(steps):
-        opt.zero_grad(set_to_none=True)
-        loss = loss_of(V0d + offsets)
-        loss.backward()
-        opt.step()
-        losses.append(float(loss.detach()))
+    losses, ran = optimize(lambda off: loss_of(V0d + off), offsets, opt, steps, checkpoint, checkpoint_every, resume)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     V = (V0d + offsets).detach()
     grad_norm = float(offsets.grad.norm()) if offsets.grad is not None else 0.0
-    return {"steps": steps, "steps_per_s": steps / dt, "initial_iou": iou0, "final_iou": exact_iou(V),
+    return {"steps": steps, "steps_run": ran, "steps_per_s": ran / dt if ran else None, "initial_iou": iou0,
+            "final_iou": exact_iou(V),
             "initial_loss": losses[0] if losses else None, "final_loss": losses[-1] if losses else None,
             "last_grad_norm": grad_norm, "surrogate": surrogate,
             "pairs_per_step": grid.num_queries * len(F)}
@@ -165,11 +218,15 @@ def main(argv=None):
     ap.add_argument("--surrogate", choices=["dipole", "exact"], default="dipole")
     ap.add_argument("--subdiv", type=int, default=6)
     ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--checkpoint", type=str, default=None, help="file for the offsets and Adam state")
+    ap.add_argument("--checkpoint-every", type=int, default=0, help="save every k steps (and at the end)")
+    ap.add_argument("--resume", action="store_true", help="continue from --checkpoint if it exists")
     a = ap.parse_args(argv)
     V0, F = meshgen.icosphere(a.subdiv, 0.5)
     grid = dv.Grid.cube(a.n)
     target = ellipsoid_union_target(grid)
-    res = morph(V0, F, target, grid, steps=a.steps, lr=a.lr, surrogate=a.surrogate)
+    res = morph(V0, F, target, grid, steps=a.steps, lr=a.lr, surrogate=a.surrogate, checkpoint=a.checkpoint,
+                checkpoint_every=a.checkpoint_every, resume=a.resume)
     res.update(template=f"icosphere k={a.subdiv} ({len(V0)} V, {len(F)} F, r=0.5)", grid=a.n,
                target="union of 4 seeded ellipsoids, semi-axes U[0.2,0.5]", lr=a.lr)
     print(json.dumps(res))
