@@ -18,6 +18,7 @@ Functions (each follows the passage named in ``oracle.c``):
 * ``winding_grad_scale(V, F, Q, g)``  per-vertex sum of |face contributions| (cancellation scale)
 * ``fd_vertex_grad(V, F, Q, g, ids)`` FP64 central differences of sum_q g_q W(q)
 * ``dipole_winding(V, F, Q)``         Eq. (4), naive dipole discretization
+* ``ray_winding_grid(V, F, lo, hi, n)``  closed meshes: w on a grid by signed ray crossings (Eq. (3))
 * ``flipped_duplication(V, F, eps)``  Algorithm 2, open mesh to thin closed shell
 
 All arrays are converted to float64 / int32 before the call; vertex inputs
@@ -73,6 +74,9 @@ def _load():
         lib.orc_winding_grad_scale.argtypes = mesh_q + [_d, _d, ctypes.c_int]
         lib.orc_grid_queries.argtypes = [_f, _f, _i32, _d]
         lib.orc_grid_points.argtypes = [_f, _f, _i32, _i64, _I64, _d]
+        lib.orc_ray_winding_grid.argtypes = [_d, _I64, _i32, _I64, _f, _f, _i32, ctypes.c_double, ctypes.c_double,
+                                             _i32, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int]
+        lib.orc_ray_winding_grid.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -196,6 +200,27 @@ def grid_points(lo, hi, n, cells) -> np.ndarray:
     _load().orc_grid_points(lo.ctypes.data_as(_f), hi.ctypes.data_as(_f), nn.ctypes.data_as(_i32),
                             c.ctypes.data_as(_i64), len(c), _dp(out))
     return out
+
+
+def ray_winding_grid(V, F, lo, hi, n, eps_bary: float = 1e-12, eps_x: float = 1e-9, threads: int = 0):
+    """Winding number of a CLOSED, consistently oriented mesh at every cell centre of the grid
+    (x fastest), by signed crossings of rays along +x (Eq. (3)), and a mask of the cells whose
+    count is undecided (a ray grazing an edge or vertex, or a centre within eps_x of a crossing).
+    Returns (w int32 [nx*ny*nz], undecided bool [nx*ny*nz])."""
+    V, F = _mesh(V, F)
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    nn = np.ascontiguousarray(n, dtype=np.int32)
+    total = int(nn[0]) * int(nn[1]) * int(nn[2])
+    w = np.empty(total, dtype=np.int32)
+    amb = np.empty(total, dtype=np.uint8)
+    st = _load().orc_ray_winding_grid(_dp(V), len(V), F.ctypes.data_as(_i32), len(F), lo.ctypes.data_as(_f),
+                                      hi.ctypes.data_as(_f), nn.ctypes.data_as(_i32), eps_bary, eps_x,
+                                      w.ctypes.data_as(_i32), amb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                      threads)
+    if st != 0:
+        raise MemoryError("orc_ray_winding_grid: out of host memory")
+    return w, amb.astype(bool)
 
 
 def occupancy(w: np.ndarray) -> np.ndarray:

@@ -22,6 +22,8 @@
  *   orc_point_mesh_distance   exact point-to-triangle Euclidean distance
  *   orc_fd_vertex_grad   central finite differences of Eq. (5) in FP64
  *   orc_dipole_winding   Eq. (4), the naive dipole discretization (§2.4)
+ *   orc_ray_winding_grid the winding number of a CLOSED mesh on a grid by signed ray
+ *                        crossings (Eq. (3)): a check of Eq. (5) that evaluates no solid angle
  *
  * Readings of the paper used here (each is pinned by a test):
  *   - Eq. (7) prints arctan and no factor 2; Algorithm 1 adds ATAN2(alpha, beta).
@@ -394,4 +396,132 @@ void orc_dipole_winding(const double *V, int64_t nv, const int32_t *F, int64_t n
         }
         w_out[i] = s / (4.0 * ORC_PI);
     }
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Winding number of a CLOSED, consistently oriented mesh at every cell centre of a grid, by
+ * counting signed crossings of rays (an independent check of Eq. (5) / Algorithm 1 that never
+ * evaluates a solid angle). For a closed surface and q off it, the winding number equals the
+ * signed number of times a ray from q crosses the surface (Eq. (3): the flux of E_q through the
+ * closed surface is 1 inside and 0 outside; a ray leaving the enclosed volume crosses a face
+ * whose outward normal points along the ray). Each row of cells (fixed y, z) gets one ray along
+ * +x: for every face whose projection onto the yz plane contains (y, z), the crossing abscissa
+ * x_c (barycentric interpolation) counts +1 if the face normal n = (v1 - v0) x (v2 - v0) has
+ * n_x > 0 and -1 if n_x < 0, and a cell with centre x gets the sum over crossings with x_c > x.
+ * A count is marked undecided (amb_out = 1) when its row passes within a relative barycentric
+ * distance eps_bary of an edge or vertex of a face in the projection, or when the centre lies
+ * within eps_x of a crossing (q on or next to the surface). Grid layout as orc_grid_queries.
+ */
+typedef struct {
+    double x;
+    int sign;
+} orc_crossing;
+
+static int orc_crossing_cmp(const void *a, const void *b) {
+    const double xa = ((const orc_crossing *)a)->x, xb = ((const orc_crossing *)b)->x;
+    return (xa > xb) - (xa < xb);
+}
+
+/* Rows j with centre lo + (j + 0.5) h inside [a, b], clamped to [0, n - 1]. */
+static void orc_row_range(double a, double b, double lo, double h, int32_t n, int64_t *j0, int64_t *j1) {
+    double s = ceil((a - lo) / h - 0.5), e = floor((b - lo) / h - 0.5);
+    if (s < 0) s = 0;
+    if (e > n - 1) e = n - 1;
+    *j0 = (int64_t)s;
+    *j1 = (int64_t)e;
+}
+
+int orc_ray_winding_grid(const double *V, int64_t nv, const int32_t *F, int64_t nf, const float *lo, const float *hi,
+                         const int32_t *n, double eps_bary, double eps_x, int32_t *w_out, uint8_t *amb_out,
+                         int nthreads) {
+    (void)nv;
+    set_threads(nthreads);
+    double h[3];
+    for (int k = 0; k < 3; ++k) h[k] = ((double)hi[k] - (double)lo[k]) / (double)n[k];
+    const int64_t nrows = (int64_t)n[1] * n[2];
+    int64_t *count = (int64_t *)calloc((size_t)nrows + 1, sizeof(int64_t));
+    uint8_t *row_amb = (uint8_t *)calloc((size_t)nrows, 1);
+    if (!count || !row_amb) {
+        free(count);
+        free(row_amb);
+        return 1;
+    }
+    /* two passes over the faces: count the crossings of each row, then store them */
+    orc_crossing *cr = NULL;
+    int64_t *fill = NULL;
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t f = 0; f < nf; ++f) {
+            const double *a = vtx(V, F, f, 0), *b = vtx(V, F, f, 1), *c = vtx(V, F, f, 2);
+            const double d = (b[1] - a[1]) * (c[2] - a[2]) - (c[1] - a[1]) * (b[2] - a[2]); /* n_x */
+            if (d == 0.0) continue; /* seen edge-on from the rays: its edges decide */
+            const double ymin = fmin(a[1], fmin(b[1], c[1])), ymax = fmax(a[1], fmax(b[1], c[1]));
+            const double zmin = fmin(a[2], fmin(b[2], c[2])), zmax = fmax(a[2], fmax(b[2], c[2]));
+            const double gy = 1e-9 * (1.0 + ymax - ymin), gz = 1e-9 * (1.0 + zmax - zmin);
+            int64_t y0, y1, z0, z1;
+            orc_row_range(ymin - gy, ymax + gy, lo[1], h[1], n[1], &y0, &y1);
+            orc_row_range(zmin - gz, zmax + gz, lo[2], h[2], n[2], &z0, &z1);
+            for (int64_t iz = z0; iz <= z1; ++iz)
+                for (int64_t iy = y0; iy <= y1; ++iy) {
+                    const double y = (double)lo[1] + ((double)iy + 0.5) * h[1];
+                    const double z = (double)lo[2] + ((double)iz + 0.5) * h[2];
+                    const double l1 = ((y - a[1]) * (c[2] - a[2]) - (c[1] - a[1]) * (z - a[2])) / d;
+                    const double l2 = ((b[1] - a[1]) * (z - a[2]) - (y - a[1]) * (b[2] - a[2])) / d;
+                    const double l0 = 1.0 - l1 - l2;
+                    const double m = fmin(l0, fmin(l1, l2));
+                    const int64_t row = iz * n[1] + iy;
+                    if (m > eps_bary) {
+                        if (pass == 0) {
+#pragma omp atomic
+                            count[row + 1] += 1;
+                        } else {
+                            int64_t slot;
+#pragma omp atomic capture
+                            slot = fill[row]++;
+                            cr[slot].x = l0 * a[0] + l1 * b[0] + l2 * c[0];
+                            cr[slot].sign = d > 0 ? 1 : -1;
+                        }
+                    } else if (pass == 0 && m > -eps_bary) {
+                        row_amb[row] = 1; /* the ray grazes an edge or a vertex */
+                    }
+                }
+        }
+        if (pass == 0) {
+            for (int64_t r = 0; r < nrows; ++r) count[r + 1] += count[r];
+            cr = (orc_crossing *)malloc(sizeof(orc_crossing) * (size_t)(count[nrows] > 0 ? count[nrows] : 1));
+            fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nrows);
+            if (!cr || !fill) {
+                free(cr);
+                free(fill);
+                free(count);
+                free(row_amb);
+                return 1;
+            }
+            for (int64_t r = 0; r < nrows; ++r) fill[r] = count[r];
+        }
+    }
+    /* per row: crossings in x order, then each centre counts those beyond it */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < nrows; ++r) {
+        orc_crossing *c = cr + count[r];
+        const int64_t m = count[r + 1] - count[r];
+        qsort(c, (size_t)m, sizeof(orc_crossing), orc_crossing_cmp);
+        int64_t k = m; /* crossings c[k..m) lie beyond the current centre */
+        int32_t beyond = 0;
+        for (int64_t ix = n[0] - 1; ix >= 0; --ix) {
+            const double x = (double)lo[0] + (0.5 + (double)ix) * h[0];
+            while (k > 0 && c[k - 1].x > x) beyond += c[--k].sign;
+            int near = 0;
+            if (k > 0 && x - c[k - 1].x <= eps_x) near = 1;
+            if (k < m && c[k].x - x <= eps_x) near = 1;
+            const int64_t idx = r * n[0] + ix;
+            w_out[idx] = beyond;
+            amb_out[idx] = (uint8_t)(row_amb[r] || near);
+        }
+    }
+    free(cr);
+    free(fill);
+    free(count);
+    free(row_amb);
+    return 0;
 }

@@ -36,6 +36,9 @@ MUTANTS = {
     "dipole_unnormalized_normal": ("double nrm[3] = {m[0] / (2 * area), m[1] / (2 * area), m[2] / (2 * area)};",
                                    "double nrm[3] = {m[0], m[1], m[2]};"),
     "dipole_r_squared": ("/ (r * r * r) * area", "/ (r * r) * area"),
+    # ray crossings of a closed mesh: the crossing's sign from the wrong normal component's sign
+    "ray_sign": ("cr[slot].sign = d > 0 ? 1 : -1;", "cr[slot].sign = d < 0 ? 1 : -1;"),
+    "ray_beyond_side": ("while (k > 0 && c[k - 1].x > x)", "while (k > 0 && c[k - 1].x < x)"),
 }
 
 _d = ctypes.POINTER(ctypes.c_double)
@@ -90,6 +93,22 @@ def _dipole(lib, V, F, Q):
     return out
 
 
+def _ray(lib, V, F, lo, hi, n):
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    lo, hi = np.asarray(lo, np.float32), np.asarray(hi, np.float32)
+    nn = np.asarray(n, np.int32)
+    w = np.empty(int(np.prod(nn)), np.int32)
+    amb = np.empty(int(np.prod(nn)), np.uint8)
+    lib.orc_ray_winding_grid(V.ctypes.data_as(_d), ctypes.c_int64(len(V)), F.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                             ctypes.c_int64(len(F)), lo.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             hi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.c_double(1e-12),
+                             ctypes.c_double(1e-9), w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                             amb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), ctypes.c_int(1))
+    return w, amb.astype(bool)
+
+
 def _grid(lib, n):
     lo = np.full(3, -1, np.float32)
     hi = np.full(3, 1, np.float32)
@@ -142,9 +161,26 @@ def _pins_pass(lib) -> bool:
     ok &= np.allclose(_dipole(lib, Vt, np.array([[0, 1, 2]]), Qt),
                       [area / (4 * math.pi * d * d), area * d / (4 * math.pi * (d * d + t * t) ** 1.5)],
                       rtol=1e-12, atol=0)
+    # closed convex mesh by ray crossings: 1 inside, 0 outside (the cube's plane-side indicator)
+    Vq, Fq = meshgen.cube(0.45, centre=(0.02, 0.01, -0.03))
+    wq, uq = _ray(lib, Vq, Fq, (-1, -1, -1), (1, 1, 1), (9, 8, 7))
+    Qq = _grid_any(lib, (9, 8, 7))
+    inq = np.all(np.abs(Qq - np.array([0.02, 0.01, -0.03])) < 0.45, axis=1)
+    ok &= bool(np.array_equal(wq[~uq], inq[~uq].astype(np.int32))) and not uq.any()  # generic: all decided
     ok &= np.allclose(_grid(lib, 4)[0], [-0.75, -0.75, -0.75])
     ok &= np.allclose(_grid_points(lib, (4, 2, 8), [4 * 2 * 8 - 1]), [[0.75, 0.5, 0.875]])
     return bool(ok)
+
+
+def _grid_any(lib, n):
+    lo = np.full(3, -1, np.float32)
+    hi = np.full(3, 1, np.float32)
+    nn = np.asarray(n, np.int32)
+    out = np.empty((int(np.prod(nn)), 3))
+    lib.orc_grid_queries(lo.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                         hi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                         nn.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), out.ctypes.data_as(_d))
+    return out
 
 
 def _grid_points(lib, n, cells):

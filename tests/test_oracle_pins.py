@@ -416,3 +416,50 @@ def test_flipped_duplication_closes_open_cap():
     # without the duplication the open cap leaves that point far from binary
     w1 = oracle.winding(V, F, qs[:1])[0]
     assert 0.1 < w1 < 0.9
+
+
+# ---------------------------------------------------------------- closed meshes by ray crossings
+
+@pytest.mark.parametrize("mesh", ["tetra", "cube", "ico2"])
+def test_ray_winding_of_convex_mesh_is_indicator(mesh):
+    # a closed convex mesh: the signed ray-crossing count is the plane-side indicator, on an
+    # anisotropic grid over an off-centre box; reversing every face negates it
+    V, F = {"tetra": lambda: meshgen.regular_tetrahedron(0.5, centre=(0.03, -0.02, 0.05)),
+            "cube": lambda: meshgen.cube(0.45, centre=(0.02, 0.01, -0.03)),
+            "ico2": lambda: meshgen.icosphere(2, 0.8)}[mesh]()
+    lo, hi, n = (-0.97, -1.01, -0.93), (1.03, 0.99, 1.07), (23, 19, 17)
+    w, und = oracle.ray_winding_grid(V, F, lo, hi, n)
+    Q = oracle.grid_queries(lo, hi, n)
+    inside, dplane = _inside_convex(V, F, Q)
+    keep = (dplane > 1e-6) & ~und
+    assert keep.sum() > 0.95 * len(Q)
+    assert np.array_equal(w[keep], inside[keep].astype(np.int32))
+    wr, undr = oracle.ray_winding_grid(V, F[:, ::-1], lo, hi, n)
+    assert np.array_equal(wr[keep & ~undr], -w[keep & ~undr])
+
+
+def test_ray_winding_marks_rays_through_a_vertex_undecided():
+    # a vertex placed exactly on a row's ray: that row's counts are undecided, the others are not
+    # (a generically rotated tetrahedron, so that no other row or centre meets an edge or face)
+    V, F = meshgen.regular_tetrahedron(0.5)
+    R, _ = np.linalg.qr(np.random.default_rng(21).normal(size=(3, 3)))
+    V = V.astype(np.float64) @ R.T
+    lo, hi, n = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), (16, 16, 16)
+    h = 2.0 / 16
+    V = V + np.array([0.0137, (-1.0 + 10.5 * h) - V[0, 1], (-1.0 + 5.5 * h) - V[0, 2]])
+    w, und = oracle.ray_winding_grid(V, F, lo, hi, n)
+    rows = und.reshape(16, 16, 16).any(axis=2)  # [iz, iy]
+    assert rows[5, 10] and rows.sum() == 1
+    inside, _ = _inside_convex(V, F, oracle.grid_queries(lo, hi, n))
+    assert np.array_equal(w[~und], inside[~und].astype(np.int32))
+
+
+def test_ray_winding_matches_solid_angles_on_closed_nonconvex_mesh():
+    # closed jittered torus (no faces deleted): the signed crossing count equals the solid-angle
+    # winding number of Eq. (5) rounded, wherever the count is decided
+    V, F = meshgen.jittered_torus(nu=40, nv=20, sigma=0.01, delete_frac=0.0, seed=2)
+    lo, hi, n = (-1.0, -1.0, -0.5), (1.0, 1.0, 0.5), (26, 24, 13)
+    w, und = oracle.ray_winding_grid(V, F, lo, hi, n)
+    w64 = oracle.winding(V, F, oracle.grid_queries(lo, hi, n))
+    assert np.abs(w64[~und] - w[~und]).max() < 1e-9
+    assert (w == 1).sum() > 100 and (w == 0).sum() > 100
