@@ -98,6 +98,21 @@ typedef struct {
 /* Version of this ABI (DV_ABI_VERSION). */
 int dv_abi_version(void);
 
+/* Report of the bounds checks of the debug build (no counterpart in the paper).
+ * The debug build of this library (libdv_debug.so, the same sources compiled
+ * with -DDV_DEBUG) checks the index of every indexed global access of the hot
+ * kernels against its buffer's length; an index outside it is counted, the
+ * first is recorded, and the access is skipped instead of faulting. Outputs
+ * (host pointers, all required): *count = the number of rejected accesses
+ * since the last clear; *site, *index, *bound = the first one's site code
+ * (1 forward tile copy, 2 forward output, 3 flagged list, 4 split partials,
+ * 5 FP64-pass event, 6 FP64-pass query, 7 adjoint record, 8 upstream, 9 face
+ * gradient, 10 vertex gather, 11 near-surface flag, 12 packing), its index and
+ * the length it was checked against. clear != 0 resets the records. Reads
+ * device memory synchronously (waits for the device). The release build
+ * returns DV_ERR_UNSUPPORTED. */
+dv_status dv_debug_report(int64_t *count, int32_t *site, int64_t *index, int64_t *bound, int clear);
+
 /* Self-test of the bounded waits used by every shared-memory copy pipeline of
  * this library (no counterpart in the paper). One CTA waits on a barrier phase
  * with a limit of limit_us microseconds (1 .. 1e7). With arrive != 0 the phase
@@ -294,8 +309,10 @@ typedef struct {
  * are identical to running it alone (same kernels, same launch plans). Used by
  * the request server (continuous batching). Scratch is reserved on `stream`
  * before capture; the meshes must not be used by other work until the batch is
- * done, and a mesh may appear only once per batch. Host calls are serialized
- * by a lock. No counterpart in the paper (serving is this library's addition). */
+ * done, and a mesh may appear only once per batch. `stream` must be a created
+ * stream: the legacy and per-thread default streams cannot be captured and are
+ * rejected with DV_ERR_INVALID_ARG. Host calls are serialized by a lock. No
+ * counterpart in the paper (serving is this library's addition). */
 dv_status dv_run_batch(const dv_request *reqs, int n, dv_precision prec, void *stream);
 
 /* Eq. (4), the naive dipole discretization used by the paper for mesh morphing

@@ -60,6 +60,17 @@ static std::mutex g_prof_mu;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Readers of the debug build's per-translation-unit bounds records (registered at load time).
+static std::vector<DebugFetchFn> &debug_fetchers() {
+    static std::vector<DebugFetchFn> v;
+    return v;
+}
+
+int debug_register(DebugFetchFn fn) {
+    debug_fetchers().push_back(fn);
+    return (int)debug_fetchers().size();
+}
+
 dv_status report_error(dv_status s, const char *msg) { return fail(s, "%s", msg); }
 
 void prof_begin(const char *name, cudaStream_t s) {
@@ -295,6 +306,30 @@ extern "C" {
 
 int dv_abi_version(void) { return DV_ABI_VERSION; }
 
+dv_status dv_debug_report(int64_t *count, int32_t *site, int64_t *index, int64_t *bound, int clear) {
+    if (!count || !site || !index || !bound) return fail(DV_ERR_INVALID_ARG, "null output pointer");
+    *count = 0;
+    *site = 0;
+    *index = *bound = 0;
+#ifdef DV_DEBUG
+    for (dv::DebugFetchFn fn : dv::debug_fetchers()) {
+        dv::DebugRecord r{};
+        const cudaError_t e = fn(&r, clear != 0);
+        if (e != cudaSuccess) return fail(DV_ERR_CUDA, "debug record: %s", cudaGetErrorString(e));
+        if (r.count && *count == 0) {
+            *site = (int32_t)r.site;
+            *index = r.index;
+            *bound = r.bound;
+        }
+        *count += (int64_t)r.count;
+    }
+    return DV_OK;
+#else
+    (void)clear;
+    return fail(DV_ERR_UNSUPPORTED, "bounds checks exist only in the debug build (libdv_debug.so)");
+#endif
+}
+
 const char *dv_status_string(dv_status s) {
     switch (s) {
         case DV_OK: return "DV_OK";
@@ -404,8 +439,9 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
         return bail(fail(DV_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e)));
     if ((e = dv::prepare_backward_kernels()))
         return bail(fail(DV_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e)));
-    if ((e = dv::launch_pack(d_verts, m->faces, nf, m->rec, m->rec64, s)) ||
-        (e = dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64, s)) ||
+    if ((e = dv::launch_pack(d_verts, nv, m->faces, nf, m->rec, m->rec64, s)) ||
+        (e = dv::launch_pack_strips(d_verts, nv, nf, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec,
+                                         m->srec64, s)) ||
         (e = dv::launch_pack_pairs(m->rec, m->ptopo, m->np, m->prec, s)))
         return bail(fail(DV_ERR_CUDA, "pack: %s", cudaGetErrorString(e)));
     // the host vectors above must outlive the async uploads
@@ -434,9 +470,9 @@ dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
     if (!m || !d_verts) return fail(DV_ERR_INVALID_ARG, "mesh or vertex pointer is NULL");
     DeviceGuard dg(m->device);
     m->last_stream = (cudaStream_t)stream;
-    DV_CUDA(dv::launch_pack(d_verts, m->faces, m->nf, m->rec, m->rec64, (cudaStream_t)stream));
-    DV_CUDA(dv::launch_pack_strips(d_verts, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec, m->srec64,
-                                   (cudaStream_t)stream));
+    DV_CUDA(dv::launch_pack(d_verts, m->nv, m->faces, m->nf, m->rec, m->rec64, (cudaStream_t)stream));
+    DV_CUDA(dv::launch_pack_strips(d_verts, m->nv, m->nf, m->ev_vert, m->ev_face, m->ne, m->rec, m->rec64, m->srec,
+                                   m->srec64, (cudaStream_t)stream));
     DV_CUDA(dv::launch_pack_pairs(m->rec, m->ptopo, m->np, m->prec, (cudaStream_t)stream));
     if (m->bnd_dev)
         DV_CUDA(dv::launch_pack_boundary(m->rec, m->vtx_ptr, m->vtx_corner, m->bnd_edges, m->nb, m->bnd_rec,
@@ -725,6 +761,9 @@ dv_status dv_run_batch(const dv_request *reqs, int n, dv_precision prec, void *s
     if (n == 0) return DV_OK;
     if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED && prec != DV_PREC_FP16)
         return fail(DV_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (stream == nullptr || (cudaStream_t)stream == cudaStreamLegacy || (cudaStream_t)stream == cudaStreamPerThread)
+        return fail(DV_ERR_INVALID_ARG, "dv_run_batch captures a CUDA graph on `stream`: pass a created stream, "
+                                        "not the default stream");
     int dev = -1;
     for (int i = 0; i < n; ++i) {
         const dv_request &r = reqs[i];

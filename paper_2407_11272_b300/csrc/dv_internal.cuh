@@ -174,6 +174,66 @@ __device__ __forceinline__ void set_error(int *err, int code) {
     if (err) atomicCAS(err, 0, code);
 }
 
+// ------------------------------------------------------------------------------------------
+// Bounds checks of the debug build (libdv_debug.so, compiled with -DDV_DEBUG). The indexed global
+// accesses of the hot kernels go through DV_INB(index, length, site). In the debug build an index
+// outside [0, length) is counted, the first one is recorded with its site and length in this
+// translation unit's device record, and the access is skipped: a wrong index shows up as a
+// report (dv_debug_report), never as a memory fault or a trap. Release builds compile every check
+// to `true`.
+enum DebugSite : int {
+    kSiteFwdTile = 1,      // forward: copy of a tile of face / strip records
+    kSiteFwdOut = 2,       // forward epilogue: w, occupancy, near flag of a query
+    kSiteFwdFlagList = 3,  // forward epilogue: slot of the flagged-query list
+    kSiteFwdPartial = 4,   // forward: per-split partial sums
+    kSiteReevalEvent = 5,  // FP64 pass: strip event record
+    kSiteReevalQuery = 6,  // FP64 pass: flagged-list entry and the query it names
+    kSiteBwdRecord = 7,    // adjoint: pair or face record, unpaired-face list
+    kSiteBwdUpstream = 8,  // adjoint: upstream value of a query
+    kSiteBwdFaceGrad = 9,  // adjoint: per-split face gradient
+    kSiteGather = 10,      // vertex gather: CSR entry, face gradient, dL/dV
+    kSiteNear = 11,        // near-surface flag of a grid query
+    kSitePack = 12,        // packing: vertex of a face or of a strip event
+};
+
+struct DebugRecord {
+    unsigned long long count;
+    long long site, index, bound;
+};
+using DebugFetchFn = cudaError_t (*)(DebugRecord *out, bool clear);
+// Registers one translation unit's record reader (dv_api.cu); returns the count so far.
+int debug_register(DebugFetchFn fn);
+
+#ifdef DV_DEBUG
+namespace {
+__device__ DebugRecord g_debug_record;  // this translation unit's record
+
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int site) {
+    if (i >= 0 && i < n) return true;
+    if (atomicAdd(&g_debug_record.count, 1ull) == 0ull) {
+        g_debug_record.site = site;
+        g_debug_record.index = i;
+        g_debug_record.bound = n;
+    }
+    return false;
+}
+
+cudaError_t debug_fetch(DebugRecord *out, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_debug_record, sizeof(DebugRecord));
+    if (e == cudaSuccess && clear) {
+        const DebugRecord z{};
+        e = cudaMemcpyToSymbol(g_debug_record, &z, sizeof(DebugRecord));
+    }
+    return e;
+}
+
+[[maybe_unused]] const int g_debug_registered = debug_register(debug_fetch);
+}  // namespace
+#define DV_INB(i, n, site) (::dv::in_bounds((long long)(i), (long long)(n), (int)(site)))
+#else
+#define DV_INB(i, n, site) true
+#endif
+
 }  // namespace dv
 
 // ------------------------------------------------------------------------------------------
@@ -199,13 +259,13 @@ dv_status report_error(dv_status s, const char *msg);
 // pack.cu
 cudaError_t launch_validate(const float *verts, int64_t nv, const int32_t *faces, int64_t nf, int *d_bad,
                             cudaStream_t s);
-cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, FaceRec *rec, FaceRec64 *rec64,
-                        cudaStream_t s);
+cudaError_t launch_pack(const float *verts, int64_t nv, const int32_t *faces, int64_t nf, FaceRec *rec,
+                        FaceRec64 *rec64, cudaStream_t s);
 // Strip events from the vertices and the packed face records (normals copied from rec/rec64, so
 // both orders see the same n_f). Runs after launch_pack on the same stream.
-cudaError_t launch_pack_strips(const float *verts, const int32_t *ev_vert, const int32_t *ev_face, int64_t ne,
-                               const FaceRec *rec, const FaceRec64 *rec64, StripRec *srec, StripRec64 *srec64,
-                               cudaStream_t s);
+cudaError_t launch_pack_strips(const float *verts, int64_t nv, int64_t nf, const int32_t *ev_vert,
+                               const int32_t *ev_face, int64_t ne, const FaceRec *rec, const FaceRec64 *rec64,
+                               StripRec *srec, StripRec64 *srec64, cudaStream_t s);
 
 // winding_bnd.cu: the adjoint from the mesh's boundary edges.
 struct BndPlan {

@@ -91,7 +91,9 @@ __global__ void near_grid_kernel(const FaceRec *__restrict__ rec, int64_t nf, Gr
                 const int iy = i0[1] + (int)(t / sx);
                 const float px = __fmaf_rn((float)ix + 0.5f, g.h[0], g.lo[0]);
                 const float py = __fmaf_rn((float)iy + 0.5f, g.h[1], g.lo[1]);
-                if (tri_d2(px, py, pz, r) <= T2) flag[((int64_t)iz * g.n[1] + iy) * g.n[0] + ix] = 1;
+                const int64_t qi = ((int64_t)iz * g.n[1] + iy) * g.n[0] + ix;
+                if (tri_d2(px, py, pz, r) <= T2 && DV_INB(qi, (int64_t)g.n[0] * g.n[1] * g.n[2], kSiteNear))
+                    flag[qi] = 1;
             }
         }
     }
@@ -202,7 +204,7 @@ __global__ void bin_scatter_kernel(int64_t nq, const int *__restrict__ qcell, co
 
 // One warp per (face, z-group of bin layers): test the queries in the bins that the face's
 // grown box overlaps.
-__global__ void near_binned_kernel(const FaceRec *__restrict__ rec, int64_t nf, const float *__restrict__ q,
+__global__ void near_binned_kernel(const FaceRec *__restrict__ rec, int64_t nf, const float *__restrict__ q, int64_t nq,
                                    const float *__restrict__ box, const int *__restrict__ offsets,
                                    const int *__restrict__ sorted, uint8_t *__restrict__ flag) {
     const int lane = threadIdx.x & 31;
@@ -230,6 +232,7 @@ __global__ void near_binned_kernel(const FaceRec *__restrict__ rec, int64_t nf, 
                 const int cell = (cz * kBinG + c0[1] + t / sx) * kBinG + c0[0] + t % sx;
                 for (int j = offsets[cell]; j < offsets[cell + 1]; ++j) {
                     const int i = sorted[j];
+                    if (!DV_INB(i, nq, kSiteNear)) continue;
                     if (tri_d2(q[3 * (int64_t)i], q[3 * (int64_t)i + 1], q[3 * (int64_t)i + 2], r) <= T2) flag[i] = 1;
                 }
             }
@@ -257,7 +260,7 @@ cudaError_t launch_near_surface(const FaceRec *rec, int64_t nf, const GridF *g, 
         bin_count_kernel<<<qb, 256, 0, s>>>(queries, nq, box, counts, qcell);
         bin_scan_kernel<<<1, kBoxThreads, 0, s>>>(counts, offsets);
         bin_scatter_kernel<<<qb, 256, 0, s>>>(nq, qcell, offsets, counts, sorted);
-        near_binned_kernel<<<dim3((unsigned)nfb, 4), 256, 0, s>>>(rec, nf, queries, box, offsets, sorted, near_flag);
+        near_binned_kernel<<<dim3((unsigned)nfb, 4), 256, 0, s>>>(rec, nf, queries, nq, box, offsets, sorted, near_flag);
         for (int k = 0; k < 5; ++k) count_launch();
         prof_end("near_surface_list", s);
     } else {

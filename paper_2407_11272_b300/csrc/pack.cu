@@ -21,11 +21,12 @@ __global__ void validate_kernel(const float *__restrict__ verts, int64_t nv, con
 // Per face: gather the three vertices, compute n = (v1 - v0) x (v2 - v0) in FP64 (products of
 // FP32 values are exact in FP64), and store the FP32 record (normal scaled by 8) and the FP64
 // record used by the re-evaluation pass.
-__device__ __forceinline__ void pack_one(const float *__restrict__ verts, const int32_t *__restrict__ faces, int64_t f,
-                                         FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
+__device__ __forceinline__ void pack_one(const float *__restrict__ verts, int64_t nv, const int32_t *__restrict__ faces,
+                                         int64_t f, FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
     double v[3][3];
     for (int k = 0; k < 3; ++k) {
         int64_t id = faces[3 * f + k];
+        if (!DV_INB(id, nv, kSitePack)) id = 0;
         for (int c = 0; c < 3; ++c) v[k][c] = (double)verts[3 * id + c];
     }
     double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
@@ -43,10 +44,10 @@ __device__ __forceinline__ void pack_one(const float *__restrict__ verts, const 
     rec64[f] = r64;
 }
 
-__global__ void pack_kernel(const float *__restrict__ verts, const int32_t *__restrict__ faces, int64_t nf,
+__global__ void pack_kernel(const float *__restrict__ verts, int64_t nv, const int32_t *__restrict__ faces, int64_t nf,
                             FaceRec *__restrict__ rec, FaceRec64 *__restrict__ rec64) {
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x)
-        pack_one(verts, faces, f, rec, rec64);
+        pack_one(verts, nv, faces, f, rec, rec64);
 }
 
 // dverts[v] = sum over the faces f incident to v (corner k) and over the query splits s of
@@ -58,7 +59,9 @@ __global__ void gather_dverts_kernel(const float *__restrict__ face_grad, int ns
     if (v >= nv) return;
     double s0 = 0, s1 = 0, s2 = 0;
     for (int32_t c = vtx_ptr[v]; c < vtx_ptr[v + 1]; ++c) {
+        if (!DV_INB(c, 3 * nf, kSiteGather)) break;
         int32_t corner = vtx_corner[c];
+        if (!DV_INB(corner, 3 * nf, kSiteGather)) continue;
         int64_t f = corner / 3;
         int k = corner - 3 * (int)f;
         for (int s = 0; s < nsplit; ++s) {
@@ -85,7 +88,9 @@ __global__ void gather_dverts_warp_kernel(const float *__restrict__ face_grad, i
     for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < nv; v += warps) {  // whole warps
         double s0 = 0, s1 = 0, s2 = 0;
         for (int32_t c = vtx_ptr[v]; c < vtx_ptr[v + 1]; ++c) {
+            if (!DV_INB(c, 3 * nf, kSiteGather)) break;
             const int32_t corner = vtx_corner[c];
+            if (!DV_INB(corner, 3 * nf, kSiteGather)) continue;
             const int64_t f = corner / 3;
             const int k = corner - 3 * (int)f;
             for (int s = lane; s < nsplit; s += 32) {
@@ -124,10 +129,10 @@ cudaError_t launch_validate(const float *verts, int64_t nv, const int32_t *faces
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, FaceRec *rec, FaceRec64 *rec64,
-                        cudaStream_t s) {
+cudaError_t launch_pack(const float *verts, int64_t nv, const int32_t *faces, int64_t nf, FaceRec *rec,
+                        FaceRec64 *rec64, cudaStream_t s) {
     prof_begin("pack_faces", s);
-    pack_kernel<<<blocks_for(nf, 256), 256, 0, s>>>(verts, faces, nf, rec, rec64);
+    pack_kernel<<<blocks_for(nf, 256), 256, 0, s>>>(verts, nv, faces, nf, rec, rec64);
     count_launch();
     prof_end("pack_faces", s);
     return cudaGetLastError();
@@ -135,12 +140,15 @@ cudaError_t launch_pack(const float *verts, const int32_t *faces, int64_t nf, Fa
 
 // One strip event: the vertex (FP32 as given, and widened to FP64) and, for an event that
 // completes a face, that face's normal taken from the packed face records.
-__device__ __forceinline__ void pack_strip_one(const float *__restrict__ verts, const int32_t *__restrict__ ev_vert,
-                                               const int32_t *__restrict__ ev_face, int64_t e,
+__device__ __forceinline__ void pack_strip_one(const float *__restrict__ verts, int64_t nv, int64_t nf,
+                                               const int32_t *__restrict__ ev_vert, const int32_t *__restrict__ ev_face,
+                                               int64_t e,
                                                const FaceRec *__restrict__ rec, const FaceRec64 *__restrict__ rec64,
                                                StripRec *__restrict__ srec, StripRec64 *__restrict__ srec64) {
-    const int64_t v = ev_vert[e];
-    const int32_t f = ev_face[e];
+    int64_t v = ev_vert[e];
+    int32_t f = ev_face[e];
+    if (!DV_INB(v, nv, kSitePack)) v = 0;
+    if (f >= 0 && !DV_INB(f, nf, kSitePack)) f = -1;
     const float x = verts[3 * v], y = verts[3 * v + 1], z = verts[3 * v + 2];
     StripRec r;
     StripRec64 r64;
@@ -164,20 +172,22 @@ __device__ __forceinline__ void pack_strip_one(const float *__restrict__ verts, 
     srec64[e] = r64;
 }
 
-__global__ void pack_strips_kernel(const float *__restrict__ verts, const int32_t *__restrict__ ev_vert,
+__global__ void pack_strips_kernel(const float *__restrict__ verts, int64_t nv, int64_t nf,
+                                   const int32_t *__restrict__ ev_vert,
                                    const int32_t *__restrict__ ev_face, int64_t ne, const FaceRec *__restrict__ rec,
                                    const FaceRec64 *__restrict__ rec64, StripRec *__restrict__ srec,
                                    StripRec64 *__restrict__ srec64) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x)
-        pack_strip_one(verts, ev_vert, ev_face, e, rec, rec64, srec, srec64);
+        pack_strip_one(verts, nv, nf, ev_vert, ev_face, e, rec, rec64, srec, srec64);
 }
 
-cudaError_t launch_pack_strips(const float *verts, const int32_t *ev_vert, const int32_t *ev_face, int64_t ne,
-                               const FaceRec *rec, const FaceRec64 *rec64, StripRec *srec, StripRec64 *srec64,
-                               cudaStream_t s) {
+cudaError_t launch_pack_strips(const float *verts, int64_t nv, int64_t nf, const int32_t *ev_vert,
+                               const int32_t *ev_face, int64_t ne, const FaceRec *rec, const FaceRec64 *rec64,
+                               StripRec *srec, StripRec64 *srec64, cudaStream_t s) {
     if (ne == 0) return cudaSuccess;
     prof_begin("pack_strips", s);
-    pack_strips_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(verts, ev_vert, ev_face, ne, rec, rec64, srec, srec64);
+    pack_strips_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(verts, nv, nf, ev_vert, ev_face, ne, rec, rec64, srec,
+                                                           srec64);
     count_launch();
     prof_end("pack_strips", s);
     return cudaGetLastError();

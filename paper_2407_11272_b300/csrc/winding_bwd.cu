@@ -351,7 +351,7 @@ __device__ __forceinline__ void for_each_row(const BwdArgs &a, float *wf, RowFn 
             for (int64_t i = threadIdx.x; i < len; i += kBwdThreads) {
                 const int ix = whole ? (int)(i % nx) : x0 + (int)i;
                 wf[4 * (i >> 1) + (i & 1)] = -__fmaf_rn((float)ix + 0.5f, a.g.h[0], a.g.lo[0]);
-                wf[4 * (i >> 1) + 2 + (i & 1)] = a.upstream[base + i];
+                wf[4 * (i >> 1) + 2 + (i & 1)] = DV_INB(base + i, a.nq, kSiteBwdUpstream) ? a.upstream[base + i] : 0.f;
             }
             __syncthreads();
             const int64_t nr = whole ? rend - rw : 1;
@@ -404,7 +404,8 @@ __device__ __forceinline__ void bwd_grid_singles(const BwdArgs &a, float *wf, fl
     const int64_t count = a.singles ? a.nsingle : a.nf;
     const int64_t idx = ((int64_t)blockIdx.x - a.pblocks) * kBwdThreads + threadIdx.x;
     const int64_t ic = idx < count ? idx : count - 1;
-    const int64_t f = a.singles ? (int64_t)a.singles[ic] : ic;
+    int64_t f = a.singles ? (DV_INB(ic, a.nsingle, kSiteBwdRecord) ? (int64_t)a.singles[ic] : 0) : ic;
+    if (!DV_INB(f, a.nf, kSiteBwdRecord)) f = 0;
     const FaceF F = load_face(a.rec, f);
     FaceF2 F2;
     F2.v0x = bc2(F.v0x);
@@ -439,7 +440,8 @@ __device__ __forceinline__ void bwd_grid_singles(const BwdArgs &a, float *wf, fl
         }
         if (!ok) row_guarded(F, qy, qz, wf, i0, xlen, ks);
     });
-    if (idx < count) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+    if (idx < count && DV_INB(f, a.nf, kSiteBwdFaceGrad))
+        write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
 // A CTA of edge-sharing face pairs: thread t owns pair t; its two faces keep separate sums
@@ -447,7 +449,7 @@ __device__ __forceinline__ void bwd_grid_singles(const BwdArgs &a, float *wf, fl
 __device__ __forceinline__ void bwd_grid_pairs(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads]) {
     const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     const int64_t ic = idx < a.np ? idx : a.np - 1;
-    const PairRec P = a.prec[ic];
+    const PairRec P = a.prec[DV_INB(ic, a.np, kSiteBwdRecord) ? ic : 0];
     PairF2 P2;
     P2.p0x = bc2(P.r0.x);
     P2.p1x = bc2(P.r1.x);
@@ -483,9 +485,11 @@ __device__ __forceinline__ void bwd_grid_pairs(const BwdArgs &a, float *wf, floa
         const int32_t *t = a.ptopo + 8 * idx;
         const int code = t[6];
         float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
-        write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
-        write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
-                           (code >> 12) & 1 ? -1.0 : 1.0);
+        if (DV_INB(t[4], a.nf, kSiteBwdFaceGrad))
+            write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
+        if (DV_INB(t[5], a.nf, kSiteBwdFaceGrad))
+            write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
+                               (code >> 12) & 1 ? -1.0 : 1.0);
     }
 }
 
@@ -638,7 +642,8 @@ __device__ __forceinline__ void for_each_chunk(const BwdArgs &a, float4 *win, Ch
         const int len2 = (len + 1) & ~1;
         __syncthreads();
         for (int i = threadIdx.x; i < len2; i += kBwdThreads) {
-            const int64_t k = w0 + (i < len ? i : len - 1);
+            int64_t k = w0 + (i < len ? i : len - 1);
+            if (!DV_INB(k, a.nq, kSiteBwdUpstream)) k = 0;
             float *wf = reinterpret_cast<float *>(win) + 8 * (i >> 1) + (i & 1);
             wf[0] = -a.queries[3 * k];
             wf[2] = -a.queries[3 * k + 1];
@@ -689,7 +694,8 @@ __device__ __forceinline__ void bwd_list_singles(const BwdArgs &a, float4 *win, 
     const int64_t count = a.singles ? a.nsingle : a.nf;
     const int64_t idx = ((int64_t)blockIdx.x - a.pblocks) * kBwdThreads + threadIdx.x;
     const int64_t ic = idx < count ? idx : count - 1;
-    const int64_t f = a.singles ? (int64_t)a.singles[ic] : ic;
+    int64_t f = a.singles ? (DV_INB(ic, a.nsingle, kSiteBwdRecord) ? (int64_t)a.singles[ic] : 0) : ic;
+    if (!DV_INB(f, a.nf, kSiteBwdRecord)) f = 0;
     const FaceF F = load_face(a.rec, f);
     FaceL2 F2;
     F2.v0x = bc2(F.v0x); F2.v0y = bc2(F.v0y); F2.v0z = bc2(F.v0z);
@@ -711,13 +717,14 @@ __device__ __forceinline__ void bwd_list_singles(const BwdArgs &a, float4 *win, 
         else
             list_guarded(F, win, c0, c1 < len ? c1 : len, ks);
     });
-    if (idx < count) write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+    if (idx < count && DV_INB(f, a.nf, kSiteBwdFaceGrad))
+        write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
 }
 
 __device__ __forceinline__ void bwd_list_pairs(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads]) {
     const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     const int64_t ic = idx < a.np ? idx : a.np - 1;
-    const PairRec P = a.prec[ic];
+    const PairRec P = a.prec[DV_INB(ic, a.np, kSiteBwdRecord) ? ic : 0];
     const PairL2 P2 = pair_l2(P);
     float2(*ksB)[kBwdThreads] = ks + kFaceSlots;
 #pragma unroll
@@ -743,9 +750,11 @@ __device__ __forceinline__ void bwd_list_pairs(const BwdArgs &a, float4 *win, fl
         const int32_t *t = a.ptopo + 8 * idx;
         const int code = t[6];
         float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
-        write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
-        write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
-                           (code >> 12) & 1 ? -1.0 : 1.0);
+        if (DV_INB(t[4], a.nf, kSiteBwdFaceGrad))
+            write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
+        if (DV_INB(t[5], a.nf, kSiteBwdFaceGrad))
+            write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
+                               (code >> 12) & 1 ? -1.0 : 1.0);
     }
 }
 
@@ -767,6 +776,10 @@ __global__ void __launch_bounds__(kBwdThreads, 3) bwd_list_kernel(const BwdArgs 
 
 // Once per device (mesh creation calls it, outside any stream capture): the adjoint kernels'
 // dynamic shared memory exceeds the 48 KB default.
+// CTAs of the grid adjoint resident per SM on each device (from the occupancy calculator, set by
+// prepare_backward_kernels; 0 = not known yet).
+static std::atomic<int> g_bwd_resident[64];
+
 cudaError_t prepare_backward_kernels() {
     static std::atomic<uint64_t> smem_set{0};
     int dev = 0;
@@ -777,8 +790,20 @@ cudaError_t prepare_backward_kernels() {
     e = cudaFuncSetAttribute(bwd_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdGridSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(bwd_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdListSmem);
-    if (e == cudaSuccess) smem_set.fetch_or(bit);
+    int resident = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, bwd_grid_kernel, kBwdThreads, kBwdGridSmem);
+    if (e == cudaSuccess) {
+        g_bwd_resident[dev & 63].store(resident);
+        smem_set.fetch_or(bit);
+    }
     return e;
+}
+
+// Fraction of the CTA slots the last wave leaves busy: total CTAs / (waves x slots).
+static double wave_efficiency(int64_t ctas, int64_t slots) {
+    const int64_t waves = (ctas + slots - 1) / slots;
+    return (double)ctas / (double)(waves * slots);
 }
 
 BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g, int num_sms) {
@@ -801,6 +826,23 @@ BwdPlan plan_backward(int64_t nq, const BwdFaces &fc, bool grid, const GridF *g,
     if (ns > units / per_min) ns = units / per_min;
     if (ns < 1) ns = 1;
     if (ns > 4096) ns = 4096;
+    // Every CTA carries the same work, so a last wave that fills few of the GPU's CTA slots
+    // idles most SMs for a whole CTA time. Among up to 4x as many splits, take the fewest whose
+    // waves fill at least 98 % of the slots (else the best filled), e.g. 799 face CTAs on 148 SMs
+    // x 3: 4 splits fill 90 % (7.2 waves), 5 splits 99.97 % (9.0 waves).
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int resident = g_bwd_resident[dev & 63].load();
+    if (resident > 0) {
+        const int64_t slots = (int64_t)resident * num_sms;
+        int64_t hi = 4 * ns;
+        if (hi > units / per_min) hi = units / per_min;
+        if (hi > 4096) hi = 4096;
+        int64_t best = ns;
+        for (int64_t k = ns; k <= hi && wave_efficiency(p.fblocks * best, slots) < 0.98; ++k)
+            if (wave_efficiency(p.fblocks * k, slots) > wave_efficiency(p.fblocks * best, slots)) best = k;
+        ns = best;
+    }
     p.rows_per_split = (units + ns - 1) / ns;
     p.nsplit = (int)((units + p.rows_per_split - 1) / p.rows_per_split);
     if (p.nsplit < 1) p.nsplit = 1;

@@ -69,8 +69,8 @@ __device__ __forceinline__ void arg_product_mul(ArgProduct &P, double D, double 
 
 __global__ void __launch_bounds__(kReThreads, 2)
     reeval_strip_kernel(const StripRec64 *__restrict__ srec, int64_t ne, GridD g, const float *__restrict__ queries,
-                        const int *__restrict__ list, const int *__restrict__ count, float *w_out, uint8_t *occ_out,
-                        unsigned *maxdiff_bits, int *occ_changed) {
+                        const int *__restrict__ list, const int *__restrict__ count, int64_t nq, float *w_out,
+                        uint8_t *occ_out, unsigned *maxdiff_bits, int *occ_changed) {
     __shared__ double red[kReThreads / 32][kRsQB];
     const int M = *count;
     const int nb = (M + kRsQB - 1) / kRsQB;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kReThreads, 2)
 #pragma unroll
         for (int j = 0; j < kRsQB; ++j) {
             const int k = b * kRsQB + j < M ? b * kRsQB + j : M - 1;
-            const int idx = list[k];
+            const int idx = DV_INB(k, nq, kSiteReevalQuery) && DV_INB(list[k], nq, kSiteReevalQuery) ? list[k] : 0;
             ids[j] = idx;
             if (queries) {
                 qx[j] = (double)queries[3 * (int64_t)idx];
@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kReThreads, 2)
             P2.ax[j] = P2.ay[j] = P2.az[j] = P2.l[j] = P2.e[j] = 0.0;
         }
         for (int64_t ev = es; ev < ee; ++ev) {
+            if (!DV_INB(ev, ne, kSiteReevalEvent)) break;
             const StripRec64 r = srec[ev];
             const bool face = r.flag != 0.0 && ev >= eb;
             Slot64 V;
@@ -181,8 +182,9 @@ cudaError_t launch_reeval_fp64(const StripRec64 *srec64, int64_t ne, const GridD
     const int64_t need = (max_flagged + kRsQB - 1) / kRsQB;
     if (need < blocks) blocks = need > 0 ? need : 1;
     prof_begin("reeval_fp64", s);
-    reeval_strip_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(srec64, ne, gd, queries, flag_list, flag_count, w_out,
-                                                                occ_out, stat_maxdiff_bits, stat_occ_changed);
+    reeval_strip_kernel<<<(unsigned)blocks, kReThreads, 0, s>>>(srec64, ne, gd, queries, flag_list, flag_count,
+                                                                max_flagged, w_out, occ_out, stat_maxdiff_bits,
+                                                                stat_occ_changed);
     count_launch();
     prof_end("reeval_fp64", s);
     return cudaGetLastError();

@@ -290,13 +290,14 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 
 // Final per-query write: w, occupancy, and the re-evaluation flag.
 __device__ __forceinline__ void epilogue(const FwdArgs &a, int64_t idx, float w) {
+    if (!DV_INB(idx, a.nq, kSiteFwdOut)) return;
     a.w_out[idx] = w;
     if (a.occ_out) a.occ_out[idx] = w > 0.5f ? 1 : 0;
     if (a.flag_list) {
         const bool flagged = a.near_flag[idx] != 0 || fabsf(__fsub_rn(w, 0.5f)) < kThreshBand;
         if (flagged) {
             const int pos = atomicAdd(a.flag_count, 1);
-            a.flag_list[pos] = (int)idx;
+            if (DV_INB(pos, a.nq, kSiteFwdFlagList)) a.flag_list[pos] = (int)idx;
         }
     }
 }
@@ -314,6 +315,7 @@ struct TilePipe {
     int ntiles;
     int skip_tile;     // self-test hook: this tile is never issued (-1: none)
     uint64_t wait_ns;  // limit of each bounded wait
+    int64_t total;     // records in the source array (bounds check of the debug build)
 
     __device__ __forceinline__ int tile_count(int t) const {
         const int64_t left = nfaces - (int64_t)t * kT;
@@ -323,6 +325,10 @@ struct TilePipe {
         if (t == skip_tile) return;
         const int s = t % kStages;
         const uint32_t bytes = (uint32_t)tile_count(t) * (uint32_t)sizeof(Rec);
+        // debug build: a tile reaching outside the records is not copied (its wait then runs out)
+        if (!DV_INB(f0 + (int64_t)t * kT, total, kSiteFwdTile) ||
+            !DV_INB(f0 + (int64_t)t * kT + tile_count(t) - 1, total, kSiteFwdTile))
+            return;
         mbar_arrive_expect_tx(&full[s], bytes);
         tma_load_1d(&sm[s][0], src + f0 + (int64_t)t * kT, bytes, &full[s]);
     }
@@ -424,6 +430,7 @@ __global__ void __launch_bounds__(kFwdThreads, 3) fwd_grid_kernel(const FwdArgs 
     pp.ntiles = (int)((pp.nfaces + kTileFaces - 1) / kTileFaces);
     pp.skip_tile = a.skip_tile;
     pp.wait_ns = a.wait_ns;
+    pp.total = a.nf;
 
     run_face_tiles(
         pp, a.err,
@@ -469,9 +476,10 @@ __global__ void __launch_bounds__(kFwdThreads, 3) fwd_grid_kernel(const FwdArgs 
             const float plain = HALF ? acc[i][j] : (j % 2 ? acc2[i][j / 2].y : acc2[i][j / 2].x);
             const float2 k = KAHAN ? kst[i * QX + j][threadIdx.x] : make_float2(plain, 0.0f);
             const float s = k.x, c = k.y;
-            if (a.nsplit > 1)
-                a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(s, -c);
-            else
+            if (a.nsplit > 1) {
+                if (DV_INB((int64_t)blockIdx.y * a.nq + idx, (int64_t)a.nsplit * a.nq, kSiteFwdPartial))
+                    a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(s, -c);
+            } else
                 epilogue(a, idx, __fmul_rn(__fsub_rn(s, c), kInv2Pi));
         }
     }
@@ -661,6 +669,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_grid_strip_kernel(const 
     pp.ntiles = (int)((pp.nfaces + kTileEvents - 1) / kTileEvents);
     pp.skip_tile = a.skip_tile;
     pp.wait_ns = a.wait_ns;
+    pp.total = a.ne;
 
     int first = warm;  // leading events of the current tile that are warm-up only
     run_face_tiles(
@@ -730,9 +739,10 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_grid_strip_kernel(const 
             const int64_t idx = ((int64_t)z * ny + iy) * nx + ix;
             const float plain = j % 2 ? acc[i][j / 2].y : acc[i][j / 2].x;
             const float2 k = KAHAN ? kst[i * QX + j][threadIdx.x] : make_float2(plain, 0.0f);
-            if (a.nsplit > 1)
-                a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(k.x, -k.y);
-            else
+            if (a.nsplit > 1) {
+                if (DV_INB((int64_t)blockIdx.y * a.nq + idx, (int64_t)a.nsplit * a.nq, kSiteFwdPartial))
+                    a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(k.x, -k.y);
+            } else
                 epilogue(a, idx, __fmul_rn(__fsub_rn(k.x, k.y), kInv2Pi));
         }
     }
@@ -874,6 +884,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_list_strip_kernel(const 
     pp.ntiles = (int)((pp.nfaces + kTileEvents - 1) / kTileEvents);
     pp.skip_tile = a.skip_tile;
     pp.wait_ns = a.wait_ns;
+    pp.total = a.ne;
 
     int first = warm;
     run_face_tiles(
@@ -930,9 +941,10 @@ __global__ void __launch_bounds__(kStripThreads, 4) fwd_list_strip_kernel(const 
         if (idx >= a.nq) continue;
         const float plain = j % 2 ? acc[j / 2].y : acc[j / 2].x;
         const float2 k = KAHAN ? kst[j][threadIdx.x] : make_float2(plain, 0.0f);
-        if (a.nsplit > 1)
-            a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(k.x, -k.y);
-        else
+        if (a.nsplit > 1) {
+            if (DV_INB((int64_t)blockIdx.y * a.nq + idx, (int64_t)a.nsplit * a.nq, kSiteFwdPartial))
+                a.partial[(int64_t)blockIdx.y * a.nq + idx] = make_float2(k.x, -k.y);
+        } else
             epilogue(a, idx, __fmul_rn(__fsub_rn(k.x, k.y), kInv2Pi));
     }
 }
@@ -943,6 +955,7 @@ __global__ void split_reduce_kernel(const float2 *__restrict__ partial, int nspl
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < a.nq; idx += stride) {
         double s = 0.0;
         for (int k = 0; k < nsplit; ++k) {
+            if (!DV_INB((int64_t)k * a.nq + idx, (int64_t)nsplit * a.nq, kSiteFwdPartial)) break;
             const float2 p = partial[(int64_t)k * a.nq + idx];
             s += (double)p.x;
             s += (double)p.y;

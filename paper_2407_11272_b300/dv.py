@@ -17,7 +17,7 @@ __all__ = [
     "DvError", "Grid", "Mesh", "PRECISION", "dv_abi_version", "dv_mesh_create", "dv_mesh_update_verts",
     "dv_mesh_reserve", "dv_mesh_check", "dv_winding", "dv_voxelize_grid", "dv_winding_backward",
     "dv_winding_backward_boundary", "dv_mesh_num_boundary_edges", "dv_mesh_num_strip_events",
-    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_build_face_pairs", "dv_selftest_bounded_wait", "dv_selftest_forward_timeout", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
+    "dv_run_batch", "dv_dipole_winding", "dv_dipole_backward", "dv_flipped_duplication", "dv_build_strips", "dv_build_face_pairs", "dv_selftest_bounded_wait", "dv_selftest_forward_timeout", "dv_debug_report", "dv_profile_enable", "dv_profile_reset", "dv_profile_read", "dv_launch_count", "library_path", "load",
 ]
 
 PRECISION = {"fp32": 0, "kahan": 1, "mixed": 2, "fp16": 3}
@@ -79,7 +79,10 @@ _I64 = ctypes.c_int64
 
 
 def library_path():
-    return _build.LIB
+    """libdv.so, or its bounds-checked debug build libdv_debug.so when DV_DEBUG=1 is set."""
+    import os
+
+    return _build.LIB_DEBUG if os.environ.get("DV_DEBUG") == "1" else _build.LIB
 
 
 def load():
@@ -87,11 +90,13 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not _build.LIB.exists():
-        raise DvError(4, "load", f"{_build.LIB} is missing; run `python -m paper_2407_11272_b300.build`")
+    path = library_path()
+    if not path.exists():
+        flag = " --debug" if path == _build.LIB_DEBUG else ""
+        raise DvError(4, "load", f"{path} is missing; run `python -m paper_2407_11272_b300.build{flag}`")
     import torch  # noqa: F401  (loads the CUDA runtime the library links against)
 
-    lib = ctypes.CDLL(str(_build.LIB))
+    lib = ctypes.CDLL(str(path))
     lib.dv_abi_version.restype = ctypes.c_int
     lib.dv_status_string.restype = ctypes.c_char_p
     lib.dv_status_string.argtypes = [ctypes.c_int]
@@ -123,6 +128,9 @@ def load():
     lib.dv_dipole_backward.restype = ctypes.c_int
     lib.dv_flipped_duplication.argtypes = [_P, _P, ctypes.c_float, _P, _P, _P]
     lib.dv_flipped_duplication.restype = ctypes.c_int
+    lib.dv_debug_report.argtypes = [ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_I64),
+                                    ctypes.POINTER(_I64), ctypes.c_int]
+    lib.dv_debug_report.restype = ctypes.c_int
     lib.dv_selftest_bounded_wait.argtypes = [_I64, ctypes.c_int, _P]
     lib.dv_selftest_bounded_wait.restype = ctypes.c_int
     lib.dv_selftest_forward_timeout.argtypes = [_P, ctypes.POINTER(_Grid), _P, _I64, _I64, _P]
@@ -399,6 +407,18 @@ def dv_dipole_backward(mesh: Mesh, upstream, queries=None, grid: Grid | None = N
 def dv_selftest_bounded_wait(limit_us: int, arrive: bool, stream=None) -> int:
     """Status code of one bounded wait on the GPU (0 = DV_OK, 5 = DV_ERR_TIMEOUT); no exception."""
     return int(load().dv_selftest_bounded_wait(int(limit_us), 1 if arrive else 0, _stream(stream)))
+
+
+def dv_debug_report(clear: bool = False):
+    """Bounds-check report of the debug build: dict(count, site, index, bound) of the accesses it
+    rejected since the last clear; None with the release library (which has no checks)."""
+    c, site, idx, bound = _I64(0), ctypes.c_int32(0), _I64(0), _I64(0)
+    st = load().dv_debug_report(ctypes.byref(c), ctypes.byref(site), ctypes.byref(idx), ctypes.byref(bound),
+                                1 if clear else 0)
+    if st == 6:  # DV_ERR_UNSUPPORTED: release build
+        return None
+    _check(st, "dv_debug_report")
+    return {"count": c.value, "site": site.value, "index": idx.value, "bound": bound.value}
 
 
 def dv_selftest_forward_timeout(mesh: Mesh, grid: Grid, out, skip_tile: int, limit_us: int, stream=None) -> int:

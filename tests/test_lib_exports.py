@@ -109,3 +109,30 @@ def test_oracle_and_product_are_independent():
             assert not re.search(r"^\s*(import|from)\s+paper_2407_11272_b300", p.read_text(), flags=re.M), p
         if p.suffix in (".c", ".h"):
             assert not re.search(r'#include\s+"', p.read_text()), p  # system headers only
+
+
+def test_debug_library_exports_the_same_symbols_and_release_has_no_checks(lib):
+    """libdv_debug.so (the bounds-checked build) exports every declared symbol; the release
+    library answers dv_debug_report with DV_ERR_UNSUPPORTED without touching the GPU."""
+    dbg = ctypes.CDLL(str(dvbuild.build(debug=True)))
+    missing = [n for n in _declared_functions() if not hasattr(dbg, n)]
+    assert not missing, f"debug build misses: {missing}"
+    assert "sm_103a" in (dvbuild.BUILD / "debug" / "ptxas.log").read_text()
+    I64 = ctypes.c_int64
+    c, site, idx, bound = I64(7), ctypes.c_int32(7), I64(7), I64(7)
+    lib.dv_debug_report.restype = ctypes.c_int
+    lib.dv_debug_report.argtypes = [ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(I64),
+                                    ctypes.POINTER(I64), ctypes.c_int]
+    assert lib.dv_debug_report(ctypes.byref(c), ctypes.byref(site), ctypes.byref(idx), ctypes.byref(bound), 0) == 6
+    assert c.value == 0
+
+
+def test_run_batch_rejects_the_default_stream(lib):
+    """dv_run_batch captures a CUDA graph on its stream; the legacy default stream (0) cannot be
+    captured and is rejected on the host before any CUDA call."""
+    buf = (ctypes.c_byte * 256)()  # one request slot; only the stream is examined before the error
+    lib.dv_run_batch.restype = ctypes.c_int
+    lib.dv_run_batch.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    assert lib.dv_run_batch(ctypes.cast(buf, ctypes.c_void_p), 1, 2, None) == 1
+    lib.dv_last_error.restype = ctypes.c_char_p
+    assert b"default stream" in lib.dv_last_error()
