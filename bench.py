@@ -67,14 +67,23 @@ EXEC_BWD_PAIRED = 38.5
 # FP32 kernels, DFMA + DADD + DMUL per re-evaluated query x strip event for the FP64 pass. Keyed
 # by (mesh, kernel); each entry records the SHA-256 of the kernel's source file at capture time
 # and is ignored once that file changes.
-EXECUTED = {}
+EXECUTED = {
+    # 8.255e11 FP32 lane ops / (262 144 x 204 020) pairs; profiles/hot_kernels_shsphere_64_ncu.md
+    ("sh_sphere", "fwd_strip_kahan"): (15.44, "paper_2407_11272_b300/csrc/winding_fwd.cu",
+                                       "c21070f8ec6075ccb701b639ef36e42e75799744f8df52c1773f722b409f7a49"),
+    # 3.351e9 FP64 ops / (480 flagged queries x 205 030 events)
+    ("sh_sphere", "reeval_fp64"): (34.05, "paper_2407_11272_b300/csrc/winding_fp64.cu",
+                                   "8c594e484ada6aa7cf91bbf908944d2813b8df3c27fe0c9620151088ab2747b9"),
+}
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the dominant kernel on the full workload, keyed by (workload, kernel), with the same source
 # digest rule as EXECUTED.
 TRAFFIC = {
-    ("torus_128", "bwd_grid"): (11298304, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "b6c3d3a58e597cc97d82f06b22944d858cd3bc9d5611dd9cbd4ca087a86631da"),
+    # 87 581 952 B read + 23 813 376 B written, one full-size launch (799 x 5 CTAs);
+    # profiles/bwd_grid_shsphere_256_dram.md
+    ("shsphere_256", "bwd_grid"): (111395328, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                   "149c50f6040dab2b32958ff63e6654eb2441686af6d915f3ed17ca0ee5ea38bc"),
 }
 
 ACC_QUERIES = 100_000  # seeded voxel-centre sample of the accuracy block
@@ -250,8 +259,18 @@ def _oracle_leg_main(conn, workload, acc_queries, budget_s):
     t1 = time.perf_counter()
     d = oracle.point_mesh_distance(V, F, Q)
     t2 = time.perf_counter()
-    conn.send(("accuracy", {"idx": idx, "w64": w64, "d": d, "winding_s": t1 - t0, "distance_s": t2 - t1,
-                            "threads": oracle.max_threads()}))
+    acc = {"idx": idx, "w64": w64, "d": d, "winding_s": t1 - t0, "distance_s": t2 - t1,
+           "threads": oracle.max_threads(), "cells": n ** 3}
+    # a closed mesh (every edge shared by exactly two faces): its occupancy on the whole grid from
+    # signed ray crossings, which needs no solid angle
+    und = np.sort(np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]]), axis=1)
+    _, cnt = np.unique(und, axis=0, return_counts=True)
+    if np.all(cnt == 2):
+        t3 = time.perf_counter()
+        wr, amb = oracle.ray_winding_grid(V, F, [-1.0] * 3, [1.0] * 3, [n] * 3)
+        acc["whole_grid"] = {"occ_bits": np.packbits(wr == 1), "undecided_bits": np.packbits(amb),
+                             "values": sorted(int(v) for v in np.unique(wr[~amb])), "seconds": time.perf_counter() - t3}
+    conn.send(("accuracy", acc))
 
 
 class OracleLeg:
@@ -404,7 +423,9 @@ def _accuracy_gpu(mesh, grid, w, occ, idx, stream, dev):
         dv.dv_voxelize_grid(mesh, grid, out_w=w, out_occ=occ, precision=prec, stream=stream)
         b.record(stream)
         torch.cuda.synchronize(dev)
-        out[prec] = (w[idx_t].cpu().numpy(), occ[idx_t].cpu().numpy(), a.elapsed_time(b))
+        # the whole grid's occupancy too, for closed meshes' ray-crossing check (2 MB as bits)
+        out[prec] = (w[idx_t].cpu().numpy(), occ[idx_t].cpu().numpy(), a.elapsed_time(b),
+                     np.packbits(occ.cpu().numpy().astype(bool)))
     return out
 
 
@@ -420,7 +441,7 @@ def _accuracy(gpu, ref, n_flagged, pairs):
            "ties": int(tie.sum()),
            "oracle": f"FP64 winding + exact point-triangle distance, {ref['threads']} threads, "
                      f"{ref['winding_s']:.1f} s + {ref['distance_s']:.1f} s"}
-    for prec, (wg, og, ms) in gpu.items():
+    for prec, (wg, og, ms, _) in gpu.items():
         err = np.abs(wg.astype(np.float64) - w64)
         mism = (og.astype(bool) != occ64) & ~tie
         ent = {"fwd_ms": ms, "fwd_pairs_per_s": pairs / (ms * 1e-3),
@@ -433,6 +454,19 @@ def _accuracy(gpu, ref, n_flagged, pairs):
         if prec == "mixed":
             ent["n_flagged_grid"] = int(n_flagged)
         out[prec] = ent
+    wg = ref.get("whole_grid")
+    if wg is not None:
+        # every voxel of the grid: occupancy against the signed ray-crossing count of the closed mesh
+        total = int(ref["cells"])
+        amb = np.unpackbits(wg["undecided_bits"])[:total].astype(bool)
+        ray = np.unpackbits(wg["occ_bits"])[:total].astype(bool)
+        whole = {"cells": total, "undecided": int(amb.sum()), "ray_values": wg["values"],
+                 "method": "signed ray crossings along +x per row (closed mesh), independent of Eq. 5",
+                 "oracle_s": wg["seconds"]}
+        for prec, (_, _, _, bits) in gpu.items():
+            occ = np.unpackbits(bits)[:total].astype(bool)
+            whole[f"occ_mismatch_{prec}"] = int(((occ != ray) & ~amb).sum())
+        out["whole_grid"] = whole
     return out
 
 

@@ -55,5 +55,11 @@ def test_oracle_leg_runs_in_a_spawned_process():
         V, F = meshgen.icosphere(3, 0.8)
         Q = oracle.grid_points([-1.0] * 3, [1.0] * 3, [32] * 3, ref["idx"])
         assert np.array_equal(ref["w64"], oracle.winding(V, F, Q))
+        wg = ref["whole_grid"]  # the icosphere is closed: the whole grid by ray crossings
+        occ = np.unpackbits(wg["occ_bits"])[:ref["cells"]].astype(bool)
+        assert ref["cells"] == 32 ** 3 and wg["values"] == [0, 1]
+        w_all = oracle.winding(V, F, oracle.grid_queries([-1.0] * 3, [1.0] * 3, [32] * 3))
+        und = np.unpackbits(wg["undecided_bits"])[:ref["cells"]].astype(bool)
+        assert np.array_equal(occ[~und], (w_all > 0.5)[~und])
     finally:
         leg.close()
