@@ -14,8 +14,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/dv_api.h"
 #include "dv_internal.cuh"
+
+// An NVTX range around each host entry point, named after it, so that a timeline tool (Nsight
+// Systems, ncu --nvtx) shows which call issued which kernels. NVTX is header-only: without a tool
+// attached a range costs a few nanoseconds.
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+#define DV_NVTX_RANGE(name) const NvtxRange dv_nvtx_range_(name)
 
 // ------------------------------------------------------------------------------------------
 // Errors
@@ -454,6 +469,7 @@ dv_status mesh_create_impl(const float *d_verts, int64_t nv, const int32_t *d_fa
 
 dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, void *stream,
                          dv_mesh **out) {
+    DV_NVTX_RANGE("dv_mesh_create");
     g_last_error.clear();
     dv_mesh *held = nullptr;
     try {
@@ -467,6 +483,7 @@ dv_status dv_mesh_create(const float *d_verts, int64_t nv, const int32_t *d_face
 }
 
 dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
+    DV_NVTX_RANGE("dv_mesh_update_verts");
     if (!m || !d_verts) return fail(DV_ERR_INVALID_ARG, "mesh or vertex pointer is NULL");
     DeviceGuard dg(m->device);
     m->last_stream = (cudaStream_t)stream;
@@ -481,6 +498,7 @@ dv_status dv_mesh_update_verts(dv_mesh *m, const float *d_verts, void *stream) {
 }
 
 dv_status dv_mesh_reserve(dv_mesh *m, const dv_grid *grid, int64_t max_list_queries) {
+    DV_NVTX_RANGE("dv_mesh_reserve");
     if (!m || max_list_queries < 0) return fail(DV_ERR_INVALID_ARG, "bad reserve arguments");
     DeviceGuard dg(m->device);
     dv_status st;
@@ -565,6 +583,7 @@ dv_status dv_selftest_forward_timeout(dv_mesh *m, const dv_grid *grid, float *d_
 
 dv_status dv_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid, float *d_out_w,
                      dv_precision prec, void *stream) {
+    DV_NVTX_RANGE("dv_winding");
     int64_t n = 0;
     dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
     if (st) return st;
@@ -576,6 +595,7 @@ dv_status dv_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, co
 
 dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_out_w, uint8_t *d_out_occ,
                            dv_precision prec, dv_report *report, void *stream) {
+    DV_NVTX_RANGE("dv_voxelize_grid");
     int64_t n = 0;
     if (!grid) return fail(DV_ERR_INVALID_ARG, "grid is NULL");
     dv_status st = check_queries(mesh, nullptr, 0, grid, &n);
@@ -588,6 +608,7 @@ dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_ou
 
 dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                               const float *d_upstream, float *d_dverts, void *stream) {
+    DV_NVTX_RANGE("dv_winding_backward");
     int64_t n = 0;
     dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
     if (st) return st;
@@ -658,6 +679,7 @@ dv_status boundary_device(dv_mesh *m, cudaStream_t s) {
 
 dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                                        const float *d_upstream, float *d_dverts, void *stream) {
+    DV_NVTX_RANGE("dv_winding_backward_boundary");
     int64_t n = 0;
     dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
     if (st) return st;
@@ -757,6 +779,7 @@ dv_status backward_on(dv_mesh *m, const dv_grid *grid, int64_t nq, const float *
 }  // namespace
 
 dv_status dv_run_batch(const dv_request *reqs, int n, dv_precision prec, void *stream) {
+    DV_NVTX_RANGE("dv_run_batch");
     if (n < 0 || (n > 0 && !reqs)) return fail(DV_ERR_INVALID_ARG, "bad request array");
     if (n == 0) return DV_OK;
     if (prec != DV_PREC_FP32 && prec != DV_PREC_FP32_KAHAN && prec != DV_PREC_MIXED && prec != DV_PREC_FP16)
@@ -830,6 +853,7 @@ dv_status dv_run_batch(const dv_request *reqs, int n, dv_precision prec, void *s
 
 dv_status dv_dipole_winding(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                             float *d_out_w, void *stream) {
+    DV_NVTX_RANGE("dv_dipole_winding");
     int64_t n = 0;
     dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
     if (st) return st;
@@ -845,6 +869,7 @@ dv_status dv_dipole_winding(const dv_mesh *mesh, const float *d_queries, int64_t
 
 dv_status dv_dipole_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                              const float *d_upstream, float *d_dverts, void *stream) {
+    DV_NVTX_RANGE("dv_dipole_backward");
     int64_t n = 0;
     dv_status st = check_queries(mesh, d_queries, nq, grid, &n);
     if (st) return st;
@@ -864,6 +889,7 @@ dv_status dv_dipole_backward(const dv_mesh *mesh, const float *d_queries, int64_
 
 dv_status dv_flipped_duplication(const dv_mesh *mesh, const float *d_verts, float eps, float *d_out_verts,
                                  int32_t *d_out_faces, void *stream) {
+    DV_NVTX_RANGE("dv_flipped_duplication");
     if (!mesh || !d_verts || !d_out_verts || !d_out_faces)
         return fail(DV_ERR_INVALID_ARG, "mesh, d_verts, d_out_verts and d_out_faces must be non-NULL");
     if (!std::isfinite(eps)) return fail(DV_ERR_INVALID_ARG, "eps must be finite");
