@@ -228,10 +228,16 @@ def test_whole_grid_occupancy_matches_ray_crossings(cuda_device, case):
         V, F = meshgen.jittered_torus(delete_frac=0.0, seed=0)
         grid = dv.Grid.cube(128)
     mesh = make_mesh(V, F, cuda_device)
-    _, occ, rep = dv.dv_voxelize_grid(mesh, grid, precision="mixed", report=True)
+    w, occ, rep = dv.dv_voxelize_grid(mesh, grid, precision="mixed", report=True)
     w_ray, und = oracle.ray_winding_grid(V, F, grid.lo, grid.hi, grid.n)
-    assert set(np.unique(w_ray[~und]).tolist()) <= {0, 1}
+    if case == "shsphere_256":
+        assert set(np.unique(w_ray[~und]).tolist()) == {0, 1}
+    # (the jittered torus folds over itself in places: integer winding numbers -1 and 2 occur)
     assert und.sum() < 1e-5 * grid.num_queries
-    bad = (occ.cpu().numpy().astype(bool) != (w_ray == 1)) & ~und
+    # off the surface w is an integer: every decided voxel within the forward bar of it, and its
+    # occupancy (w > 0.5) that of the integer (w >= 1)
+    err = np.abs(w.cpu().numpy().astype(np.float64) - w_ray)[~und]
+    assert err.max() <= 1e-4, f"max |w - ray count| over the whole grid {err.max():.3e}"
+    bad = (occ.cpu().numpy().astype(bool) != (w_ray >= 1)) & ~und
     assert not bad.any(), f"{bad.sum()} occupancy mismatches over the whole grid"
-    assert (w_ray == 1).sum() > 0.05 * grid.num_queries and rep["n_flagged"] > 0
+    assert (w_ray >= 1).sum() > 0.05 * grid.num_queries and rep["n_flagged"] > 0
