@@ -373,7 +373,7 @@ def run_reference(args):
 
 
 def _kernel_rooflines(args, prof, pairs, nflagged, ne, F, nv, fp32_peak, fp64_peak):
-    """Per hot kernel: the rate on the survey's algorithmic basis (FP32 lane operations of the direct
+    """Per hot kernel: the rate on the algorithmic basis (FP32 lane operations of the direct
     formula per pair; exceeds 1 by operation sharing) and on the executed basis (operations the
     kernel executes per unit, measured by ncu counters, else counted from the code), both against
     the peak of the pipe that bounds it."""
