@@ -1,12 +1,20 @@
-// Adjoint of the winding number: dL/dV = sum_q g_q dw(q)/dV.
+// Adjoint of the winding number: dL/dV = sum_q g_q dw(q)/dV, every (query, face) pair.
 //
-// With a = v0 - q, b = v1 - q, c = v2 - q, N = a.n (n = (v1-v0)x(v2-v0)), D as in the forward,
-// Omega = 2 ATAN2(N, D) and w = (1/4pi) sum Omega:
+// Two exact formulations of the per-face derivative of Eq. (7), w = (1/4pi) sum Omega:
+//
+// Grid queries (bwd_grid_kernel) -- from each face's edges. The solid angle of a triangle depends
+// only on its boundary, so for an edge p -> r of the face (a = p - q, b = r - q)
+//   dOmega/dp += (b x a) / (|a| (|a||b| + a.b)),   dOmega/dr += (b x a) / (|b| (|a||b| + a.b)).
+// A thread owns two faces that share an edge (consecutive faces of a strip, paired on the host);
+// their shared edge's terms cancel, leaving the quad's four edges: per query four distances, four
+// dots and four reciprocals serve both faces, and every edge keeps four packed row sums (details at
+// bwd_grid_pairs_edges). Faces left unpaired run alone (three edges).
+//
+// Query lists (bwd_list_kernel) -- the chain rule through N and D. With a = v0 - q, b = v1 - q,
+// c = v2 - q, N = a.n (n = (v1-v0)x(v2-v0)), D as in the forward and Omega = 2 ATAN2(N, D):
 //   dw = (1/2pi) (D dN - N dD) / (N^2 + D^2)
 //   dN/da = b x c,  dN/db = c x a,  dN/dc = a x b
 //   dD/da = (a/|a|)(|b||c| + b.c) + b|c| + c|b|   (and cyclically)
-// No arctangent is needed. The kernels are face-parallel: a thread owns its faces (below), streams
-// the queries (uniform across the warp), and keeps each face's gradient as a few scalar sums.
 // Writing b = e1 + a, c = e2 + a (e1 = v1 - v0, e2 = v2 - v0), every per-query vector term is
 // (scalar) x a or a constant vector, so per face only these sums are needed:
 //   T_cD = sum cD, T_P = sum cN|a|, T_Q = sum cN|b|, T_R = sum cN|c|,
@@ -17,13 +25,12 @@
 //   dL/dv0 = k [T_cD n + (e1 - e2) x U_cD - T_R e1 - T_Q e2 - U_a]
 //   dL/dv1 = k [e2 x U_cD - T_ab e1 - T_P e2 - U_b]
 //   dL/dv2 = k [-e1 x U_cD - T_P e1 - T_ac e2 - U_c],   k = 1/(2 pi).
-// On a grid row (fixed y, z) the y and z parts of a are constant, so the sums over a row are
-// kept as 7 scalars and their x-weighted versions (14 FMAs per pair) and folded per row.
-// A thread owns two faces that share an edge (consecutive faces of a strip, paired on the host):
-// per query the four vertex distances (one MUFU reciprocal square root each) and the five edge
-// dots serve both faces; the faces left unpaired run one per thread (grid and list paths).
-// Per-face sums are FP32 with Kahan compensation; per-split face gradients are summed over
-// splits and incident faces in FP64 by the gather kernel (pack.cu), in a fixed order.
+// Edge-sharing face pairs share the four distances and five edge dots here too.
+//
+// Both kernels are face-parallel: a thread owns its faces, streams the queries (uniform across the
+// warp) through shared memory, keeps per-face (per-edge) sums in FP32 with Kahan compensation in
+// shared memory, and writes per-split face gradients that the gather kernel (pack.cu) sums over
+// splits and incident faces in FP64, in a fixed order.
 #include <math.h>
 
 #include <atomic>
@@ -121,111 +128,10 @@ __device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx
     X[6] = fmaf(alC, ax, X[6]);
 }
 
-// The same arithmetic as bwd_pair<false> for two queries of one row at once, every FP32 operation
-// a packed FP32x2 instruction (Blackwell FFMA2/FADD2/FMUL2: one issue slot for both queries);
-// only the MUFU reciprocal square roots and reciprocals stay scalar. The even and odd queries of
-// the row accumulate in the two halves of S2/X2.
+// Packed FP32x2 helpers (Blackwell FFMA2/FADD2/FMUL2 take two queries per instruction; the MUFU
+// reciprocal square roots and reciprocals stay scalar).
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
-
-struct FaceF2 {
-    float2 v0x, v1x, v2x, nx;
-};
-struct RowB2 {
-    float2 La, Lb, Lc, Pab, Pbc, Pca, Nyz;
-};
-
 __device__ __forceinline__ float2 rsqrt2(float2 v) { return make_float2(rsqrt_approx(v.x), rsqrt_approx(v.y)); }
-
-// The adjoint terms of one face for two queries of a row, from the distances |a|, |b|, |c|, their
-// reciprocals, the edge dots, N and the x offset of the face's first vertex.
-__device__ __forceinline__ void bwd_face2(float2 la, float2 lb, float2 lc, float2 ia, float2 ib, float2 ic,
-                                          float2 ab, float2 bc, float2 ca, float2 N, float2 ax, float2 g,
-                                          float2 (&S)[7], float2 (&X)[7]) {
-    // |a||b| + a.b, written lb * la so that for two faces sharing the edge (a, b) = (c', b') it is
-    // the same expression as the other face's lb * lc + b.c (one computation after CSE)
-    const float2 tc = __ffma2_rn(lb, la, ab);
-    float2 D = __fmul2_rn(tc, lc);
-    D = __ffma2_rn(la, bc, D);
-    D = __ffma2_rn(lb, ca, D);
-    const float2 den = __ffma2_rn(N, N, __fmul2_rn(D, D));
-    const float2 r = make_float2(rcp_approx(den.x), rcp_approx(den.y));
-    const float2 gr = __fmul2_rn(g, r);
-    const float2 cD = __fmul2_rn(gr, D), cN = __fmul2_rn(gr, N);
-    // the six cN-scaled coefficients (cN |a|, cN |b|, cN |c|, alpha_a, alpha_b, alpha_c) enter
-    // the sums through one FMA each: S += cN * k and X += (cN * ax) * k
-    const float2 kA = __fmul2_rn(__ffma2_rn(lb, lc, bc), ia);
-    const float2 kB = __fmul2_rn(__ffma2_rn(lc, la, ca), ib);
-    const float2 kC = __fmul2_rn(tc, ic);
-    const float2 pa = __fmul2_rn(cN, ax);
-    S[0] = __fadd2_rn(S[0], cD);
-    S[1] = __ffma2_rn(cN, la, S[1]);
-    S[2] = __ffma2_rn(cN, lb, S[2]);
-    S[3] = __ffma2_rn(cN, lc, S[3]);
-    S[4] = __ffma2_rn(cN, kA, S[4]);
-    S[5] = __ffma2_rn(cN, kB, S[5]);
-    S[6] = __ffma2_rn(cN, kC, S[6]);
-    X[0] = __ffma2_rn(cD, ax, X[0]);
-    X[1] = __ffma2_rn(pa, la, X[1]);
-    X[2] = __ffma2_rn(pa, lb, X[2]);
-    X[3] = __ffma2_rn(pa, lc, X[3]);
-    X[4] = __ffma2_rn(pa, kA, X[4]);
-    X[5] = __ffma2_rn(pa, kB, X[5]);
-    X[6] = __ffma2_rn(pa, kC, X[6]);
-}
-
-__device__ __forceinline__ void bwd_pair2(const FaceF2 &F, const RowB2 &R, float2 nqx, float2 g, float2 (&S)[7],
-                                          float2 (&X)[7]) {
-    const float2 ax = __fadd2_rn(F.v0x, nqx), bx = __fadd2_rn(F.v1x, nqx), cx = __fadd2_rn(F.v2x, nqx);
-    const float2 la2 = __ffma2_rn(ax, ax, R.La), lb2 = __ffma2_rn(bx, bx, R.Lb), lc2 = __ffma2_rn(cx, cx, R.Lc);
-    const float2 ia = rsqrt2(la2), ib = rsqrt2(lb2), ic = rsqrt2(lc2);
-    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
-    const float2 ab = __ffma2_rn(ax, bx, R.Pab), bc = __ffma2_rn(bx, cx, R.Pbc), ca = __ffma2_rn(cx, ax, R.Pca);
-    const float2 N = __ffma2_rn(ax, F.nx, R.Nyz);
-    bwd_face2(la, lb, lc, ia, ib, ic, ab, bc, ca, N, ax, g, S, X);
-}
-
-// Two faces sharing the edge (p1, p2): A = (p0, p1, p2) and B = (p2, p1, p3). Per pair of queries
-// the four distances (four MUFU square roots per query instead of six) and the five edge dots
-// serve both faces; the per-face arithmetic is bwd_face2, as for a face alone.
-struct PairF2 {
-    float2 p0x, p1x, p2x, p3x, nAx, nBx;
-};
-struct PairRow2 {
-    float2 L0, L1, L2, L3, P01, P12, P20, P13, P32, NA, NB;
-};
-
-__device__ __forceinline__ PairRow2 pair_row(const PairRec &P, float qy, float qz) {
-    const float y0 = P.r0.y - qy, z0 = P.r0.z - qz, y1 = P.r1.y - qy, z1 = P.r1.z - qz;
-    const float y2 = P.r2.y - qy, z2 = P.r2.z - qz, y3 = P.r3.y - qy, z3 = P.r3.z - qz;
-    PairRow2 R;
-    R.L0 = bc2(fmaf(y0, y0, z0 * z0));
-    R.L1 = bc2(fmaf(y1, y1, z1 * z1));
-    R.L2 = bc2(fmaf(y2, y2, z2 * z2));
-    R.L3 = bc2(fmaf(y3, y3, z3 * z3));
-    R.P01 = bc2(fmaf(y0, y1, z0 * z1));
-    R.P12 = bc2(fmaf(y1, y2, z1 * z2));
-    R.P20 = bc2(fmaf(y2, y0, z2 * z0));
-    R.P13 = bc2(fmaf(y1, y3, z1 * z3));
-    R.P32 = bc2(fmaf(y3, y2, z3 * z2));
-    R.NA = bc2(fmaf(y0, P.r1.w, z0 * P.r2.w));
-    R.NB = bc2(fmaf(y2, P.r4.x, z2 * P.r4.y));
-    return R;
-}
-
-__device__ __forceinline__ void bwd_quad2(const PairF2 &P, const PairRow2 &R, float2 nqx, float2 g, float2 (&SA)[7],
-                                          float2 (&XA)[7], float2 (&SB)[7], float2 (&XB)[7]) {
-    const float2 x0 = __fadd2_rn(P.p0x, nqx), x1 = __fadd2_rn(P.p1x, nqx);
-    const float2 x2 = __fadd2_rn(P.p2x, nqx), x3 = __fadd2_rn(P.p3x, nqx);
-    const float2 m0 = __ffma2_rn(x0, x0, R.L0), m1 = __ffma2_rn(x1, x1, R.L1);
-    const float2 m2 = __ffma2_rn(x2, x2, R.L2), m3 = __ffma2_rn(x3, x3, R.L3);
-    const float2 i0 = rsqrt2(m0), i1 = rsqrt2(m1), i2 = rsqrt2(m2), i3 = rsqrt2(m3);
-    const float2 l0 = __fmul2_rn(m0, i0), l1 = __fmul2_rn(m1, i1), l2 = __fmul2_rn(m2, i2), l3 = __fmul2_rn(m3, i3);
-    const float2 d01 = __ffma2_rn(x0, x1, R.P01), d12 = __ffma2_rn(x1, x2, R.P12), d20 = __ffma2_rn(x2, x0, R.P20);
-    const float2 d13 = __ffma2_rn(x1, x3, R.P13), d32 = __ffma2_rn(x3, x2, R.P32);
-    const float2 NA = __ffma2_rn(x0, P.nAx, R.NA), NB = __ffma2_rn(x2, P.nBx, R.NB);
-    bwd_face2(l0, l1, l2, i0, i1, i2, d01, d12, d20, NA, x0, g, SA, XA);  // A: a = p0, b = p1, c = p2
-    bwd_face2(l2, l1, l3, i2, i1, i3, d12, d13, d32, NB, x2, g, SB, XB);  // B: a = p2, b = p1, c = p3
-}
 
 // Face A (which = 0) or B (which = 1) of a pair as a face alone, in its canonical corner order.
 __device__ __forceinline__ FaceF pair_face(const PairRec &P, int which) {
@@ -367,144 +273,281 @@ __device__ __forceinline__ void for_each_row(const BwdArgs &a, float *wf, RowFn 
     }
 }
 
-// The guarded scalar path over one row (or piece) for one face, folded into its face sums: rows
-// with an odd number of queries, pieces of long rows, and rows whose packed sums are not finite
-// (a query on a vertex or on an edge line).
-__device__ __noinline__ void row_guarded(const FaceF F, float qy, float qz, const float *wf, int64_t i0, int xlen,
-                                         float2 (*ks)[kBwdThreads]) {
-    const RowB R = row_b(F, qy, qz);
-    float S[7], X[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-    for (int ix = 0; ix < xlen; ++ix) bwd_pair<true>(F, R, -win_nqx(wf, i0 + ix), win_g(wf, i0 + ix), S, X);
-    fold_sm(ks, S, X, R.ay, R.az);
+// ---------------------------------------------------------------------------------------------
+// Grid adjoint from the faces' edges. The derivative of one face's solid angle (Eq. (7)) with
+// respect to its vertices depends only on the face's boundary, its three directed edges: for an
+// edge p -> r of the face, with a = p - q and b = r - q,
+//   dOmega/dp += (b x a) / (|a| (|a||b| + a.b)),   dOmega/dr += (b x a) / (|b| (|a||b| + a.b))
+// (the closed form of winding_bnd.cu applied to one triangle, equal to the chain rule through
+// Eq. (7) for q off the face). For the two faces of an edge-sharing pair, A = (p0, p1, p2) and
+// B = (p2, p1, p3) in the canonical orientation, the shared edge is p1 -> p2 in A and p2 -> p1 in
+// B, whose terms are exact negatives: the pair's derivative is the sum over the quad's four edges
+// p0 -> p1, p2 -> p0 (A) and p1 -> p3, p3 -> p2 (B, times B's orientation sign sB = +-1) plus the
+// shared edge p1 -> p2 with multiplicity 1 - sB (0 unless B's input orientation is reversed).
+// Every (pair, query) is still evaluated; per one the four distances (one MUFU reciprocal square
+// root each) serve four edges, each one dot, |a||b| + a.b, one MUFU reciprocal and four sums.
+// Because b x a = r x p - (r - p) x q is linear in q, an edge needs only
+//   S_p = sum g c_p, Q_p = sum g c_p q, S_r, Q_r   (c_p = 1/(|a| (|a||b| + a.b)), c_r with |b|):
+// per grid row the packed sums of g c and g c (-x) for two x-adjacent queries at a time, folded
+// per row into Kahan sums in shared memory (y and z enter as qy S, qz S). At the end the thread
+// forms in FP64 dL/dp = m/(4 pi) [(r x p) S_p - (r - p) x Q_p] (r likewise) and writes each vertex's
+// share into the gradient slots of the pair's faces (A's slot gets A's edges and the shared edge,
+// B's slot B's edges); the gather sums the slots per vertex, so only the per-vertex sum is that of
+// the face formula, not each slot.
+constexpr int kEdgeSlots = 8;  // per directed edge: S_p, Q_p (3), S_r, Q_r (3)
+
+// Edge tables: pair (4 points, edges 0-3 the quad, 4 the shared edge) and single face (3 edges).
+template <int NP>
+__device__ __forceinline__ constexpr int edge_start(int k) {
+    return NP == 4 ? (k == 0 ? 0 : k == 1 ? 2 : k == 2 ? 1 : k == 3 ? 3 : 1) : (k == 0 ? 0 : k == 1 ? 1 : 2);
+}
+template <int NP>
+__device__ __forceinline__ constexpr int edge_end(int k) {
+    return NP == 4 ? (k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 3 : k == 3 ? 2 : 2) : (k == 0 ? 1 : k == 1 ? 2 : 0);
 }
 
-__device__ __forceinline__ bool all_finite2(const float2 (&S)[7], const float2 (&X)[7]) {
-    float t = 0.f;
-#pragma unroll
-    for (int i = 0; i < 7; ++i) t += (S[i].x + S[i].y) + (X[i].x + X[i].y);
-    return isfinite(t);
-}
+// Packed per-row sums of one directed edge: g c and g c (-x) at its start (p) and its end (r).
+struct EdgeRow2 {
+    float2 Sp, Xp, Sr, Xr;
+};
 
-__device__ __forceinline__ void fold_sm2(float2 (*ks)[kBwdThreads], const float2 (&S2)[7], const float2 (&X2)[7],
-                                         float ay, float az) {
-    float S[7], X[7];
+// The NP points of a pair or face, their per-row (y, z) parts and the edges' per-row dot parts.
+template <int NP, int NE>
+struct EdgeRowConst {
+    float2 px[NP];  // point x, broadcast to both halves
+    float2 L[NP];   // (y - qy)^2 + (z - qz)^2
+    float2 P[NE];   // (y_p - qy)(y_r - qy) + (z_p - qz)(z_r - qz) of each edge
+};
+
+// One row (or piece) of packed query pairs from the window: every edge's four sums.
+template <int NP, int NE>
+__device__ __forceinline__ void edges_row2(const EdgeRowConst<NP, NE> &C, const float *wf, int64_t i0, int xlen,
+                                           EdgeRow2 (&R)[NE]) {
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        S[k] = S2[k].x + S2[k].y;
-        X[k] = X2[k].x + X2[k].y;
+    for (int k = 0; k < NE; ++k) R[k].Sp = R[k].Xp = R[k].Sr = R[k].Xr = make_float2(0.f, 0.f);
+    const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
+#pragma unroll 2
+    for (int p = 0; p < xlen / 2; ++p) {
+        const float4 q = wp[p];
+        const float2 nqx = make_float2(q.x, q.y), g = make_float2(q.z, q.w);
+        float2 x[NP], l[NP], iv[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            x[k] = __fadd2_rn(C.px[k], nqx);
+            const float2 m = __ffma2_rn(x[k], x[k], C.L[k]);
+            iv[k] = make_float2(rsqrt_approx(m.x), rsqrt_approx(m.y));
+            l[k] = __fmul2_rn(m, iv[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const int s = edge_start<NP>(k), e = edge_end<NP>(k);
+            const float2 t = __ffma2_rn(l[s], l[e], __ffma2_rn(x[s], x[e], C.P[k]));  // |a||b| + a.b
+            const float2 c = __fmul2_rn(g, make_float2(rcp_approx(t.x), rcp_approx(t.y)));
+            const float2 cp = __fmul2_rn(c, iv[s]), cr = __fmul2_rn(c, iv[e]);
+            R[k].Sp = __fadd2_rn(R[k].Sp, cp);
+            R[k].Xp = __ffma2_rn(cp, nqx, R[k].Xp);
+            R[k].Sr = __fadd2_rn(R[k].Sr, cr);
+            R[k].Xr = __ffma2_rn(cr, nqx, R[k].Xr);
+        }
     }
-    fold_sm(ks, S, X, ay, az);
 }
 
-// A CTA of single faces: thread t owns one face (from the list of unpaired faces, or face index
-// order when there is no list).
-__device__ __forceinline__ void bwd_grid_singles(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads]) {
+// The guarded scalar path of one row (or piece) and one edge: rows with an odd number of queries,
+// pieces of long rows, and rows whose packed sums are not finite (a query at an endpoint or on the
+// edge segment, where the derivative does not exist: those pairs are skipped). Returns the row's
+// S_p, sum g c_p (-x), S_r, sum g c_r (-x).
+__device__ __noinline__ float4 edge_row_guarded(float px, float py, float pz, float rx, float ry, float rz, float qy,
+                                               float qz, const float *wf, int64_t i0, int xlen) {
+    const float ay = py - qy, az = pz - qz, by = ry - qy, bz = rz - qz;
+    float sp = 0.f, sr = 0.f, xp = 0.f, xr = 0.f;
+    for (int ix = 0; ix < xlen; ++ix) {
+        const float nqx = win_nqx(wf, i0 + ix), g = win_g(wf, i0 + ix);
+        const float ax = px + nqx, bx = rx + nqx;
+        const float la2 = fmaf(ax, ax, fmaf(ay, ay, az * az)), lb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        if (!(la2 > 0.f) || !(lb2 > 0.f)) continue;
+        const float la = sqrtf(la2), lb = sqrtf(lb2);
+        const float t = fmaf(la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)));
+        if (!(t > 1e-30f * la * lb)) continue;
+        const float c = g / t, cp = c / la, cr = c / lb;
+        sp += cp;
+        sr += cr;
+        xp = fmaf(cp, nqx, xp);
+        xr = fmaf(cr, nqx, xr);
+    }
+    return make_float4(sp, xp, sr, xr);
+}
+
+// Fold one edge's row sums into its 8 Kahan slots: S_p, Q_p = (sum g c_p x, qy S_p, qz S_p), S_r, Q_r.
+__device__ __forceinline__ void fold_edge(float2 (*ks)[kBwdThreads], int edge, float sp, float nxp, float sr,
+                                          float nxr, float qy, float qz) {
+    const int t = threadIdx.x;
+    float2 (*k)[kBwdThreads] = ks + kEdgeSlots * edge;
+    kahan_sm(&k[0][t], sp);
+    kahan_sm(&k[1][t], -nxp);
+    kahan_sm(&k[2][t], qy * sp);
+    kahan_sm(&k[3][t], qz * sp);
+    kahan_sm(&k[4][t], sr);
+    kahan_sm(&k[5][t], -nxr);
+    kahan_sm(&k[6][t], qy * sr);
+    kahan_sm(&k[7][t], qz * sr);
+}
+
+// m/(4 pi) [(r x p) S - (r - p) x Q] for both endpoints of edge `edge` (FP64, from its Kahan slots),
+// added to gp (the start p) and gr (the end r).
+__device__ __forceinline__ void edge_grad(float2 (*ks)[kBwdThreads], int edge, const double (&p)[3],
+                                          const double (&r)[3], double m, double (&gp)[3], double (&gr)[3]) {
+    const int t = threadIdx.x;
+    float2 (*k)[kBwdThreads] = ks + kEdgeSlots * edge;
+    double v[kEdgeSlots];
+#pragma unroll
+    for (int i = 0; i < kEdgeSlots; ++i) v[i] = (double)k[i][t].x - (double)k[i][t].y;
+    const double w = m * (0.5 * kInv2PiD);
+    const double d[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
+    const double rxp[3] = {r[1] * p[2] - r[2] * p[1], r[2] * p[0] - r[0] * p[2], r[0] * p[1] - r[1] * p[0]};
+    const double *Qp = v + 1, *Qr = v + 5;
+    const double dxp[3] = {d[1] * Qp[2] - d[2] * Qp[1], d[2] * Qp[0] - d[0] * Qp[2], d[0] * Qp[1] - d[1] * Qp[0]};
+    const double dxr[3] = {d[1] * Qr[2] - d[2] * Qr[1], d[2] * Qr[0] - d[0] * Qr[2], d[0] * Qr[1] - d[1] * Qr[0]};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        gp[c] += w * (rxp[c] * v[0] - dxp[c]);
+        gr[c] += w * (rxp[c] * v[4] - dxr[c]);
+    }
+}
+
+// Every row of the CTA's split for the NP points and NE edges of this thread: packed rows, the
+// guarded path for the others, folded into the edges' Kahan slots.
+template <int NP, int NE>
+__device__ __forceinline__ void edges_all_rows(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads],
+                                               const float (&X)[NP], const float (&Y)[NP], const float (&Z)[NP]) {
+#pragma unroll
+    for (int k = 0; k < kEdgeSlots * NE; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
+    for_each_row(a, wf, [&](float qy, float qz, int64_t i0, int xlen, bool packed) {
+        float y[NP], z[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            y[k] = Y[k] - qy;
+            z[k] = Z[k] - qz;
+        }
+        bool ok = false;
+        if (packed) {
+            EdgeRowConst<NP, NE> C;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                C.px[k] = bc2(X[k]);
+                C.L[k] = bc2(fmaf(y[k], y[k], z[k] * z[k]));
+            }
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                const int s = edge_start<NP>(k), e = edge_end<NP>(k);
+                C.P[k] = bc2(fmaf(y[s], y[e], z[s] * z[e]));
+            }
+            EdgeRow2 R[NE];
+            edges_row2<NP, NE>(C, wf, i0, xlen, R);
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < NE; ++k)
+                t += ((R[k].Sp.x + R[k].Sp.y) + (R[k].Xp.x + R[k].Xp.y)) + ((R[k].Sr.x + R[k].Sr.y) + (R[k].Xr.x + R[k].Xr.y));
+            ok = isfinite(t);
+            if (ok) {
+#pragma unroll
+                for (int k = 0; k < NE; ++k)
+                    fold_edge(ks, k, R[k].Sp.x + R[k].Sp.y, R[k].Xp.x + R[k].Xp.y, R[k].Sr.x + R[k].Sr.y,
+                              R[k].Xr.x + R[k].Xr.y, qy, qz);
+            }
+        }
+        if (!ok) {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                const int s = edge_start<NP>(k), e = edge_end<NP>(k);
+                const float4 v = edge_row_guarded(X[s], Y[s], Z[s], X[e], Y[e], Z[e], qy, qz, wf, i0, xlen);
+                fold_edge(ks, k, v.x, v.y, v.z, v.w, qy, qz);
+            }
+        }
+    });
+}
+
+// A CTA of edge-sharing face pairs, edge form: thread t owns pair t. When a pair of the warp has
+// B reversed, the warp also evaluates the shared edge (multiplicity 1 - sB: 2 for that pair, 0 for
+// the others); otherwise the four quad edges suffice.
+__device__ __forceinline__ void bwd_grid_pairs_edges(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads]) {
+    const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    const int64_t ic = idx < a.np ? idx : a.np - 1;
+    const PairRec P = a.prec[DV_INB(ic, a.np, kSiteBwdRecord) ? ic : 0];
+    const int32_t *tp = a.ptopo + 8 * ic;
+    const int code = tp[6];
+    const bool rev = (code >> 12) & 1;
+    const float X[4] = {P.r0.x, P.r1.x, P.r2.x, P.r3.x};
+    const float Y[4] = {P.r0.y, P.r1.y, P.r2.y, P.r3.y};
+    const float Z[4] = {P.r0.z, P.r1.z, P.r2.z, P.r3.z};
+    const bool five = __syncthreads_or(rev) != 0;  // CTA-uniform: the row loop has barriers
+    if (five)
+        edges_all_rows<4, 5>(a, wf, ks, X, Y, Z);
+    else
+        edges_all_rows<4, 4>(a, wf, ks, X, Y, Z);
+    if (idx >= a.np) return;
+    const double p[4][3] = {{P.r0.x, P.r0.y, P.r0.z}, {P.r1.x, P.r1.y, P.r1.z},
+                            {P.r2.x, P.r2.y, P.r2.z}, {P.r3.x, P.r3.y, P.r3.z}};
+    const double sB = rev ? -1.0 : 1.0;
+    // slot A: canonical corners (p0, p1, p2); slot B: (p2, p1, p3)
+    double gA[3][3] = {}, gB[3][3] = {};
+    edge_grad(ks, 0, p[0], p[1], 1.0, gA[0], gA[1]);  // p0 -> p1
+    edge_grad(ks, 1, p[2], p[0], 1.0, gA[2], gA[0]);  // p2 -> p0
+    edge_grad(ks, 2, p[1], p[3], sB, gB[1], gB[2]);   // p1 -> p3
+    edge_grad(ks, 3, p[3], p[2], sB, gB[2], gB[0]);   // p3 -> p2
+    if (five && rev) edge_grad(ks, 4, p[1], p[2], 1.0 - sB, gA[1], gA[2]);  // shared p1 -> p2
+    float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
+    const int cA = code & 63, cB = (code >> 6) & 63;
+    if (DV_INB(tp[4], a.nf, kSiteBwdFaceGrad)) {
+        float *o = out + (int64_t)tp[4] * 9;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[3 * ((cA >> (2 * j)) & 3) + c] = (float)gA[j][c];
+    }
+    if (DV_INB(tp[5], a.nf, kSiteBwdFaceGrad)) {
+        float *o = out + (int64_t)tp[5] * 9;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[3 * ((cB >> (2 * j)) & 3) + c] = (float)gB[j][c];
+    }
+}
+
+// A CTA of single faces, edge form: thread t owns one face (unpaired list, or face index order).
+__device__ __forceinline__ void bwd_grid_singles_edges(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads]) {
     const int64_t count = a.singles ? a.nsingle : a.nf;
     const int64_t idx = ((int64_t)blockIdx.x - a.pblocks) * kBwdThreads + threadIdx.x;
     const int64_t ic = idx < count ? idx : count - 1;
     int64_t f = a.singles ? (DV_INB(ic, a.nsingle, kSiteBwdRecord) ? (int64_t)a.singles[ic] : 0) : ic;
     if (!DV_INB(f, a.nf, kSiteBwdRecord)) f = 0;
-    const FaceF F = load_face(a.rec, f);
-    FaceF2 F2;
-    F2.v0x = bc2(F.v0x);
-    F2.v1x = bc2(F.v1x);
-    F2.v2x = bc2(F.v2x);
-    F2.nx = bc2(F.nx);
+    const FaceRec r = a.rec[f];
+    const float X[3] = {r.r0.x, r.r1.x, r.r2.x}, Y[3] = {r.r0.y, r.r1.y, r.r2.y}, Z[3] = {r.r0.z, r.r1.z, r.r2.z};
+    edges_all_rows<3, 3>(a, wf, ks, X, Y, Z);
+    if (idx >= count || !DV_INB(f, a.nf, kSiteBwdFaceGrad)) return;
+    const double p[3][3] = {{r.r0.x, r.r0.y, r.r0.z}, {r.r1.x, r.r1.y, r.r1.z}, {r.r2.x, r.r2.y, r.r2.z}};
+    double g[3][3] = {};
+    edge_grad(ks, 0, p[0], p[1], 1.0, g[0], g[1]);
+    edge_grad(ks, 1, p[1], p[2], 1.0, g[1], g[2]);
+    edge_grad(ks, 2, p[2], p[0], 1.0, g[2], g[0]);
+    float *o = a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9;
 #pragma unroll
-    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
-    for_each_row(a, wf, [&](float qy, float qz, int64_t i0, int xlen, bool packed) {
-        bool ok = false;
-        if (packed) {
-            const RowB R = row_b(F, qy, qz);
-            RowB2 R2;
-            R2.La = bc2(R.La);
-            R2.Lb = bc2(R.Lb);
-            R2.Lc = bc2(R.Lc);
-            R2.Pab = bc2(R.Pab);
-            R2.Pbc = bc2(R.Pbc);
-            R2.Pca = bc2(R.Pca);
-            R2.Nyz = bc2(R.Nyz);
-            float2 S2[7], X2[7];
+    for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int k = 0; k < 7; ++k) S2[k] = X2[k] = make_float2(0.f, 0.f);
-            const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
-#pragma unroll 4
-            for (int p = 0; p < xlen / 2; ++p) {
-                const float4 q = wp[p];
-                bwd_pair2(F2, R2, make_float2(q.x, q.y), make_float2(q.z, q.w), S2, X2);
-            }
-            ok = all_finite2(S2, X2);
-            if (ok) fold_sm2(ks, S2, X2, R.ay, R.az);
-        }
-        if (!ok) row_guarded(F, qy, qz, wf, i0, xlen, ks);
-    });
-    if (idx < count && DV_INB(f, a.nf, kSiteBwdFaceGrad))
-        write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+        for (int c = 0; c < 3; ++c) o[3 * j + c] = (float)g[j][c];
 }
 
-// A CTA of edge-sharing face pairs: thread t owns pair t; its two faces keep separate sums
-// (shared-memory slots 0..17 for A, 18..35 for B).
-__device__ __forceinline__ void bwd_grid_pairs(const BwdArgs &a, float *wf, float2 (*ks)[kBwdThreads]) {
-    const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    const int64_t ic = idx < a.np ? idx : a.np - 1;
-    const PairRec P = a.prec[DV_INB(ic, a.np, kSiteBwdRecord) ? ic : 0];
-    PairF2 P2;
-    P2.p0x = bc2(P.r0.x);
-    P2.p1x = bc2(P.r1.x);
-    P2.p2x = bc2(P.r2.x);
-    P2.p3x = bc2(P.r3.x);
-    P2.nAx = bc2(P.r0.w);
-    P2.nBx = bc2(P.r3.w);
-    float2(*ksB)[kBwdThreads] = ks + kFaceSlots;
-#pragma unroll
-    for (int k = 0; k < 2 * kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
-    for_each_row(a, wf, [&](float qy, float qz, int64_t i0, int xlen, bool packed) {
-        bool okA = false, okB = false;
-        if (packed) {
-            const PairRow2 R = pair_row(P, qy, qz);
-            float2 SA[7], XA[7], SB[7], XB[7];
-#pragma unroll
-            for (int k = 0; k < 7; ++k) SA[k] = XA[k] = SB[k] = XB[k] = make_float2(0.f, 0.f);
-            const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
-#pragma unroll 2
-            for (int p = 0; p < xlen / 2; ++p) {
-                const float4 q = wp[p];
-                bwd_quad2(P2, R, make_float2(q.x, q.y), make_float2(q.z, q.w), SA, XA, SB, XB);
-            }
-            okA = all_finite2(SA, XA);
-            okB = all_finite2(SB, XB);
-            if (okA) fold_sm2(ks, SA, XA, P.r0.y - qy, P.r0.z - qz);
-            if (okB) fold_sm2(ksB, SB, XB, P.r2.y - qy, P.r2.z - qz);
-        }
-        if (!okA) row_guarded(pair_face(P, 0), qy, qz, wf, i0, xlen, ks);
-        if (!okB) row_guarded(pair_face(P, 1), qy, qz, wf, i0, xlen, ksB);
-    });
-    if (idx < a.np) {
-        const int32_t *t = a.ptopo + 8 * idx;
-        const int code = t[6];
-        float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
-        if (DV_INB(t[4], a.nf, kSiteBwdFaceGrad))
-            write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
-        if (DV_INB(t[5], a.nf, kSiteBwdFaceGrad))
-            write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
-                               (code >> 12) & 1 ? -1.0 : 1.0);
-    }
-}
-
-// Grid adjoint: CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces. Dynamic
-// shared memory: the query window, then 2 x 18 face-sum slots per thread.
-constexpr size_t kBwdGridSmem = sizeof(float) * 2 * kBwdWin + sizeof(float2) * 2 * kFaceSlots * kBwdThreads;
+// Grid adjoint (edge form): CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces.
+// Dynamic shared memory: the query window, then 5 edges x 8 Kahan slots per thread.
+constexpr size_t kBwdGridSmem = sizeof(float) * 2 * kBwdWin + sizeof(float2) * 5 * kEdgeSlots * kBwdThreads;
 
 __global__ void __launch_bounds__(kBwdThreads, 3) bwd_grid_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) float bwd_smem[];
     float *wf = bwd_smem;
     float2(*ks)[kBwdThreads] = reinterpret_cast<float2(*)[kBwdThreads]>(bwd_smem + 2 * kBwdWin);
     if ((int64_t)blockIdx.x < a.pblocks)
-        bwd_grid_pairs(a, wf, ks);
+        bwd_grid_pairs_edges(a, wf, ks);
     else
-        bwd_grid_singles(a, wf, ks);
+        bwd_grid_singles_edges(a, wf, ks);
 }
 
 // List path: arbitrary queries, so no row sharing. Two queries per packed FP32x2 instruction;
@@ -523,7 +566,9 @@ struct FaceL2 {
 __device__ __forceinline__ void list_face2(float2 la, float2 lb, float2 lc, float2 ia, float2 ib, float2 ic,
                                            float2 ab, float2 bcd, float2 ca, float2 N, float2 ax, float2 ay,
                                            float2 az, float2 g, float2 (&T)[6], float2 (&U)[4][3]) {
-    const float2 tc = __ffma2_rn(lb, la, ab);  // operand order as in bwd_face2
+    // |a||b| + a.b written lb * la, so that for the two faces of a pair the shared edge's term
+    // (the other face's lb * lc + b.c) is the same expression, computed once
+    const float2 tc = __ffma2_rn(lb, la, ab);
     float2 D = __fmul2_rn(tc, lc);
     D = __ffma2_rn(la, bcd, D);
     D = __ffma2_rn(lb, ca, D);
