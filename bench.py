@@ -56,11 +56,12 @@ UNIT = "pairs/s"
 # a rate on this basis is an algorithmic-equivalent rate that can exceed the FP32 peak.
 OPS_FWD = 59
 OPS_BWD = 120
-# FP32 lane operations the grid adjoint kernel executes per pair, counted from its code (FMA = 1):
-# 42 for a face alone, 38.5 for a face of an edge-sharing pair (distances and dots shared). Used
-# when no measured count (EXECUTED) matches the kernel's current source.
-EXEC_BWD_SINGLE = 42.0
-EXEC_BWD_PAIRED = 38.5
+# FP32 lane operations the grid adjoint kernel executes per pair, counted from its code (FMA = 1;
+# edge form: per point 3, per edge 9 per query): 36 for a face alone (3 points, 3 edges), 24 for a
+# face of an edge-sharing pair (4 points and 4 edges per two faces). Used when no measured count
+# (EXECUTED) matches the kernel's current source.
+EXEC_BWD_SINGLE = 36.0
+EXEC_BWD_PAIRED = 24.0
 
 # Executed operations per unit, measured by ncu thread-instruction counters on the same mesh over
 # a 64^3 grid: FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2) per query x face pair for the
@@ -393,7 +394,8 @@ def _kernel_rooflines(args, prof, pairs, nflagged, ne, F, nv, fp32_peak, fp64_pe
         if ex is None and name == "bwd_grid":
             pair_recs, singles = __import__("paper_2407_11272_b300.dv", fromlist=["dv"]).dv_build_face_pairs(F, nv)
             ex = (EXEC_BWD_PAIRED * 2 * len(pair_recs) + EXEC_BWD_SINGLE * len(singles)) / len(F)
-            basis = "counted from the kernel's code (38.5 per paired face, 42 per single face)"
+            basis = (f"counted from the kernel's code ({EXEC_BWD_PAIRED:g} per paired face, "
+                     f"{EXEC_BWD_SINGLE:g} per single face)")
         if ex is not None:
             ent.update(executed_ops_per_pair=ex, frac_executed=ex * rate / fp32_peak, executed_basis=basis)
         out[name] = ent

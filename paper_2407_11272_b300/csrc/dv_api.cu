@@ -692,7 +692,8 @@ dv_status dv_winding_backward_boundary(const dv_mesh *mesh, const float *d_queri
     m->last_stream = s;
     if ((st = boundary_device(m, s))) return st;
     const dv::BndPlan plan = dv::plan_boundary(n, m->nb, grid != nullptr, grid ? &gf : nullptr, m->num_sms);
-    if (m->nb > 0 && (st = grow(m->ws_bpart, m->cap_bpart, (int64_t)plan.nsplit * m->nb * 8, s))) return st;
+    const int64_t bpart = (int64_t)plan.nsplit * m->nb * dv::kBndPartFloats;
+    if (m->nb > 0 && (st = grow(m->ws_bpart, m->cap_bpart, bpart, s))) return st;
     DV_CUDA(dv::launch_boundary_backward(plan, m->bnd_rec, m->nb, grid ? &gf : nullptr, d_queries, n, d_upstream,
                                          m->ws_bpart, s));
     DV_CUDA(dv::launch_boundary_gather(m->nv, m->bnd_rec, m->nb, m->ws_bpart, plan.nsplit, m->bnd_vptr, m->bnd_vend,

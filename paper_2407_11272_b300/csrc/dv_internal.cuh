@@ -169,6 +169,42 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return r;
 }
 
+// ------------------------------------------------------------------------------------------
+// Edge terms of the adjoint, shared by the face-pair and the boundary-curve forms: for a directed
+// edge p -> r seen from q (a = p - q, b = r - q, d = r - p), dOmega/dp = (b x a) / (|a| t) with
+// t = |a||b| + a.b. Where a and b point apart (q near the segment) that sum cancels: its FP32
+// relative error grows like eps / (1 + cos(a, b)). There edge_t takes t = |a x b|^2 / (|a||b| - a.b)
+// with a x b = a x d, whose denominator does not cancel and whose cross product has relative error
+// ~ eps |a| / dist(q, edge).
+__device__ __forceinline__ float edge_t(float ax, float ay, float az, float la, float lb, float ab, float dx, float dy,
+                                        float dz) {
+    if (ab >= 0.f) return fmaf(la, lb, ab);
+    const float wx = fmaf(ay, dz, -az * dy), wy = fmaf(az, dx, -ax * dz), wz = fmaf(ax, dy, -ay * dx);
+    return fmaf(wx, wx, fmaf(wy, wy, wz * wz)) / fmaf(la, lb, -ab);
+}
+
+// Whether the grid row through (qy, qz) passes within kNearEdge |r - p| of the segment p -> r, from
+// the row's offsets (ys, zs) = (p_y - qy, p_z - qz), (ye, ze) likewise for r, and the edge's squared
+// length L2: the row is a line along x, so its distance to the segment is the distance from the
+// origin to the segment's projection on the (y, z) plane. Beyond that distance every query of the
+// row has 1 + cos(a, b) >= 7e-3, so the packed t's relative error stays below ~4e-5.
+constexpr float kNearEdge = 0.03f;
+__device__ __forceinline__ bool row_near_edge(float ys, float zs, float ye, float ze, float L2) {
+    const float dy = ye - ys, dz = ze - zs;
+    const float K = kNearEdge * kNearEdge * L2;
+    const float sn = -fmaf(ys, dy, zs * dz), den = fmaf(dy, dy, dz * dz);
+    if (sn <= 0.f) return fmaf(ys, ys, zs * zs) < K;
+    if (sn >= den) return fmaf(ye, ye, ze * ze) < K;
+    const float cr = fmaf(ys, dz, -zs * dy);  // distance to the projected line times sqrt(den)
+    return cr * cr < K * den;
+}
+
+// Query lists: a query whose t = |a||b| + a.b falls below kNearCos |a.b| for some edge
+// (1 + cos(a, b) < ~0.01: q near the segment, where the packed t cancels) sends its chunk through
+// the guarded path; for the others the packed t's relative error stays below ~3e-5. The test is the
+// sign of t + kNearCos a.b.
+constexpr float kNearCos = 0.01f;
+
 // Sticky error word: first error code wins.
 __device__ __forceinline__ void set_error(int *err, int code) {
     if (err) atomicCAS(err, 0, code);
@@ -268,6 +304,7 @@ cudaError_t launch_pack_strips(const float *verts, int64_t nv, int64_t nf, const
                                StripRec *srec, StripRec64 *srec64, cudaStream_t s);
 
 // winding_bnd.cu: the adjoint from the mesh's boundary edges.
+constexpr int kBndPartFloats = 6;  // per (split, boundary edge): V_p (3), V_r (3)
 struct BndPlan {
     int64_t eblocks;    // CTAs over boundary edges
     int nsplit;         // query (row) splits (grid dimension y)

@@ -18,8 +18,7 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int arrive) {
     }
     __syncthreads();
     if (arrive && threadIdx.x == 0) {
-        uint64_t state;
-        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(&bar)) : "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
     }
     if (!mbar_wait_bounded(&bar, 0u, limit_ns)) set_error(&g_selftest_err, (int)DV_ERR_TIMEOUT);
 }

@@ -12,14 +12,19 @@
 // with exact zeros on closed meshes and on vertices away from the boundary, and it needs one pair
 // evaluation per (boundary edge, query) instead of per (face, query).
 //
-// Because b x a = r x p - e x q (e = r - p) is linear in q, per edge only
-//   S_p = sum g c_p, Q_p = sum g c_p q, S_r = sum g c_r, Q_r = sum g c_r q
-// (c_p = 1 / (|a| (|a||b| + a.b)), c_r likewise with |b|) are accumulated; the gather forms
-//   dL/dp += m/(4 pi) [(r x p) S_p - e x Q_p],  dL/dr += m/(4 pi) [(r x p) S_r - e x Q_r]
-// in FP64. On a grid row the y and z parts of a, b are constant; two x-adjacent queries share
-// one packed FP32x2 instruction. Sums are FP32 per row (grid) or per chunk (list), Kahan across
+// With d = r - p, b x a = d x a = d x b, so the term at either endpoint is its c times d x (its own
+// offset from q): per edge only
+//   V_p = sum g c_p a,   V_r = sum g c_r b
+// (c_p = 1 / (|a| (|a||b| + a.b)), c_r likewise with |b|) are accumulated, and the gather forms
+//   dL/dp += m/(4 pi) d x V_p,  dL/dr += m/(4 pi) d x V_r
+// in FP64 (offsets, not absolute coordinates: the sums do not depend on where the mesh sits). On
+// a grid row the y and z parts of a, b are constant (V_p = (sum g c_p a_x, a_y S_p, a_z S_p)); two
+// x-adjacent queries share one packed FP32x2 instruction. Sums are FP32 per row (grid) or per
+// chunk (list), Kahan across
 // rows in shared memory. A pair with |a||b| + a.b = 0 (q on the edge segment, i.e. on the mesh)
-// has no derivative; such rows are recomputed by a guarded path that skips those pairs.
+// has no derivative; such rows are recomputed by a guarded path that skips those pairs. Rows (grid)
+// or chunks (list) with a query near the segment, where the packed sum |a||b| + a.b cancels, take
+// the same guarded path with t from edge_t.
 #include <math.h>
 
 #include "dv_internal.cuh"
@@ -28,7 +33,7 @@ namespace dv {
 
 constexpr int kBndThreads = 128;
 constexpr int kBndWin = 2048;   // grid: queries staged per window; list: 2 x (x, y, z, g) float4s
-constexpr int kBndSlots = 8;    // S_p, S_r, Q_p (3), Q_r (3)
+constexpr int kBndSlots = kBndPartFloats;  // V_p (3), V_r (3)
 constexpr int kBndChunk = 128;  // list path: queries per plain FP32 partial sum
 
 struct BndArgs {
@@ -39,7 +44,7 @@ struct BndArgs {
     int64_t nq;
     const float *upstream;
     int64_t per_split;  // grid: rows per split; list: queries per split
-    float *part;        // [nsplit][nb][8]
+    float *part;        // [nsplit][nb][6]
 };
 
 __device__ __forceinline__ void kahan_slot(float2 *slot, float x) {
@@ -51,14 +56,15 @@ __device__ __forceinline__ void kahan_slot(float2 *slot, float x) {
     *slot = k;
 }
 
-// Scalar guarded pair: skips q at an endpoint or on the edge segment.
-__device__ __forceinline__ void bnd_pair_guarded(float ax, float ay, float az, float bx, float by, float bz, float g,
-                                                 float &sp, float &sr, float &cpq, float &crq) {
+// Scalar guarded pair (t from edge_t, d = r - p): skips q at an endpoint or on the edge segment.
+__device__ __forceinline__ void bnd_pair_guarded(float ax, float ay, float az, float bx, float by, float bz, float dx,
+                                                 float dy, float dz, float g, float &sp, float &sr, float &cpq,
+                                                 float &crq) {
     const float la2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
     const float lb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
     if (!(la2 > 0.f) || !(lb2 > 0.f)) return;
     const float la = sqrtf(la2), lb = sqrtf(lb2);
-    const float De = fmaf(la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)));
+    const float De = edge_t(ax, ay, az, la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)), dx, dy, dz);
     if (!(De > 1e-30f * la * lb)) return;
     const float gr = g / De;
     cpq = gr / la;
@@ -73,6 +79,8 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_grid_kernel(const BndArgs 
     const int64_t e = (int64_t)blockIdx.x * kBndThreads + threadIdx.x;
     const BndRec R = a.rec[e < a.nb ? e : a.nb - 1];
     const float2 px = make_float2(R.p.x, R.p.x), rx = make_float2(R.r.x, R.r.x);
+    const float dx = R.r.x - R.p.x, dy = R.r.y - R.p.y, dz = R.r.z - R.p.z;
+    const float L2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const int nx = a.g.n[0], ny = a.g.n[1];
     const int64_t nrows = (int64_t)a.g.n[1] * a.g.n[2];
     const int64_t r0 = (int64_t)blockIdx.y * a.per_split;
@@ -107,12 +115,14 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_grid_kernel(const BndArgs 
                 const float ay = R.p.y - qy, az = R.p.z - qz, by = R.r.y - qy, bz = R.r.z - qz;
                 const float La = fmaf(ay, ay, az * az), Lb = fmaf(by, by, bz * bz), Pab = fmaf(ay, by, az * bz);
                 const float2 La2 = make_float2(La, La), Lb2 = make_float2(Lb, Lb), Pab2 = make_float2(Pab, Pab);
-                float2 Sp = make_float2(0.f, 0.f), Sr = Sp, Xp = Sp, Xr = Sp;  // X = sum g c (-x)
+                float2 Sp = make_float2(0.f, 0.f), Sr = Sp, Xp = Sp, Xr = Sp;  // X = sum g c a_x (b_x)
                 const int64_t p0 = whole ? rr * nx / 2 : 0;
                 const int np = whole ? nx / 2 : (int)((len + 1) / 2);
                 const float4 *wp = reinterpret_cast<const float4 *>(wf) + p0;
+                // a row close to the edge segment goes through the guarded path (edge_t)
+                const bool near = row_near_edge(ay, az, by, bz, L2);
 #pragma unroll 4
-                for (int p = 0; p < np; ++p) {
+                for (int p = 0; p < (near ? 0 : np); ++p) {
                     const float4 q = wp[p];
                     const float2 nqx = make_float2(q.x, q.y);
                     const float2 ax = __fadd2_rn(px, nqx), bx = __fadd2_rn(rx, nqx);
@@ -124,32 +134,32 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_grid_kernel(const BndArgs 
                     const float2 cp = __fmul2_rn(gr, ia), cr = __fmul2_rn(gr, ib);
                     Sp = __fadd2_rn(Sp, cp);
                     Sr = __fadd2_rn(Sr, cr);
-                    Xp = __ffma2_rn(cp, nqx, Xp);
-                    Xr = __ffma2_rn(cr, nqx, Xr);
+                    Xp = __ffma2_rn(cp, ax, Xp);
+                    Xr = __ffma2_rn(cr, bx, Xr);
                 }
                 float sp = Sp.x + Sp.y, sr = Sr.x + Sr.y, xp = Xp.x + Xp.y, xr = Xr.x + Xr.y;
-                if (!isfinite(sp + sr + xp + xr)) {
-                    // a query on an endpoint or on the edge segment: skip those pairs
+                if (near || !isfinite(sp + sr + xp + xr)) {
+                    // near the segment, or a query on an endpoint or on the segment (those pairs
+                    // are skipped)
                     sp = sr = xp = xr = 0.f;
                     const int cnt = whole ? nx : (int)len;
                     for (int i = 0; i < cnt; ++i) {
                         const int64_t wi = 2 * p0 + i;
                         const float nqxs = wf[4 * (wi >> 1) + (wi & 1)], gs = wf[4 * (wi >> 1) + 2 + (wi & 1)];
                         float cpq = 0.f, crq = 0.f;
-                        bnd_pair_guarded(R.p.x + nqxs, ay, az, R.r.x + nqxs, by, bz, gs, sp, sr, cpq, crq);
-                        xp = fmaf(cpq, nqxs, xp);
-                        xr = fmaf(crq, nqxs, xr);
+                        bnd_pair_guarded(R.p.x + nqxs, ay, az, R.r.x + nqxs, by, bz, dx, dy, dz, gs, sp, sr, cpq,
+                                         crq);
+                        xp = fmaf(cpq, R.p.x + nqxs, xp);
+                        xr = fmaf(crq, R.r.x + nqxs, xr);
                     }
                 }
                 const int t = threadIdx.x;
-                kahan_slot(&ks[0][t], sp);
-                kahan_slot(&ks[1][t], sr);
-                kahan_slot(&ks[2][t], -xp);  // Q_p.x = sum g c_p x
-                kahan_slot(&ks[3][t], qy * sp);
-                kahan_slot(&ks[4][t], qz * sp);
-                kahan_slot(&ks[5][t], -xr);
-                kahan_slot(&ks[6][t], qy * sr);
-                kahan_slot(&ks[7][t], qz * sr);
+                kahan_slot(&ks[0][t], xp);  // V_p = (sum g c_p a_x, a_y S_p, a_z S_p)
+                kahan_slot(&ks[1][t], ay * sp);
+                kahan_slot(&ks[2][t], az * sp);
+                kahan_slot(&ks[3][t], xr);  // V_r likewise with b
+                kahan_slot(&ks[4][t], by * sr);
+                kahan_slot(&ks[5][t], bz * sr);
             }
             if (whole) break;
         }
@@ -168,6 +178,8 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_list_kernel(const BndArgs 
     const BndRec R = a.rec[e < a.nb ? e : a.nb - 1];
     const float2 px = make_float2(R.p.x, R.p.x), py = make_float2(R.p.y, R.p.y), pz = make_float2(R.p.z, R.p.z);
     const float2 rx = make_float2(R.r.x, R.r.x), ry = make_float2(R.r.y, R.r.y), rz = make_float2(R.r.z, R.r.z);
+    const float dx = R.r.x - R.p.x, dy = R.r.y - R.p.y, dz = R.r.z - R.p.z;
+    const float2 kn = make_float2(kNearCos, kNearCos);
     const int64_t q0 = (int64_t)blockIdx.y * a.per_split;
     const int64_t q1 = q0 + a.per_split < a.nq ? q0 + a.per_split : a.nq;
 #pragma unroll
@@ -184,7 +196,9 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_list_kernel(const BndArgs 
         __syncthreads();
         for (int c0 = 0; c0 < len2; c0 += kBndChunk) {
             const int c1 = c0 + kBndChunk < len2 ? c0 + kBndChunk : len2;
-            float2 Sp = make_float2(0.f, 0.f), Sr = Sp, Qp[3] = {Sp, Sp, Sp}, Qr[3] = {Sp, Sp, Sp};  // Q: sum g c (-q)
+            const float2 z2 = make_float2(0.f, 0.f);
+            float2 Vp[3] = {z2, z2, z2}, Vr[3] = {z2, z2, z2};  // sum g c_p a, sum g c_r b
+            uint32_t near = 0;  // sign bit: a query near the segment (t < kNearCos |a.b|)
 #pragma unroll 2
             for (int i = c0; i < c1; i += 2) {
                 const float4 u = win[i], v = win[i + 1];
@@ -197,44 +211,45 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_list_kernel(const BndArgs 
                 const float2 ib = make_float2(rsqrt_approx(lb2.x), rsqrt_approx(lb2.y));
                 const float2 ab = __ffma2_rn(az, bz, __ffma2_rn(ay, by, __fmul2_rn(ax, bx)));
                 const float2 De = __ffma2_rn(__fmul2_rn(la2, ia), __fmul2_rn(lb2, ib), ab);
+                const float2 chk = __ffma2_rn(kn, ab, De);
+                near |= __float_as_uint(chk.x) | __float_as_uint(chk.y);
                 const float2 gr = __fmul2_rn(make_float2(u.w, v.w), make_float2(rcp_approx(De.x), rcp_approx(De.y)));
                 const float2 cp = __fmul2_rn(gr, ia), cr = __fmul2_rn(gr, ib);
-                Sp = __fadd2_rn(Sp, cp);
-                Sr = __fadd2_rn(Sr, cr);
-                Qp[0] = __ffma2_rn(cp, nx2, Qp[0]);
-                Qp[1] = __ffma2_rn(cp, ny2, Qp[1]);
-                Qp[2] = __ffma2_rn(cp, nz2, Qp[2]);
-                Qr[0] = __ffma2_rn(cr, nx2, Qr[0]);
-                Qr[1] = __ffma2_rn(cr, ny2, Qr[1]);
-                Qr[2] = __ffma2_rn(cr, nz2, Qr[2]);
+                Vp[0] = __ffma2_rn(cp, ax, Vp[0]);
+                Vp[1] = __ffma2_rn(cp, ay, Vp[1]);
+                Vp[2] = __ffma2_rn(cp, az, Vp[2]);
+                Vr[0] = __ffma2_rn(cr, bx, Vr[0]);
+                Vr[1] = __ffma2_rn(cr, by, Vr[1]);
+                Vr[2] = __ffma2_rn(cr, bz, Vr[2]);
             }
-            float v[kBndSlots] = {Sp.x + Sp.y,       Sr.x + Sr.y,       -(Qp[0].x + Qp[0].y), -(Qp[1].x + Qp[1].y),
-                                  -(Qp[2].x + Qp[2].y), -(Qr[0].x + Qr[0].y), -(Qr[1].x + Qr[1].y), -(Qr[2].x + Qr[2].y)};
+            float v[kBndSlots] = {Vp[0].x + Vp[0].y, Vp[1].x + Vp[1].y, Vp[2].x + Vp[2].y,
+                                  Vr[0].x + Vr[0].y, Vr[1].x + Vr[1].y, Vr[2].x + Vr[2].y};
             float t = 0.f;
 #pragma unroll
             for (int k = 0; k < kBndSlots; ++k) t += v[k];
-            if (!isfinite(t)) {
-                // a query on an endpoint or on the edge segment: skip those pairs
+            if ((near >> 31) || !isfinite(t)) {
+                // a query near the segment (guarded t), or on an endpoint or on the segment (those
+                // pairs are skipped)
 #pragma unroll
                 for (int k = 0; k < kBndSlots; ++k) v[k] = 0.f;
                 const int ce = c1 < len ? c1 : len;
                 for (int i = c0; i < ce; ++i) {
                     const float4 q = win[i];
-                    float cpq = 0.f, crq = 0.f;
-                    bnd_pair_guarded(R.p.x + q.x, R.p.y + q.y, R.p.z + q.z, R.r.x + q.x, R.r.y + q.y, R.r.z + q.z,
-                                     q.w, v[0], v[1], cpq, crq);
-                    v[2] = fmaf(cpq, -q.x, v[2]);
-                    v[3] = fmaf(cpq, -q.y, v[3]);
-                    v[4] = fmaf(cpq, -q.z, v[4]);
-                    v[5] = fmaf(crq, -q.x, v[5]);
-                    v[6] = fmaf(crq, -q.y, v[6]);
-                    v[7] = fmaf(crq, -q.z, v[7]);
+                    const float ax = R.p.x + q.x, ay = R.p.y + q.y, az = R.p.z + q.z;
+                    const float bx = R.r.x + q.x, by = R.r.y + q.y, bz = R.r.z + q.z;
+                    float sp = 0.f, sr = 0.f, cpq = 0.f, crq = 0.f;
+                    bnd_pair_guarded(ax, ay, az, bx, by, bz, dx, dy, dz, q.w, sp, sr, cpq, crq);
+                    v[0] = fmaf(cpq, ax, v[0]);
+                    v[1] = fmaf(cpq, ay, v[1]);
+                    v[2] = fmaf(cpq, az, v[2]);
+                    v[3] = fmaf(crq, bx, v[3]);
+                    v[4] = fmaf(crq, by, v[4]);
+                    v[5] = fmaf(crq, bz, v[5]);
                 }
             }
-            // slots: S_p, S_r, Q_p (x, y, z), Q_r (x, y, z)
-            const float sl[kBndSlots] = {v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7]};
+            // slots: V_p (x, y, z), V_r (x, y, z)
 #pragma unroll
-            for (int k = 0; k < kBndSlots; ++k) kahan_slot(&ks[k][threadIdx.x], sl[k]);
+            for (int k = 0; k < kBndSlots; ++k) kahan_slot(&ks[k][threadIdx.x], v[k]);
         }
     }
     if (e >= a.nb) return;
@@ -244,7 +259,7 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_list_kernel(const BndArgs 
 }
 
 // dverts[v] = sum over the boundary endpoints at v (CSR, fixed order) of
-//   m/(4 pi) [(r x p) S - e x Q]   (S, Q of that endpoint, summed over the splits in FP64).
+//   m/(4 pi) d x V   (V of that endpoint, summed over the splits in FP64; d = r - p).
 __global__ void bnd_gather_kernel(int64_t nv, const BndRec *__restrict__ rec, int64_t nb,
                                   const float *__restrict__ part, int nsplit, const int32_t *__restrict__ vptr,
                                   const int32_t *__restrict__ vend, float *__restrict__ dverts) {
@@ -257,18 +272,16 @@ __global__ void bnd_gather_kernel(int64_t nv, const BndRec *__restrict__ rec, in
             const int end = code & 1;  // 0: v is p (the edge's start), 1: v is r
             const BndRec b = rec[e];
             const double m = (double)b.p.w;
-            double S = 0.0, Q[3] = {0.0, 0.0, 0.0};
+            double V[3] = {0.0, 0.0, 0.0};
             for (int s = 0; s < nsplit; ++s) {
                 const float *pp = part + ((int64_t)s * nb + e) * kBndSlots;
-                S += (double)pp[end];
-                for (int k = 0; k < 3; ++k) Q[k] += (double)pp[2 + 3 * end + k];
+                for (int k = 0; k < 3; ++k) V[k] += (double)pp[3 * end + k];
             }
-            const double p[3] = {b.p.x, b.p.y, b.p.z};
-            const double r[3] = {b.r.x, b.r.y, b.r.z};
-            const double ed[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
-            const double rxp[3] = {r[1] * p[2] - r[2] * p[1], r[2] * p[0] - r[0] * p[2], r[0] * p[1] - r[1] * p[0]};
-            const double exq[3] = {ed[1] * Q[2] - ed[2] * Q[1], ed[2] * Q[0] - ed[0] * Q[2], ed[0] * Q[1] - ed[1] * Q[0]};
-            for (int k = 0; k < 3; ++k) G[k] += m * (rxp[k] * S - exq[k]);
+            const double ed[3] = {(double)b.r.x - (double)b.p.x, (double)b.r.y - (double)b.p.y,
+                                  (double)b.r.z - (double)b.p.z};
+            G[0] += m * (ed[1] * V[2] - ed[2] * V[1]);
+            G[1] += m * (ed[2] * V[0] - ed[0] * V[2]);
+            G[2] += m * (ed[0] * V[1] - ed[1] * V[0]);
         }
         for (int k = 0; k < 3; ++k) dverts[3 * v + k] = (float)(k4 * G[k]);
     }

@@ -1,36 +1,24 @@
-// Adjoint of the winding number: dL/dV = sum_q g_q dw(q)/dV, every (query, face) pair.
+// Adjoint of the winding number: dL/dV = sum_q g_q dw(q)/dV over every (query, face) pair, with
+// w = (1/4pi) sum_f Omega_f (Eq. (5)) and Omega_f the solid angle of Eq. (7).
 //
-// Two exact formulations of the per-face derivative of Eq. (7), w = (1/4pi) sum Omega:
-//
-// Grid queries (bwd_grid_kernel) -- from each face's edges. The solid angle of a triangle depends
-// only on its boundary, so for an edge p -> r of the face (a = p - q, b = r - q)
-//   dOmega/dp += (b x a) / (|a| (|a||b| + a.b)),   dOmega/dr += (b x a) / (|b| (|a||b| + a.b)).
-// A thread owns two faces that share an edge (consecutive faces of a strip, paired on the host);
-// their shared edge's terms cancel, leaving the quad's four edges: per query four distances, four
-// dots and four reciprocals serve both faces, and every edge keeps four packed row sums (details at
-// bwd_grid_pairs_edges). Faces left unpaired run alone (three edges).
-//
-// Query lists (bwd_list_kernel) -- the chain rule through N and D. With a = v0 - q, b = v1 - q,
-// c = v2 - q, N = a.n (n = (v1-v0)x(v2-v0)), D as in the forward and Omega = 2 ATAN2(N, D):
-//   dw = (1/2pi) (D dN - N dD) / (N^2 + D^2)
-//   dN/da = b x c,  dN/db = c x a,  dN/dc = a x b
-//   dD/da = (a/|a|)(|b||c| + b.c) + b|c| + c|b|   (and cyclically)
-// Writing b = e1 + a, c = e2 + a (e1 = v1 - v0, e2 = v2 - v0), every per-query vector term is
-// (scalar) x a or a constant vector, so per face only these sums are needed:
-//   T_cD = sum cD, T_P = sum cN|a|, T_Q = sum cN|b|, T_R = sum cN|c|,
-//   T_ab = sum alpha_b, T_ac = sum alpha_c,
-//   U_cD = sum cD a, U_a = sum W_a a, U_b = sum W_b a, U_c = sum W_c a,
-// with cD = g D/(N^2+D^2), cN = g N/(N^2+D^2), alpha_a = cN (|b||c| + b.c)/|a| (cyclic),
-// W_a = alpha_a + T_R-term + T_Q-term etc. Then
-//   dL/dv0 = k [T_cD n + (e1 - e2) x U_cD - T_R e1 - T_Q e2 - U_a]
-//   dL/dv1 = k [e2 x U_cD - T_ab e1 - T_P e2 - U_b]
-//   dL/dv2 = k [-e1 x U_cD - T_P e1 - T_ac e2 - U_c],   k = 1/(2 pi).
-// Edge-sharing face pairs share the four distances and five edge dots here too.
-//
-// Both kernels are face-parallel: a thread owns its faces, streams the queries (uniform across the
-// warp) through shared memory, keeps per-face (per-edge) sums in FP32 with Kahan compensation in
-// shared memory, and writes per-split face gradients that the gather kernel (pack.cu) sums over
-// splits and incident faces in FP64, in a fixed order.
+// The solid angle of a triangle depends only on its boundary, so the derivative of Omega_f with
+// respect to the face's vertices is a sum over its three directed edges: for an edge p -> r of the
+// face, with a = p - q and b = r - q,
+//   dOmega/dp += (b x a) / (|a| (|a||b| + a.b)),   dOmega/dr += (b x a) / (|b| (|a||b| + a.b)),
+// which is the chain rule through Eq. (7) rearranged (q off the face). No arctangent is needed.
+// The kernels are face-parallel: a thread owns two faces that share an edge (consecutive faces of
+// a strip, paired on the host) or one face left unpaired, streams the queries (uniform across the
+// warp) through shared memory, and for the pair evaluates the quad's four edges (the shared edge's
+// terms from the two faces cancel; details at bwd_grid_pairs_edges). Per-edge sums are FP32 with
+// Kahan compensation in shared memory; per-split face gradients are summed over splits and
+// incident faces in FP64 by the gather kernel (pack.cu), in a fixed order.
+// With d = r - p, b x a = d x a = d x b, so each edge keeps only the sums of g c times the
+// endpoint's offset from q, V_p = sum g c_p a and V_r = sum g c_r b, and forms d x V in FP64.
+//   * Grid queries (bwd_grid_kernel): the y, z parts of a, b are constant along a row, so each edge
+//     keeps two packed row sums per endpoint (g c and g c a_x).
+//   * Query lists (bwd_list_kernel): three packed sums per endpoint (the components of V).
+// Where q is near an edge segment, |a||b| + a.b cancels in FP32; rows (grid) or chunks (list) with
+// such queries take a guarded scalar path that forms it as |a x b|^2 / (|a||b| - a.b) (edge_t).
 #include <math.h>
 
 #include <atomic>
@@ -61,96 +49,10 @@ struct BwdArgs {
     int64_t pblocks;
 };
 
-struct FaceF {
-    float v0x, v0y, v0z, v1x, v1y, v1z, v2x, v2y, v2z, nx, ny, nz;
-};
-
-struct RowB {
-    float ay, az, La, Lb, Lc, Pab, Pbc, Pca, Nyz;
-};
-
-__device__ __forceinline__ RowB row_b(const FaceF &F, float qy, float qz) {
-    RowB r;
-    r.ay = F.v0y - qy;
-    r.az = F.v0z - qz;
-    const float by = F.v1y - qy, bz = F.v1z - qz, cy = F.v2y - qy, cz = F.v2z - qz;
-    r.La = fmaf(r.ay, r.ay, r.az * r.az);
-    r.Lb = fmaf(by, by, bz * bz);
-    r.Lc = fmaf(cy, cy, cz * cz);
-    r.Pab = fmaf(r.ay, by, r.az * bz);
-    r.Pbc = fmaf(by, cy, bz * cz);
-    r.Pca = fmaf(cy, r.ay, cz * r.az);
-    r.Nyz = fmaf(r.ay, F.ny, r.az * F.nz);
-    return r;
-}
-
-// One pair: accumulate the 7 row scalars S and their x-weighted versions X.
-template <bool GUARD>
-__device__ __forceinline__ void bwd_pair(const FaceF &F, const RowB &R, float qx, float g, float (&S)[7],
-                                         float (&X)[7]) {
-    const float ax = F.v0x - qx, bx = F.v1x - qx, cx = F.v2x - qx;
-    float la2 = fmaf(ax, ax, R.La), lb2 = fmaf(bx, bx, R.Lb), lc2 = fmaf(cx, cx, R.Lc);
-    if (GUARD) {
-        la2 = fmaxf(la2, 1e-30f);
-        lb2 = fmaxf(lb2, 1e-30f);
-        lc2 = fmaxf(lc2, 1e-30f);
-    }
-    const float ia = rsqrt_approx(la2), ib = rsqrt_approx(lb2), ic = rsqrt_approx(lc2);
-    const float la = la2 * ia, lb = lb2 * ib, lc = lc2 * ic;  // multiply, not a second MUFU op per vertex
-    const float ab = fmaf(ax, bx, R.Pab), bc = fmaf(bx, cx, R.Pbc), ca = fmaf(cx, ax, R.Pca);
-    const float N = fmaf(ax, F.nx, R.Nyz);
-    const float tc = fmaf(la, lb, ab);  // |a||b| + a.b, also the numerator of alpha_c
-    float D = tc * lc;
-    D = fmaf(la, bc, D);
-    D = fmaf(lb, ca, D);
-    const float den = fmaf(N, N, D * D);
-    float r = rcp_approx(den);
-    if (GUARD) r = den >= 1.17549435e-38f ? r : 0.0f;
-    const float gr = g * r;
-    const float cD = gr * D, cN = gr * N;
-    const float P = cN * la, Qb = cN * lb, Rc = cN * lc;
-    const float alA = cN * (fmaf(lb, lc, bc) * ia);
-    const float alB = cN * (fmaf(lc, la, ca) * ib);
-    const float alC = cN * (tc * ic);
-    S[0] += cD;
-    S[1] += P;
-    S[2] += Qb;
-    S[3] += Rc;
-    S[4] += alA;
-    S[5] += alB;
-    S[6] += alC;
-    X[0] = fmaf(cD, ax, X[0]);
-    X[1] = fmaf(P, ax, X[1]);
-    X[2] = fmaf(Qb, ax, X[2]);
-    X[3] = fmaf(Rc, ax, X[3]);
-    X[4] = fmaf(alA, ax, X[4]);
-    X[5] = fmaf(alB, ax, X[5]);
-    X[6] = fmaf(alC, ax, X[6]);
-}
-
 // Packed FP32x2 helpers (Blackwell FFMA2/FADD2/FMUL2 take two queries per instruction; the MUFU
 // reciprocal square roots and reciprocals stay scalar).
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 rsqrt2(float2 v) { return make_float2(rsqrt_approx(v.x), rsqrt_approx(v.y)); }
-
-// Face A (which = 0) or B (which = 1) of a pair as a face alone, in its canonical corner order.
-__device__ __forceinline__ FaceF pair_face(const PairRec &P, int which) {
-    FaceF F;
-    const float4 a = which ? P.r2 : P.r0, c = which ? P.r3 : P.r2;
-    F.v0x = a.x; F.v0y = a.y; F.v0z = a.z;
-    F.v1x = P.r1.x; F.v1y = P.r1.y; F.v1z = P.r1.z;
-    F.v2x = c.x; F.v2y = c.y; F.v2z = c.z;
-    F.nx = which ? P.r3.w : P.r0.w;
-    F.ny = which ? P.r4.x : P.r1.w;
-    F.nz = which ? P.r4.y : P.r2.w;
-    return F;
-}
-
-// Per-face sums, kept in shared memory (touched once per row or chunk of queries, so the
-// registers of the pair loop stay free): slot k of thread t is ks[k][t] = (sum, compensation),
-// k = 0..5 for T_cD, T_P, T_Q, T_R, T_ab, T_ac and 6 + 3i + j for U_i component j
-// (U_cD, U_a, U_b, U_c).
-constexpr int kFaceSlots = 18;
 
 __device__ __forceinline__ void kahan_sm(float2 *slot, float x) {
     float2 k = *slot;
@@ -161,72 +63,8 @@ __device__ __forceinline__ void kahan_sm(float2 *slot, float x) {
     *slot = k;
 }
 
-__device__ __forceinline__ void fold_sm(float2 (*ks)[kBwdThreads], const float (&S)[7], const float (&X)[7], float ay,
-                                        float az) {
-    const int t = threadIdx.x;
-    kahan_sm(&ks[0][t], S[0]);
-    kahan_sm(&ks[1][t], S[1]);
-    kahan_sm(&ks[2][t], S[2]);
-    kahan_sm(&ks[3][t], S[3]);
-    kahan_sm(&ks[4][t], S[5]);
-    kahan_sm(&ks[5][t], S[6]);
-    const float ws[4] = {S[0], S[4] + S[3] + S[2], S[5] + S[1] + S[3], S[6] + S[2] + S[1]};
-    const float wx[4] = {X[0], X[4] + X[3] + X[2], X[5] + X[1] + X[3], X[6] + X[2] + X[1]};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        kahan_sm(&ks[6 + 3 * i][t], wx[i]);
-        kahan_sm(&ks[7 + 3 * i][t], ay * ws[i]);
-        kahan_sm(&ks[8 + 3 * i][t], az * ws[i]);
-    }
-}
-
-__device__ __forceinline__ FaceF load_face(const FaceRec *rec, int64_t f) {
-    const FaceRec r = rec[f];
-    FaceF F;
-    F.v0x = r.r0.x; F.v0y = r.r0.y; F.v0z = r.r0.z;
-    F.v1x = r.r1.x; F.v1y = r.r1.y; F.v1z = r.r1.z;
-    F.v2x = r.r2.x; F.v2y = r.r2.y; F.v2z = r.r2.z;
-    F.nx = r.r0.w * (1.0f / kNormalScale);
-    F.ny = r.r1.w * (1.0f / kNormalScale);
-    F.nz = r.r2.w * (1.0f / kNormalScale);
-    return F;
-}
-
-// Combine the face sums (T, U as compensated FP64 values) into the 9 gradient components (FP64
-// arithmetic) and store them: corner c of F goes to the input corner (code >> 2c) & 3 of the face,
-// times sign (-1 when F is the face with its orientation reversed).
+// Corner codes: canonical corner j of a face goes to its input corner (code >> 2j) & 3.
 constexpr int kCornersIdentity = 0 | 1 << 2 | 2 << 4;
-
-__device__ __forceinline__ void write_face_grad_d(const FaceF &F, const double (&T)[6], const double (&U)[4][3],
-                                                  float *out, int code = kCornersIdentity, double sign = 1.0) {
-    const double e1[3] = {(double)F.v1x - F.v0x, (double)F.v1y - F.v0y, (double)F.v1z - F.v0z};
-    const double e2[3] = {(double)F.v2x - F.v0x, (double)F.v2y - F.v0y, (double)F.v2z - F.v0z};
-    const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    const double *u = U[0];
-    const double d[3] = {e1[0] - e2[0], e1[1] - e2[1], e1[2] - e2[2]};
-    const double dxu[3] = {d[1] * u[2] - d[2] * u[1], d[2] * u[0] - d[0] * u[2], d[0] * u[1] - d[1] * u[0]};
-    const double e2xu[3] = {e2[1] * u[2] - e2[2] * u[1], e2[2] * u[0] - e2[0] * u[2], e2[0] * u[1] - e2[1] * u[0]};
-    const double e1xu[3] = {e1[1] * u[2] - e1[2] * u[1], e1[2] * u[0] - e1[0] * u[2], e1[0] * u[1] - e1[1] * u[0]};
-    for (int k = 0; k < 3; ++k) {
-        const double g0 = T[0] * n[k] + dxu[k] - T[3] * e1[k] - T[2] * e2[k] - U[1][k];
-        const double g1 = e2xu[k] - T[4] * e1[k] - T[1] * e2[k] - U[2][k];
-        const double g2 = -e1xu[k] - T[1] * e1[k] - T[5] * e2[k] - U[3][k];
-        const double k2 = sign * kInv2PiD;
-        out[3 * (code & 3) + k] = (float)(g0 * k2);
-        out[3 * ((code >> 2) & 3) + k] = (float)(g1 * k2);
-        out[3 * ((code >> 4) & 3) + k] = (float)(g2 * k2);
-    }
-}
-
-__device__ __forceinline__ void write_face_grad_sm(const FaceF &F, float2 (*ks)[kBwdThreads], float *out,
-                                                   int code = kCornersIdentity, double sign = 1.0) {
-    const int t = threadIdx.x;
-    double T[6], U[4][3];
-    for (int i = 0; i < 6; ++i) T[i] = (double)ks[i][t].x - (double)ks[i][t].y;
-    for (int i = 0; i < 4; ++i)
-        for (int k = 0; k < 3; ++k) U[i][k] = (double)ks[6 + 3 * i + k][t].x - (double)ks[6 + 3 * i + k][t].y;
-    write_face_grad_d(F, T, U, out, code, sign);
-}
 
 // Staged queries of a window, in pairs: for query i (pair p = i/2, k = i%2) the window holds
 // -x_i at wf[4p + k] and the upstream g_i at wf[4p + 2 + k], so one 16-byte load gives the
@@ -286,15 +124,17 @@ __device__ __forceinline__ void for_each_row(const BwdArgs &a, float *wf, RowFn 
 // shared edge p1 -> p2 with multiplicity 1 - sB (0 unless B's input orientation is reversed).
 // Every (pair, query) is still evaluated; per one the four distances (one MUFU reciprocal square
 // root each) serve four edges, each one dot, |a||b| + a.b, one MUFU reciprocal and four sums.
-// Because b x a = r x p - (r - p) x q is linear in q, an edge needs only
-//   S_p = sum g c_p, Q_p = sum g c_p q, S_r, Q_r   (c_p = 1/(|a| (|a||b| + a.b)), c_r with |b|):
-// per grid row the packed sums of g c and g c (-x) for two x-adjacent queries at a time, folded
-// per row into Kahan sums in shared memory (y and z enter as qy S, qz S). At the end the thread
-// forms in FP64 dL/dp = m/(4 pi) [(r x p) S_p - (r - p) x Q_p] (r likewise) and writes each vertex's
+// With d = r - p, b x a = d x a = d x b, so the term at either endpoint is its c times d x (its own
+// offset from q), and an edge needs only V_p = sum g c_p a and V_r = sum g c_r b
+// (c_p = 1/(|a| (|a||b| + a.b)), c_r with |b|): per grid row the packed sums of g c and g c a_x for
+// two x-adjacent queries at a time (a_y, a_z are constant along the row and enter as a_y S, a_z S),
+// folded per row into Kahan sums in shared memory (offsets from the endpoint, not absolute
+// coordinates, so the sums do not depend on where the mesh sits). At the end the thread forms in FP64
+// dL/dp = m/(4 pi) d x V_p, dL/dr = m/(4 pi) d x V_r and writes each vertex's
 // share into the gradient slots of the pair's faces (A's slot gets A's edges and the shared edge,
-// B's slot B's edges); the gather sums the slots per vertex, so only the per-vertex sum is that of
-// the face formula, not each slot.
-constexpr int kEdgeSlots = 8;  // per directed edge: S_p, Q_p (3), S_r, Q_r (3)
+// B's slot B's edges); the gather sums the slots per vertex, so the per-vertex sums are the
+// derivative, while a single slot is not that face's own derivative.
+constexpr int kEdgeSlots = 6;  // per directed edge: V_p (3), V_r (3)
 
 // Edge tables: pair (4 points, edges 0-3 the quad, 4 the shared edge) and single face (3 edges).
 template <int NP>
@@ -306,7 +146,8 @@ __device__ __forceinline__ constexpr int edge_end(int k) {
     return NP == 4 ? (k == 0 ? 1 : k == 1 ? 0 : k == 2 ? 3 : k == 3 ? 2 : 2) : (k == 0 ? 1 : k == 1 ? 2 : 0);
 }
 
-// Packed per-row sums of one directed edge: g c and g c (-x) at its start (p) and its end (r).
+// Packed per-row sums of one directed edge: g c and g c o_x (o = P - q, the endpoint's offset) at
+// its start (p) and its end (r).
 struct EdgeRow2 {
     float2 Sp, Xp, Sr, Xr;
 };
@@ -345,20 +186,22 @@ __device__ __forceinline__ void edges_row2(const EdgeRowConst<NP, NE> &C, const 
             const float2 c = __fmul2_rn(g, make_float2(rcp_approx(t.x), rcp_approx(t.y)));
             const float2 cp = __fmul2_rn(c, iv[s]), cr = __fmul2_rn(c, iv[e]);
             R[k].Sp = __fadd2_rn(R[k].Sp, cp);
-            R[k].Xp = __ffma2_rn(cp, nqx, R[k].Xp);
+            R[k].Xp = __ffma2_rn(cp, x[s], R[k].Xp);
             R[k].Sr = __fadd2_rn(R[k].Sr, cr);
-            R[k].Xr = __ffma2_rn(cr, nqx, R[k].Xr);
+            R[k].Xr = __ffma2_rn(cr, x[e], R[k].Xr);
         }
     }
 }
 
 // The guarded scalar path of one row (or piece) and one edge: rows with an odd number of queries,
-// pieces of long rows, and rows whose packed sums are not finite (a query at an endpoint or on the
-// edge segment, where the derivative does not exist: those pairs are skipped). Returns the row's
-// S_p, sum g c_p (-x), S_r, sum g c_r (-x).
+// pieces of long rows, rows that pass close to one of the thread's edges (t from edge_t), and rows
+// whose packed sums are not finite (a query at an endpoint or on the edge segment, where the
+// derivative does not exist: those pairs are skipped). Returns the row's S_p, sum g c_p a_x, S_r,
+// sum g c_r b_x.
 __device__ __noinline__ float4 edge_row_guarded(float px, float py, float pz, float rx, float ry, float rz, float qy,
                                                float qz, const float *wf, int64_t i0, int xlen) {
     const float ay = py - qy, az = pz - qz, by = ry - qy, bz = rz - qz;
+    const float dx = rx - px, dy = ry - py, dz = rz - pz;
     float sp = 0.f, sr = 0.f, xp = 0.f, xr = 0.f;
     for (int ix = 0; ix < xlen; ++ix) {
         const float nqx = win_nqx(wf, i0 + ix), g = win_g(wf, i0 + ix);
@@ -366,34 +209,33 @@ __device__ __noinline__ float4 edge_row_guarded(float px, float py, float pz, fl
         const float la2 = fmaf(ax, ax, fmaf(ay, ay, az * az)), lb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
         if (!(la2 > 0.f) || !(lb2 > 0.f)) continue;
         const float la = sqrtf(la2), lb = sqrtf(lb2);
-        const float t = fmaf(la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)));
+        const float t = edge_t(ax, ay, az, la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)), dx, dy, dz);
         if (!(t > 1e-30f * la * lb)) continue;
         const float c = g / t, cp = c / la, cr = c / lb;
         sp += cp;
         sr += cr;
-        xp = fmaf(cp, nqx, xp);
-        xr = fmaf(cr, nqx, xr);
+        xp = fmaf(cp, ax, xp);
+        xr = fmaf(cr, bx, xr);
     }
     return make_float4(sp, xp, sr, xr);
 }
 
-// Fold one edge's row sums into its 8 Kahan slots: S_p, Q_p = (sum g c_p x, qy S_p, qz S_p), S_r, Q_r.
-__device__ __forceinline__ void fold_edge(float2 (*ks)[kBwdThreads], int edge, float sp, float nxp, float sr,
-                                          float nxr, float qy, float qz) {
+// Fold one edge's row sums into its 6 Kahan slots V_p = sum g c_p a and V_r = sum g c_r b, whose y
+// and z parts are the row's constant offsets times S: (sum g c_p a_x, a_y S_p, a_z S_p), ...
+__device__ __forceinline__ void fold_edge(float2 (*ks)[kBwdThreads], int edge, float sp, float xp, float sr, float xr,
+                                          float ay, float az, float by, float bz) {
     const int t = threadIdx.x;
     float2 (*k)[kBwdThreads] = ks + kEdgeSlots * edge;
-    kahan_sm(&k[0][t], sp);
-    kahan_sm(&k[1][t], -nxp);
-    kahan_sm(&k[2][t], qy * sp);
-    kahan_sm(&k[3][t], qz * sp);
-    kahan_sm(&k[4][t], sr);
-    kahan_sm(&k[5][t], -nxr);
-    kahan_sm(&k[6][t], qy * sr);
-    kahan_sm(&k[7][t], qz * sr);
+    kahan_sm(&k[0][t], xp);
+    kahan_sm(&k[1][t], ay * sp);
+    kahan_sm(&k[2][t], az * sp);
+    kahan_sm(&k[3][t], xr);
+    kahan_sm(&k[4][t], by * sr);
+    kahan_sm(&k[5][t], bz * sr);
 }
 
-// m/(4 pi) [(r x p) S - (r - p) x Q] for both endpoints of edge `edge` (FP64, from its Kahan slots),
-// added to gp (the start p) and gr (the end r).
+// m/(4 pi) (r - p) x V for both endpoints of edge `edge` (FP64, from its Kahan slots): with
+// d = r - p, b x a = d x a = d x b, so the start gets d x V_p and the end d x V_r.
 __device__ __forceinline__ void edge_grad(float2 (*ks)[kBwdThreads], int edge, const double (&p)[3],
                                           const double (&r)[3], double m, double (&gp)[3], double (&gr)[3]) {
     const int t = threadIdx.x;
@@ -403,15 +245,13 @@ __device__ __forceinline__ void edge_grad(float2 (*ks)[kBwdThreads], int edge, c
     for (int i = 0; i < kEdgeSlots; ++i) v[i] = (double)k[i][t].x - (double)k[i][t].y;
     const double w = m * (0.5 * kInv2PiD);
     const double d[3] = {r[0] - p[0], r[1] - p[1], r[2] - p[2]};
-    const double rxp[3] = {r[1] * p[2] - r[2] * p[1], r[2] * p[0] - r[0] * p[2], r[0] * p[1] - r[1] * p[0]};
-    const double *Qp = v + 1, *Qr = v + 5;
-    const double dxp[3] = {d[1] * Qp[2] - d[2] * Qp[1], d[2] * Qp[0] - d[0] * Qp[2], d[0] * Qp[1] - d[1] * Qp[0]};
-    const double dxr[3] = {d[1] * Qr[2] - d[2] * Qr[1], d[2] * Qr[0] - d[0] * Qr[2], d[0] * Qr[1] - d[1] * Qr[0]};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        gp[c] += w * (rxp[c] * v[0] - dxp[c]);
-        gr[c] += w * (rxp[c] * v[4] - dxr[c]);
-    }
+    const double *Vp = v, *Vr = v + 3;
+    gp[0] += w * (d[1] * Vp[2] - d[2] * Vp[1]);
+    gp[1] += w * (d[2] * Vp[0] - d[0] * Vp[2]);
+    gp[2] += w * (d[0] * Vp[1] - d[1] * Vp[0]);
+    gr[0] += w * (d[1] * Vr[2] - d[2] * Vr[1]);
+    gr[1] += w * (d[2] * Vr[0] - d[0] * Vr[2]);
+    gr[2] += w * (d[0] * Vr[1] - d[1] * Vr[0]);
 }
 
 // Every row of the CTA's split for the NP points and NE edges of this thread: packed rows, the
@@ -428,8 +268,15 @@ __device__ __forceinline__ void edges_all_rows(const BwdArgs &a, float *wf, floa
             y[k] = Y[k] - qy;
             z[k] = Z[k] - qz;
         }
+        bool near = false;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const int s = edge_start<NP>(k), e = edge_end<NP>(k);
+            const float dx = X[e] - X[s], dy = Y[e] - Y[s], dz = Z[e] - Z[s];
+            near |= row_near_edge(y[s], z[s], y[e], z[e], fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
         bool ok = false;
-        if (packed) {
+        if (packed && !near) {
             EdgeRowConst<NP, NE> C;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
@@ -449,22 +296,35 @@ __device__ __forceinline__ void edges_all_rows(const BwdArgs &a, float *wf, floa
                 t += ((R[k].Sp.x + R[k].Sp.y) + (R[k].Xp.x + R[k].Xp.y)) + ((R[k].Sr.x + R[k].Sr.y) + (R[k].Xr.x + R[k].Xr.y));
             ok = isfinite(t);
             if (ok) {
+                // the row offsets again, from an opaque copy of (qy, qz): the compiler would
+                // otherwise keep all 2 NP of them live through the packed loop
+                float qy2 = qy, qz2 = qz;
+                asm volatile("" : "+f"(qy2), "+f"(qz2));
 #pragma unroll
-                for (int k = 0; k < NE; ++k)
+                for (int k = 0; k < NE; ++k) {
+                    const int s = edge_start<NP>(k), e = edge_end<NP>(k);
                     fold_edge(ks, k, R[k].Sp.x + R[k].Sp.y, R[k].Xp.x + R[k].Xp.y, R[k].Sr.x + R[k].Sr.y,
-                              R[k].Xr.x + R[k].Xr.y, qy, qz);
+                              R[k].Xr.x + R[k].Xr.y, Y[s] - qy2, Z[s] - qz2, Y[e] - qy2, Z[e] - qz2);
+                }
             }
         }
         if (!ok) {
+            float qy2 = qy, qz2 = qz;
+            asm volatile("" : "+f"(qy2), "+f"(qz2));
 #pragma unroll
             for (int k = 0; k < NE; ++k) {
                 const int s = edge_start<NP>(k), e = edge_end<NP>(k);
-                const float4 v = edge_row_guarded(X[s], Y[s], Z[s], X[e], Y[e], Z[e], qy, qz, wf, i0, xlen);
-                fold_edge(ks, k, v.x, v.y, v.z, v.w, qy, qz);
+                const float4 v = edge_row_guarded(X[s], Y[s], Z[s], X[e], Y[e], Z[e], qy2, qz2, wf, i0, xlen);
+                fold_edge(ks, k, v.x, v.y, v.z, v.w, Y[s] - qy2, Z[s] - qz2, Y[e] - qy2, Z[e] - qz2);
             }
         }
     });
 }
+
+__device__ __forceinline__ void write_pair_edges(const BwdArgs &a, float2 (*ks)[kBwdThreads], const PairRec &P,
+                                                 const int32_t *tp, bool five);
+__device__ __forceinline__ void write_single_edges(const BwdArgs &a, float2 (*ks)[kBwdThreads], const FaceRec &r,
+                                                   int64_t f);
 
 // A CTA of edge-sharing face pairs, edge form: thread t owns pair t. When a pair of the warp has
 // B reversed, the warp also evaluates the shared edge (multiplicity 1 - sB: 2 for that pair, 0 for
@@ -484,7 +344,15 @@ __device__ __forceinline__ void bwd_grid_pairs_edges(const BwdArgs &a, float *wf
         edges_all_rows<4, 5>(a, wf, ks, X, Y, Z);
     else
         edges_all_rows<4, 4>(a, wf, ks, X, Y, Z);
-    if (idx >= a.np) return;
+    if (idx < a.np) write_pair_edges(a, ks, P, tp, five);
+}
+
+// The gradient of a pair (edge form) from its edges' Kahan slots, FP64, into the slots of its
+// two faces in face_grad (split blockIdx.y).
+__device__ __forceinline__ void write_pair_edges(const BwdArgs &a, float2 (*ks)[kBwdThreads], const PairRec &P,
+                                                 const int32_t *tp, bool five) {
+    const int code = tp[6];
+    const bool rev = (code >> 12) & 1;
     const double p[4][3] = {{P.r0.x, P.r0.y, P.r0.z}, {P.r1.x, P.r1.y, P.r1.z},
                             {P.r2.x, P.r2.y, P.r2.z}, {P.r3.x, P.r3.y, P.r3.z}};
     const double sB = rev ? -1.0 : 1.0;
@@ -523,7 +391,12 @@ __device__ __forceinline__ void bwd_grid_singles_edges(const BwdArgs &a, float *
     const FaceRec r = a.rec[f];
     const float X[3] = {r.r0.x, r.r1.x, r.r2.x}, Y[3] = {r.r0.y, r.r1.y, r.r2.y}, Z[3] = {r.r0.z, r.r1.z, r.r2.z};
     edges_all_rows<3, 3>(a, wf, ks, X, Y, Z);
-    if (idx >= count || !DV_INB(f, a.nf, kSiteBwdFaceGrad)) return;
+    if (idx < count && DV_INB(f, a.nf, kSiteBwdFaceGrad)) write_single_edges(a, ks, r, f);
+}
+
+// The gradient of a single face (edge form) from its edges' Kahan slots, FP64, into its slot.
+__device__ __forceinline__ void write_single_edges(const BwdArgs &a, float2 (*ks)[kBwdThreads], const FaceRec &r,
+                                                   int64_t f) {
     const double p[3][3] = {{r.r0.x, r.r0.y, r.r0.z}, {r.r1.x, r.r1.y, r.r1.z}, {r.r2.x, r.r2.y, r.r2.z}};
     double g[3][3] = {};
     edge_grad(ks, 0, p[0], p[1], 1.0, g[0], g[1]);
@@ -537,7 +410,7 @@ __device__ __forceinline__ void bwd_grid_singles_edges(const BwdArgs &a, float *
 }
 
 // Grid adjoint (edge form): CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces.
-// Dynamic shared memory: the query window, then 5 edges x 8 Kahan slots per thread.
+// Dynamic shared memory: the query window, then 5 edges x 6 Kahan slots per thread.
 constexpr size_t kBwdGridSmem = sizeof(float) * 2 * kBwdWin + sizeof(float2) * 5 * kEdgeSlots * kBwdThreads;
 
 __global__ void __launch_bounds__(kBwdThreads, 3) bwd_grid_kernel(const BwdArgs a) {
@@ -550,124 +423,12 @@ __global__ void __launch_bounds__(kBwdThreads, 3) bwd_grid_kernel(const BwdArgs 
         bwd_grid_singles_edges(a, wf, ks);
 }
 
-// List path: arbitrary queries, so no row sharing. Two queries per packed FP32x2 instruction;
-// per pair of queries the adjoint terms go straight into the 6 T sums and the 4 a-weighted
-// combinations U_i = sum W_i a (12 FMAs), plain FP32 over chunks of kListChunk queries, folded
-// per chunk into the Kahan face sums (shared memory). A chunk whose sums are not finite (a query
-// on a vertex or an edge line) is recomputed by the guarded scalar path.
+// Query lists: queries staged in windows, taken in chunks of kListChunk (plain FP32 sums within a
+// chunk, Kahan across chunks).
 constexpr int kListChunk = 128;
-
-struct FaceL2 {
-    float2 v0x, v0y, v0z, v1x, v1y, v1z, v2x, v2y, v2z, nx, ny, nz;
-};
-
-// The list-path adjoint terms of one face for two queries, from the distances, their reciprocals,
-// the edge dots, N and the offsets (ax, ay, az) of the face's first vertex.
-__device__ __forceinline__ void list_face2(float2 la, float2 lb, float2 lc, float2 ia, float2 ib, float2 ic,
-                                           float2 ab, float2 bcd, float2 ca, float2 N, float2 ax, float2 ay,
-                                           float2 az, float2 g, float2 (&T)[6], float2 (&U)[4][3]) {
-    // |a||b| + a.b written lb * la, so that for the two faces of a pair the shared edge's term
-    // (the other face's lb * lc + b.c) is the same expression, computed once
-    const float2 tc = __ffma2_rn(lb, la, ab);
-    float2 D = __fmul2_rn(tc, lc);
-    D = __ffma2_rn(la, bcd, D);
-    D = __ffma2_rn(lb, ca, D);
-    const float2 den = __ffma2_rn(N, N, __fmul2_rn(D, D));
-    const float2 gr = __fmul2_rn(g, make_float2(rcp_approx(den.x), rcp_approx(den.y)));
-    const float2 cD = __fmul2_rn(gr, D), cN = __fmul2_rn(gr, N);
-    const float2 kA = __fmul2_rn(__ffma2_rn(lb, lc, bcd), ia);
-    const float2 kB = __fmul2_rn(__ffma2_rn(lc, la, ca), ib);
-    const float2 kC = __fmul2_rn(tc, ic);
-    T[0] = __fadd2_rn(T[0], cD);
-    T[1] = __ffma2_rn(cN, la, T[1]);
-    T[2] = __ffma2_rn(cN, lb, T[2]);
-    T[3] = __ffma2_rn(cN, lc, T[3]);
-    T[4] = __ffma2_rn(cN, kB, T[4]);
-    T[5] = __ffma2_rn(cN, kC, T[5]);
-    // W_a = alpha_a + cN |c| + cN |b| = cN (k_a + |b| + |c|), cyclically
-    const float2 W[4] = {cD, __fmul2_rn(cN, __fadd2_rn(kA, __fadd2_rn(lc, lb))),
-                         __fmul2_rn(cN, __fadd2_rn(kB, __fadd2_rn(la, lc))),
-                         __fmul2_rn(cN, __fadd2_rn(kC, __fadd2_rn(lb, la)))};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        U[i][0] = __ffma2_rn(W[i], ax, U[i][0]);
-        U[i][1] = __ffma2_rn(W[i], ay, U[i][1]);
-        U[i][2] = __ffma2_rn(W[i], az, U[i][2]);
-    }
-}
-
-__device__ __forceinline__ void bwd_list_pair2(const FaceL2 &F, float4 q0, float4 q1, float2 (&T)[6],
-                                               float2 (&U)[4][3]) {
-    // window entries of a pair of queries: (-x0, -x1, -y0, -y1), (-z0, -z1, g0, g1)
-    const float2 nqx = make_float2(q0.x, q0.y), nqy = make_float2(q0.z, q0.w), nqz = make_float2(q1.x, q1.y);
-    const float2 g = make_float2(q1.z, q1.w);
-    const float2 ax = __fadd2_rn(F.v0x, nqx), ay = __fadd2_rn(F.v0y, nqy), az = __fadd2_rn(F.v0z, nqz);
-    const float2 bx = __fadd2_rn(F.v1x, nqx), by = __fadd2_rn(F.v1y, nqy), bz = __fadd2_rn(F.v1z, nqz);
-    const float2 cx = __fadd2_rn(F.v2x, nqx), cy = __fadd2_rn(F.v2y, nqy), cz = __fadd2_rn(F.v2z, nqz);
-    const float2 la2 = __ffma2_rn(az, az, __ffma2_rn(ay, ay, __fmul2_rn(ax, ax)));
-    const float2 lb2 = __ffma2_rn(bz, bz, __ffma2_rn(by, by, __fmul2_rn(bx, bx)));
-    const float2 lc2 = __ffma2_rn(cz, cz, __ffma2_rn(cy, cy, __fmul2_rn(cx, cx)));
-    const float2 ia = rsqrt2(la2), ib = rsqrt2(lb2), ic = rsqrt2(lc2);
-    const float2 la = __fmul2_rn(la2, ia), lb = __fmul2_rn(lb2, ib), lc = __fmul2_rn(lc2, ic);
-    const float2 ab = __ffma2_rn(az, bz, __ffma2_rn(ay, by, __fmul2_rn(ax, bx)));
-    const float2 bcd = __ffma2_rn(bz, cz, __ffma2_rn(by, cy, __fmul2_rn(bx, cx)));
-    const float2 ca = __ffma2_rn(cz, az, __ffma2_rn(cy, ay, __fmul2_rn(cx, ax)));
-    const float2 N = __ffma2_rn(az, F.nz, __ffma2_rn(ay, F.ny, __fmul2_rn(ax, F.nx)));
-    list_face2(la, lb, lc, ia, ib, ic, ab, bcd, ca, N, ax, ay, az, g, T, U);
-}
-
-// Two edge-sharing faces (A = (p0, p1, p2), B = (p2, p1, p3)) against two queries: four distances
-// and five dots for both faces.
-struct PairL2 {
-    float2 x[4], y[4], z[4];
-    float2 nA[3], nB[3];
-};
-
-__device__ __forceinline__ PairL2 pair_l2(const PairRec &P) {
-    PairL2 Q;
-    const float4 r[4] = {P.r0, P.r1, P.r2, P.r3};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        Q.x[i] = bc2(r[i].x);
-        Q.y[i] = bc2(r[i].y);
-        Q.z[i] = bc2(r[i].z);
-    }
-    Q.nA[0] = bc2(P.r0.w);
-    Q.nA[1] = bc2(P.r1.w);
-    Q.nA[2] = bc2(P.r2.w);
-    Q.nB[0] = bc2(P.r3.w);
-    Q.nB[1] = bc2(P.r4.x);
-    Q.nB[2] = bc2(P.r4.y);
-    return Q;
-}
 
 __device__ __forceinline__ float2 dot2(float2 ax, float2 ay, float2 az, float2 bx, float2 by, float2 bz) {
     return __ffma2_rn(az, bz, __ffma2_rn(ay, by, __fmul2_rn(ax, bx)));
-}
-
-__device__ __forceinline__ void bwd_list_quad2(const PairL2 &P, float4 q0, float4 q1, float2 (&TA)[6],
-                                               float2 (&UA)[4][3], float2 (&TB)[6], float2 (&UB)[4][3]) {
-    const float2 nqx = make_float2(q0.x, q0.y), nqy = make_float2(q0.z, q0.w), nqz = make_float2(q1.x, q1.y);
-    const float2 g = make_float2(q1.z, q1.w);
-    float2 x[4], y[4], z[4], l[4], r[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        x[i] = __fadd2_rn(P.x[i], nqx);
-        y[i] = __fadd2_rn(P.y[i], nqy);
-        z[i] = __fadd2_rn(P.z[i], nqz);
-        const float2 m = dot2(x[i], y[i], z[i], x[i], y[i], z[i]);
-        r[i] = rsqrt2(m);
-        l[i] = __fmul2_rn(m, r[i]);
-    }
-    const float2 d01 = dot2(x[0], y[0], z[0], x[1], y[1], z[1]);
-    const float2 d12 = dot2(x[1], y[1], z[1], x[2], y[2], z[2]);
-    const float2 d20 = dot2(x[2], y[2], z[2], x[0], y[0], z[0]);
-    const float2 d13 = dot2(x[1], y[1], z[1], x[3], y[3], z[3]);
-    const float2 d32 = dot2(x[3], y[3], z[3], x[2], y[2], z[2]);
-    const float2 NA = dot2(x[0], y[0], z[0], P.nA[0], P.nA[1], P.nA[2]);
-    const float2 NB = dot2(x[2], y[2], z[2], P.nB[0], P.nB[1], P.nB[2]);
-    list_face2(l[0], l[1], l[2], r[0], r[1], r[2], d01, d12, d20, NA, x[0], y[0], z[0], g, TA, UA);
-    list_face2(l[2], l[1], l[3], r[2], r[1], r[3], d12, d13, d32, NB, x[2], y[2], z[2], g, TB, UB);
 }
 
 // Query i of a window laid out in pairs: (-x, -y, -z, g).
@@ -701,122 +462,211 @@ __device__ __forceinline__ void for_each_chunk(const BwdArgs &a, float4 *win, Ch
     }
 }
 
-__device__ __forceinline__ bool finite_tu(const float2 (&T)[6], const float2 (&U)[4][3]) {
-    float t = 0.f;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) t += T[k].x + T[k].y;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) t += U[i][0].x + U[i][0].y + U[i][1].x + U[i][1].y + U[i][2].x + U[i][2].y;
-    return isfinite(t);
-}
+// List adjoint from the faces' edges: the same edge terms as the grid path, with the full q of each
+// query (no row sharing). With d = r - p, b x a = d x a = d x b, so the term at either endpoint is
+// its c times d x (its own offset from q): per edge and endpoint only the vector sum V = sum c o of
+// the endpoint's offsets o = P - q is kept (3 packed sums), and d x V is formed at the end in FP64.
+// Per chunk the sums fold into 6 Kahan slots per edge.
 
-__device__ __forceinline__ void fold_list(float2 (*ks)[kBwdThreads], const float2 (&T)[6], const float2 (&U)[4][3]) {
-    const int th = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) kahan_sm(&ks[k][th], T[k].x + T[k].y);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) kahan_sm(&ks[6 + 3 * i + j][th], U[i][j].x + U[i][j].y);
-}
+struct EdgeList2 {
+    float2 Vp[3], Vr[3];
+};
 
-// Guarded scalar recompute of one chunk for one face, one query at a time (a chunk whose packed
-// sums are not finite: a query on a vertex or an edge line).
-__device__ __noinline__ void list_guarded(const FaceF F, const float4 *win, int c0, int ce,
-                                          float2 (*ks)[kBwdThreads]) {
-    for (int i = c0; i < ce; ++i) {
-        const float4 q = list_query(win, i);
-        const RowB R = row_b(F, -q.y, -q.z);
-        float S[7], X[7];
+// Returns the OR of the bit patterns of every t + kNearCos a.b: its sign bit is set when a query
+// of the chunk is near one of the edges (or a sum is NaN).
+template <int NP, int NE>
+__device__ __forceinline__ uint32_t edges_list_chunk(const float2 (&X)[NP], const float2 (&Y)[NP], const float2 (&Z)[NP],
+                                                     const float4 *win, int c0, int c1, EdgeList2 (&R)[NE]) {
+    uint32_t near = 0;
+    const float2 kn = bc2(kNearCos);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) S[k] = X[k] = 0.f;
-        bwd_pair<true>(F, R, -q.x, q.w, S, X);
-        fold_sm(ks, S, X, R.ay, R.az);
+    for (int k = 0; k < NE; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) R[k].Vp[c] = R[k].Vr[c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int i = c0; i < c1; i += 2) {
+        // window entries of a pair of queries: (-x0, -x1, -y0, -y1), (-z0, -z1, g0, g1)
+        const float4 q0 = win[i], q1 = win[i + 1];
+        const float2 nqx = make_float2(q0.x, q0.y), nqy = make_float2(q0.z, q0.w), nqz = make_float2(q1.x, q1.y);
+        const float2 g = make_float2(q1.z, q1.w);
+        float2 x[NP], y[NP], z[NP], l[NP], iv[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            x[k] = __fadd2_rn(X[k], nqx);
+            y[k] = __fadd2_rn(Y[k], nqy);
+            z[k] = __fadd2_rn(Z[k], nqz);
+            const float2 m = dot2(x[k], y[k], z[k], x[k], y[k], z[k]);
+            iv[k] = rsqrt2(m);
+            l[k] = __fmul2_rn(m, iv[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            const int s = edge_start<NP>(k), e = edge_end<NP>(k);
+            const float2 ab = dot2(x[s], y[s], z[s], x[e], y[e], z[e]);
+            const float2 t = __ffma2_rn(l[s], l[e], ab);  // |a||b| + a.b
+            const float2 chk = __ffma2_rn(kn, ab, t);
+            near |= __float_as_uint(chk.x) | __float_as_uint(chk.y);
+            const float2 c = __fmul2_rn(g, make_float2(rcp_approx(t.x), rcp_approx(t.y)));
+            const float2 cp = __fmul2_rn(c, iv[s]), cr = __fmul2_rn(c, iv[e]);
+            R[k].Vp[0] = __ffma2_rn(cp, x[s], R[k].Vp[0]);
+            R[k].Vp[1] = __ffma2_rn(cp, y[s], R[k].Vp[1]);
+            R[k].Vp[2] = __ffma2_rn(cp, z[s], R[k].Vp[2]);
+            R[k].Vr[0] = __ffma2_rn(cr, x[e], R[k].Vr[0]);
+            R[k].Vr[1] = __ffma2_rn(cr, y[e], R[k].Vr[1]);
+            R[k].Vr[2] = __ffma2_rn(cr, z[e], R[k].Vr[2]);
+        }
     }
+    return near;
 }
 
-__device__ __forceinline__ void bwd_list_singles(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads]) {
+struct Edge6 {
+    float v[kEdgeSlots];  // V_p (3), V_r (3)
+};
+
+// Guarded scalar recompute of one chunk for one edge (t from edge_t): chunks with a query near one
+// of the thread's edges or with sums that are not finite. Skips queries at an endpoint or on the
+// edge segment (no derivative there).
+__device__ __noinline__ Edge6 edge_chunk_guarded(float px, float py, float pz, float rx, float ry, float rz,
+                                                 const float4 *win, int c0, int ce) {
+    Edge6 o;
+#pragma unroll
+    for (int k = 0; k < kEdgeSlots; ++k) o.v[k] = 0.f;
+    const float dx = rx - px, dy = ry - py, dz = rz - pz;
+    for (int i = c0; i < ce; ++i) {
+        const float4 q = list_query(win, i);  // (-x, -y, -z, g)
+        const float ax = px + q.x, ay = py + q.y, az = pz + q.z, bx = rx + q.x, by = ry + q.y, bz = rz + q.z;
+        const float la2 = fmaf(ax, ax, fmaf(ay, ay, az * az)), lb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
+        if (!(la2 > 0.f) || !(lb2 > 0.f)) continue;
+        const float la = sqrtf(la2), lb = sqrtf(lb2);
+        const float t = edge_t(ax, ay, az, la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)), dx, dy, dz);
+        if (!(t > 1e-30f * la * lb)) continue;
+        const float c = q.w / t, cp = c / la, cr = c / lb;
+        o.v[0] = fmaf(cp, ax, o.v[0]);
+        o.v[1] = fmaf(cp, ay, o.v[1]);
+        o.v[2] = fmaf(cp, az, o.v[2]);
+        o.v[3] = fmaf(cr, bx, o.v[3]);
+        o.v[4] = fmaf(cr, by, o.v[4]);
+        o.v[5] = fmaf(cr, bz, o.v[5]);
+    }
+    return o;
+}
+
+// Every chunk of the CTA's split for this thread's NP points and NE edges, folded into the edges'
+// Kahan slots (the guarded path for chunks with a query near an edge or sums that are not finite).
+template <int NP, int NE>
+__device__ __forceinline__ void edges_list_all(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads],
+                                               const float (&X)[NP], const float (&Y)[NP], const float (&Z)[NP]) {
+#pragma unroll
+    for (int k = 0; k < kEdgeSlots * NE; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
+    float2 X2[NP], Y2[NP], Z2[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        X2[k] = bc2(X[k]);
+        Y2[k] = bc2(Y[k]);
+        Z2[k] = bc2(Z[k]);
+    }
+    for_each_chunk(a, win, [&](int c0, int c1, int len) {
+        EdgeList2 R[NE];
+        const uint32_t near = edges_list_chunk<NP, NE>(X2, Y2, Z2, win, c0, c1, R);
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < NE; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) t += (R[k].Vp[j].x + R[k].Vp[j].y) + (R[k].Vr[j].x + R[k].Vr[j].y);
+        const bool ok = isfinite(t) && !(near >> 31);
+        const int th = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            float v[kEdgeSlots];
+            if (ok) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    v[j] = R[k].Vp[j].x + R[k].Vp[j].y;
+                    v[3 + j] = R[k].Vr[j].x + R[k].Vr[j].y;
+                }
+            } else {
+                const int s = edge_start<NP>(k), e = edge_end<NP>(k);
+                const Edge6 gv = edge_chunk_guarded(X[s], Y[s], Z[s], X[e], Y[e], Z[e], win, c0, c1 < len ? c1 : len);
+#pragma unroll
+                for (int j = 0; j < kEdgeSlots; ++j) v[j] = gv.v[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kEdgeSlots; ++j) kahan_sm(&ks[kEdgeSlots * k + j][th], v[j]);
+        }
+    });
+}
+
+// Store the 3 x 3 gradient g (canonical corners) of a face into its slot, corner j at input corner
+// (code >> 2j) & 3.
+__device__ __forceinline__ void store_face_grad(float *o, const double (&g)[3][3], int code) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[3 * ((code >> (2 * j)) & 3) + c] = (float)g[j][c];
+}
+
+__device__ __forceinline__ void bwd_list_pairs_edges(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads]) {
+    const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    const int64_t ic = idx < a.np ? idx : a.np - 1;
+    const PairRec P = a.prec[DV_INB(ic, a.np, kSiteBwdRecord) ? ic : 0];
+    const int32_t *tp = a.ptopo + 8 * ic;
+    const int code = tp[6];
+    const bool rev = (code >> 12) & 1;
+    const float X[4] = {P.r0.x, P.r1.x, P.r2.x, P.r3.x};
+    const float Y[4] = {P.r0.y, P.r1.y, P.r2.y, P.r3.y};
+    const float Z[4] = {P.r0.z, P.r1.z, P.r2.z, P.r3.z};
+    const bool five = __syncthreads_or(rev) != 0;  // CTA-uniform: the chunk loop has barriers
+    if (five)
+        edges_list_all<4, 5>(a, win, ks, X, Y, Z);
+    else
+        edges_list_all<4, 4>(a, win, ks, X, Y, Z);
+    if (idx >= a.np) return;
+    const double p[4][3] = {{P.r0.x, P.r0.y, P.r0.z}, {P.r1.x, P.r1.y, P.r1.z},
+                            {P.r2.x, P.r2.y, P.r2.z}, {P.r3.x, P.r3.y, P.r3.z}};
+    const double sB = rev ? -1.0 : 1.0;
+    double gA[3][3] = {}, gB[3][3] = {};  // A: (p0, p1, p2), B: (p2, p1, p3)
+    edge_grad(ks, 0, p[0], p[1], 1.0, gA[0], gA[1]);
+    edge_grad(ks, 1, p[2], p[0], 1.0, gA[2], gA[0]);
+    edge_grad(ks, 2, p[1], p[3], sB, gB[1], gB[2]);
+    edge_grad(ks, 3, p[3], p[2], sB, gB[2], gB[0]);
+    if (five && rev) edge_grad(ks, 4, p[1], p[2], 1.0 - sB, gA[1], gA[2]);
+    float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
+    if (DV_INB(tp[4], a.nf, kSiteBwdFaceGrad)) store_face_grad(out + (int64_t)tp[4] * 9, gA, code & 63);
+    if (DV_INB(tp[5], a.nf, kSiteBwdFaceGrad)) store_face_grad(out + (int64_t)tp[5] * 9, gB, (code >> 6) & 63);
+}
+
+__device__ __forceinline__ void bwd_list_singles_edges(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads]) {
     const int64_t count = a.singles ? a.nsingle : a.nf;
     const int64_t idx = ((int64_t)blockIdx.x - a.pblocks) * kBwdThreads + threadIdx.x;
     const int64_t ic = idx < count ? idx : count - 1;
     int64_t f = a.singles ? (DV_INB(ic, a.nsingle, kSiteBwdRecord) ? (int64_t)a.singles[ic] : 0) : ic;
     if (!DV_INB(f, a.nf, kSiteBwdRecord)) f = 0;
-    const FaceF F = load_face(a.rec, f);
-    FaceL2 F2;
-    F2.v0x = bc2(F.v0x); F2.v0y = bc2(F.v0y); F2.v0z = bc2(F.v0z);
-    F2.v1x = bc2(F.v1x); F2.v1y = bc2(F.v1y); F2.v1z = bc2(F.v1z);
-    F2.v2x = bc2(F.v2x); F2.v2y = bc2(F.v2y); F2.v2z = bc2(F.v2z);
-    F2.nx = bc2(F.nx); F2.ny = bc2(F.ny); F2.nz = bc2(F.nz);
-#pragma unroll
-    for (int k = 0; k < kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
-    for_each_chunk(a, win, [&](int c0, int c1, int len) {
-        float2 T[6], U[4][3];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) T[k] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) U[i][0] = U[i][1] = U[i][2] = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int i = c0; i < c1; i += 2) bwd_list_pair2(F2, win[i], win[i + 1], T, U);  // i even: one pair
-        if (finite_tu(T, U))
-            fold_list(ks, T, U);
-        else
-            list_guarded(F, win, c0, c1 < len ? c1 : len, ks);
-    });
-    if (idx < count && DV_INB(f, a.nf, kSiteBwdFaceGrad))
-        write_face_grad_sm(F, ks, a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9);
+    const FaceRec r = a.rec[f];
+    const float X[3] = {r.r0.x, r.r1.x, r.r2.x}, Y[3] = {r.r0.y, r.r1.y, r.r2.y}, Z[3] = {r.r0.z, r.r1.z, r.r2.z};
+    edges_list_all<3, 3>(a, win, ks, X, Y, Z);
+    if (idx >= count || !DV_INB(f, a.nf, kSiteBwdFaceGrad)) return;
+    const double p[3][3] = {{r.r0.x, r.r0.y, r.r0.z}, {r.r1.x, r.r1.y, r.r1.z}, {r.r2.x, r.r2.y, r.r2.z}};
+    double g[3][3] = {};
+    edge_grad(ks, 0, p[0], p[1], 1.0, g[0], g[1]);
+    edge_grad(ks, 1, p[1], p[2], 1.0, g[1], g[2]);
+    edge_grad(ks, 2, p[2], p[0], 1.0, g[2], g[0]);
+    store_face_grad(a.face_grad + ((int64_t)blockIdx.y * a.nf + f) * 9, g, kCornersIdentity);
 }
 
-__device__ __forceinline__ void bwd_list_pairs(const BwdArgs &a, float4 *win, float2 (*ks)[kBwdThreads]) {
-    const int64_t idx = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    const int64_t ic = idx < a.np ? idx : a.np - 1;
-    const PairRec P = a.prec[DV_INB(ic, a.np, kSiteBwdRecord) ? ic : 0];
-    const PairL2 P2 = pair_l2(P);
-    float2(*ksB)[kBwdThreads] = ks + kFaceSlots;
-#pragma unroll
-    for (int k = 0; k < 2 * kFaceSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
-    for_each_chunk(a, win, [&](int c0, int c1, int len) {
-        float2 TA[6], UA[4][3], TB[6], UB[4][3];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) TA[k] = TB[k] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) UA[i][0] = UA[i][1] = UA[i][2] = UB[i][0] = UB[i][1] = UB[i][2] = make_float2(0.f, 0.f);
-        for (int i = c0; i < c1; i += 2) bwd_list_quad2(P2, win[i], win[i + 1], TA, UA, TB, UB);
-        const int ce = c1 < len ? c1 : len;
-        if (finite_tu(TA, UA))
-            fold_list(ks, TA, UA);
-        else
-            list_guarded(pair_face(P, 0), win, c0, ce, ks);
-        if (finite_tu(TB, UB))
-            fold_list(ksB, TB, UB);
-        else
-            list_guarded(pair_face(P, 1), win, c0, ce, ksB);
-    });
-    if (idx < a.np) {
-        const int32_t *t = a.ptopo + 8 * idx;
-        const int code = t[6];
-        float *out = a.face_grad + (int64_t)blockIdx.y * a.nf * 9;
-        if (DV_INB(t[4], a.nf, kSiteBwdFaceGrad))
-            write_face_grad_sm(pair_face(P, 0), ks, out + (int64_t)t[4] * 9, code & 63, 1.0);
-        if (DV_INB(t[5], a.nf, kSiteBwdFaceGrad))
-            write_face_grad_sm(pair_face(P, 1), ksB, out + (int64_t)t[5] * 9, (code >> 6) & 63,
-                               (code >> 12) & 1 ? -1.0 : 1.0);
-    }
-}
-
-// List adjoint: CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces. Dynamic
-// shared memory: the query window (consecutive queries in pairs, each pair as (-x0, -x1, -y0,
-// -y1), (-z0, -z1, g0, g1), so two 16-byte loads give the packed operands), then 2 x 18
-// face-sum slots per thread.
-constexpr size_t kBwdListSmem = sizeof(float4) * (kBwdWin / 2) + sizeof(float2) * 2 * kFaceSlots * kBwdThreads;
+// List adjoint (edge form): CTAs [0, pblocks) take edge-sharing face pairs, the rest single faces.
+// Dynamic shared memory: the query window (consecutive queries in pairs, each pair as (-x0, -x1,
+// -y0, -y1), (-z0, -z1, g0, g1), so two 16-byte loads give the packed operands), then 5 edges x 6
+// Kahan slots per thread.
+constexpr size_t kBwdListSmem = sizeof(float4) * (kBwdWin / 2) + sizeof(float2) * 5 * kEdgeSlots * kBwdThreads;
 
 __global__ void __launch_bounds__(kBwdThreads, 3) bwd_list_kernel(const BwdArgs a) {
     extern __shared__ __align__(16) float4 bwd_list_smem[];
     float4 *win = bwd_list_smem;
     float2(*ks)[kBwdThreads] = reinterpret_cast<float2(*)[kBwdThreads]>(bwd_list_smem + kBwdWin / 2);
     if ((int64_t)blockIdx.x < a.pblocks)
-        bwd_list_pairs(a, win, ks);
+        bwd_list_pairs_edges(a, win, ks);
     else
-        bwd_list_singles(a, win, ks);
+        bwd_list_singles_edges(a, win, ks);
 }
 
 // Once per device (mesh creation calls it, outside any stream capture): the adjoint kernels'

@@ -140,6 +140,58 @@ def test_list_gradient_odd_count_and_queries_on_the_mesh(cuda_device):
     grad_close(G, G_ref, "list odd/on-mesh", oracle.winding_grad_scale(V, F, Q, g))
 
 
+def _long_edge_mesh(y0, z0):
+    """Two faces sharing the edge A-C, with the long boundary edge A-B along x at height (y0, z0)."""
+    A, B = (-0.8, y0, z0), (0.8, y0, z0)
+    C, D = (0.1, y0 + 0.5, z0 - 0.4), (-0.5, y0 - 0.3, z0 + 0.6)
+    return np.array([A, B, C, D], dtype=np.float32), np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
+
+
+@pytest.mark.parametrize("form", ["faces", "boundary"])
+def test_gradient_queries_near_long_edges(cuda_device, form):
+    """Queries 1.5e-3 to 3e-2 from the interior of edges 1.2 to 1.6 long: there |a||b| + a.b
+    cancels in FP32 (relative error ~ eps (L / dist)^2), so the kernels take the guarded path with
+    t = |a x b|^2 / (|a||b| - a.b). List queries are placed around every edge; on the grid one row
+    runs parallel to the edge A-B at 2.2e-3 from it. Both adjoint forms: face pairs and the
+    boundary curve."""
+    backward = dv.dv_winding_backward if form == "faces" else dv.dv_winding_backward_boundary
+    h = 2.0 / 64
+    y0, z0 = -1 + 40.5 * h + 0.002, -1 + 20.5 * h + 0.001
+    V, F = _long_edge_mesh(y0, z0)
+    mesh = make_mesh(V, F, cuda_device)
+    rng = np.random.default_rng(41)
+    Vd = V.astype(np.float64)
+    pts = []
+    for i, j in ((0, 1), (1, 2), (2, 0), (2, 3), (3, 0)):
+        e = Vd[j] - Vd[i]
+        s = rng.uniform(0.1, 0.9, size=300)
+        u = rng.normal(size=(300, 3))
+        u -= np.outer(u @ e, e) / (e @ e)
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        dist = np.exp(rng.uniform(np.log(1.5e-3), np.log(3e-2), size=300))
+        pts.append(Vd[i] + s[:, None] * e + dist[:, None] * u)
+    Q = np.vstack(pts + [rng.uniform(-1, 1, size=(500, 3))]).astype(np.float32)
+    d = oracle.point_mesh_distance(V, F, Q)
+    g = _masked_upstream(len(Q), d, seed=14)
+    assert (g[:1500] != 0).sum() > 1000
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    G = backward(mesh, to_dev(g.astype(np.float32), cuda_device), queries=to_dev(Q, cuda_device)).cpu().numpy()
+    grad_close(G, G_ref, f"{form} list near long edges", oracle.winding_grad_scale(V, F, Q, g))
+
+    # grid: upstream on the 3 x 3 rows around the near row only (random upstream over the whole
+    # grid would let the far rows' terms, which cancel among themselves, set the error instead)
+    grid = dv.Grid.cube(64)
+    Qg, _, dg = oracle_grid(V, F, grid)
+    g = _masked_upstream(len(Qg), dg, seed=15)
+    row = (np.abs(Qg[:, 1] - (y0 - 0.002)) < 1e-6) & (np.abs(Qg[:, 2] - (z0 - 0.001)) < 1e-6)
+    block = (np.abs(Qg[:, 1] - (y0 - 0.002)) < 1.5 * h) & (np.abs(Qg[:, 2] - (z0 - 0.001)) < 1.5 * h)
+    g[~block] = 0.0
+    assert row.sum() == 64 and block.sum() == 576 and (g[row] != 0).sum() >= 40
+    G_ref = oracle.winding_grad(V, F, Qg, g)
+    G = backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    grad_close(G, G_ref, f"{form} grid row near a long edge", oracle.winding_grad_scale(V, F, Qg, g))
+
+
 def test_closed_mesh_gradient_is_cancellation_noise(cuda_device):
     """Closed icosphere: exact dL/dV = 0. Remove one face and the same vertices get O(1) gradients;
     the closed-mesh values must be orders of magnitude below those."""
