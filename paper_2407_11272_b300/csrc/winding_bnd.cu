@@ -121,21 +121,25 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_grid_kernel(const BndArgs 
                 const float4 *wp = reinterpret_cast<const float4 *>(wf) + p0;
                 // a row close to the edge segment goes through the guarded path (edge_t)
                 const bool near = row_near_edge(ay, az, by, bz, L2);
+                if (!near) {
 #pragma unroll 4
-                for (int p = 0; p < (near ? 0 : np); ++p) {
-                    const float4 q = wp[p];
-                    const float2 nqx = make_float2(q.x, q.y);
-                    const float2 ax = __fadd2_rn(px, nqx), bx = __fadd2_rn(rx, nqx);
-                    const float2 la2 = __ffma2_rn(ax, ax, La2), lb2 = __ffma2_rn(bx, bx, Lb2);
-                    const float2 ia = make_float2(rsqrt_approx(la2.x), rsqrt_approx(la2.y));
-                    const float2 ib = make_float2(rsqrt_approx(lb2.x), rsqrt_approx(lb2.y));
-                    const float2 De = __ffma2_rn(__fmul2_rn(la2, ia), __fmul2_rn(lb2, ib), __ffma2_rn(ax, bx, Pab2));
-                    const float2 gr = __fmul2_rn(make_float2(q.z, q.w), make_float2(rcp_approx(De.x), rcp_approx(De.y)));
-                    const float2 cp = __fmul2_rn(gr, ia), cr = __fmul2_rn(gr, ib);
-                    Sp = __fadd2_rn(Sp, cp);
-                    Sr = __fadd2_rn(Sr, cr);
-                    Xp = __ffma2_rn(cp, ax, Xp);
-                    Xr = __ffma2_rn(cr, bx, Xr);
+                    for (int p = 0; p < np; ++p) {
+                        const float4 q = wp[p];
+                        const float2 nqx = make_float2(q.x, q.y);
+                        const float2 ax = __fadd2_rn(px, nqx), bx = __fadd2_rn(rx, nqx);
+                        const float2 la2 = __ffma2_rn(ax, ax, La2), lb2 = __ffma2_rn(bx, bx, Lb2);
+                        const float2 ia = make_float2(rsqrt_approx(la2.x), rsqrt_approx(la2.y));
+                        const float2 ib = make_float2(rsqrt_approx(lb2.x), rsqrt_approx(lb2.y));
+                        const float2 De =
+                            __ffma2_rn(__fmul2_rn(la2, ia), __fmul2_rn(lb2, ib), __ffma2_rn(ax, bx, Pab2));
+                        const float2 gr =
+                            __fmul2_rn(make_float2(q.z, q.w), make_float2(rcp_approx(De.x), rcp_approx(De.y)));
+                        const float2 cp = __fmul2_rn(gr, ia), cr = __fmul2_rn(gr, ib);
+                        Sp = __fadd2_rn(Sp, cp);
+                        Sr = __fadd2_rn(Sr, cr);
+                        Xp = __ffma2_rn(cp, ax, Xp);
+                        Xr = __ffma2_rn(cr, bx, Xr);
+                    }
                 }
                 float sp = Sp.x + Sp.y, sr = Sr.x + Sr.y, xp = Xp.x + Xp.y, xr = Xr.x + Xr.y;
                 if (near || !isfinite(sp + sr + xp + xr)) {
