@@ -72,10 +72,11 @@ constexpr int kCornersIdentity = 0 | 1 << 2 | 2 << 4;
 __device__ __forceinline__ float win_nqx(const float *wf, int64_t i) { return wf[4 * (i >> 1) + (i & 1)]; }
 __device__ __forceinline__ float win_g(const float *wf, int64_t i) { return wf[4 * (i >> 1) + 2 + (i & 1)]; }
 
-// Rows of the grid are processed in windows of whole rows when a row fits the window (packed
-// pairs of queries when the row length is even); longer rows go in pieces through the guarded
-// path. visit(qy, qz, i0, xlen, packed) handles one row (or piece) whose queries sit at window
-// indices i0 .. i0 + xlen - 1.
+// Rows of the grid are processed in windows of whole rows when a row fits the window, longer
+// rows in pieces of up to kBwdWin queries. Each row (or piece) takes an even number of window
+// entries: an odd one is padded with a copy of its last query carrying g = 0, so every row runs
+// the packed path. visit(qy, qz, i0, xlen) handles one row (or piece) whose entries sit at window
+// indices i0 .. i0 + xlen - 1 (xlen even).
 template <typename RowFn>
 __device__ __forceinline__ void for_each_row(const BwdArgs &a, float *wf, RowFn &&visit) {
     const int nx = a.g.n[0], ny = a.g.n[1];
@@ -83,19 +84,23 @@ __device__ __forceinline__ void for_each_row(const BwdArgs &a, float *wf, RowFn 
     const int64_t r0 = (int64_t)blockIdx.y * a.rows_per_split;
     const int64_t r1 = r0 + a.rows_per_split < nrows ? r0 + a.rows_per_split : nrows;
     const bool whole = nx <= kBwdWin;
-    const bool packed = whole && (nx % 2 == 0);
-    const int rows_per_win = whole ? kBwdWin / nx : 1;
+    const int nxe = (nx + 1) & ~1;  // a whole row's entries (<= kBwdWin)
+    const int rows_per_win = whole ? kBwdWin / nxe : 1;
     for (int64_t rw = r0; rw < r1; rw += rows_per_win) {
         const int64_t rend = rw + rows_per_win < r1 ? rw + rows_per_win : r1;
         for (int x0 = 0; x0 < nx; x0 += kBwdWin) {
             const int xlen = whole ? nx : (nx - x0 < kBwdWin ? nx - x0 : kBwdWin);
-            const int64_t len = whole ? (rend - rw) * nx : xlen;
-            const int64_t base = rw * nx + (whole ? 0 : x0);
+            const int xle = (xlen + 1) & ~1;
+            const int len = whole ? (int)(rend - rw) * nxe : xle;
             __syncthreads();
-            for (int64_t i = threadIdx.x; i < len; i += kBwdThreads) {
-                const int ix = whole ? (int)(i % nx) : x0 + (int)i;
+            for (int i = threadIdx.x; i < len; i += kBwdThreads) {
+                const int rr = whole ? i / nxe : 0;
+                const int k = i - rr * nxe;  // entry within the row (piece)
+                const bool pad = k >= xlen;
+                const int ix = x0 + (pad ? xlen - 1 : k);
+                const int64_t q = (rw + rr) * nx + ix;
                 wf[4 * (i >> 1) + (i & 1)] = -__fmaf_rn((float)ix + 0.5f, a.g.h[0], a.g.lo[0]);
-                wf[4 * (i >> 1) + 2 + (i & 1)] = DV_INB(base + i, a.nq, kSiteBwdUpstream) ? a.upstream[base + i] : 0.f;
+                wf[4 * (i >> 1) + 2 + (i & 1)] = !pad && DV_INB(q, a.nq, kSiteBwdUpstream) ? a.upstream[q] : 0.f;
             }
             __syncthreads();
             const int64_t nr = whole ? rend - rw : 1;
@@ -104,7 +109,7 @@ __device__ __forceinline__ void for_each_row(const BwdArgs &a, float *wf, RowFn 
                 const int iy = (int)(row % ny), iz = (int)(row / ny);
                 const float qy = __fmaf_rn((float)iy + 0.5f, a.g.h[1], a.g.lo[1]);
                 const float qz = __fmaf_rn((float)iz + 0.5f, a.g.h[2], a.g.lo[2]);
-                visit(qy, qz, whole ? rr * nx : (int64_t)0, xlen, packed);
+                visit(qy, qz, whole ? rr * nxe : (int64_t)0, xle);
             }
             if (whole) break;
         }
@@ -193,11 +198,10 @@ __device__ __forceinline__ void edges_row2(const EdgeRowConst<NP, NE> &C, const 
     }
 }
 
-// The guarded scalar path of one row (or piece) and one edge: rows with an odd number of queries,
-// pieces of long rows, rows that pass close to one of the thread's edges (t from edge_t), and rows
-// whose packed sums are not finite (a query at an endpoint or on the edge segment, where the
-// derivative does not exist: those pairs are skipped). Returns the row's S_p, sum g c_p a_x, S_r,
-// sum g c_r b_x.
+// The guarded scalar path of one row (or piece) and one edge: rows that pass close to one of the
+// thread's edges (t from edge_t) and rows whose packed sums are not finite (a query at an endpoint
+// or on the edge segment, where the derivative does not exist: those pairs are skipped). Returns
+// the row's S_p, sum g c_p a_x, S_r, sum g c_r b_x.
 __device__ __noinline__ float4 edge_row_guarded(float px, float py, float pz, float rx, float ry, float rz, float qy,
                                                float qz, const float *wf, int64_t i0, int xlen) {
     const float ay = py - qy, az = pz - qz, by = ry - qy, bz = rz - qz;
@@ -261,7 +265,7 @@ __device__ __forceinline__ void edges_all_rows(const BwdArgs &a, float *wf, floa
                                                const float (&X)[NP], const float (&Y)[NP], const float (&Z)[NP]) {
 #pragma unroll
     for (int k = 0; k < kEdgeSlots * NE; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
-    for_each_row(a, wf, [&](float qy, float qz, int64_t i0, int xlen, bool packed) {
+    for_each_row(a, wf, [&](float qy, float qz, int64_t i0, int xlen) {
         float y[NP], z[NP];
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
@@ -276,7 +280,7 @@ __device__ __forceinline__ void edges_all_rows(const BwdArgs &a, float *wf, floa
             near |= row_near_edge(y[s], z[s], y[e], z[e], fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         }
         bool ok = false;
-        if (packed && !near) {
+        if (!near) {
             EdgeRowConst<NP, NE> C;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
