@@ -74,7 +74,7 @@ EXECUTED = {
                                        "c21070f8ec6075ccb701b639ef36e42e75799744f8df52c1773f722b409f7a49"),
     # 8.374e13 FP32 lane ops / (16 777 216 x 204 020) pairs, one full-size launch (edge form)
     ("sh_sphere", "bwd_grid"): (24.47, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "468a7ccefb223fa0f6b309cd18fb7c75d874ebdcf8e66ee093344ff7e66b2193"),
+                                "d5776d1ca44e4f0b60fc0584e5e03a440a6cf194e2c5e3ae149b9e20aaed8f65"),
     # 3.351e9 FP64 ops / (480 flagged queries x 205 030 events)
     ("sh_sphere", "reeval_fp64"): (34.05, "paper_2407_11272_b300/csrc/winding_fp64.cu",
                                    "8c594e484ada6aa7cf91bbf908944d2813b8df3c27fe0c9620151088ab2747b9"),
@@ -84,10 +84,10 @@ EXECUTED = {
 # the dominant kernel on the full workload, keyed by (workload, kernel), with the same source
 # digest rule as EXECUTED.
 TRAFFIC = {
-    # 87 569 408 B read + 23 217 408 B written, one full-size launch (799 x 5 CTAs);
+    # 87 512 576 B read + 22 927 616 B written, one full-size launch (799 x 5 CTAs);
     # profiles/bwd_grid_shsphere_256_dram.md
-    ("shsphere_256", "bwd_grid"): (110786816, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                   "468a7ccefb223fa0f6b309cd18fb7c75d874ebdcf8e66ee093344ff7e66b2193"),
+    ("shsphere_256", "bwd_grid"): (110440192, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                   "d5776d1ca44e4f0b60fc0584e5e03a440a6cf194e2c5e3ae149b9e20aaed8f65"),
 }
 
 ACC_QUERIES = 100_000  # seeded voxel-centre sample of the accuracy block
