@@ -87,23 +87,26 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_grid_kernel(const BndArgs 
     const int64_t r1 = r0 + a.per_split < nrows ? r0 + a.per_split : nrows;
 #pragma unroll
     for (int k = 0; k < kBndSlots; ++k) ks[k][threadIdx.x] = make_float2(0.f, 0.f);
-    const bool whole = nx <= kBndWin && nx % 2 == 0;
-    const int rows_per_win = whole ? kBndWin / nx : 1;
+    // Whole rows per window when a row fits, else pieces of up to kBndWin queries; each row (or
+    // piece) takes an even number of entries, an odd one padded with a copy of its last query
+    // carrying g = 0, so every row runs the packed loop.
+    const bool whole = nx <= kBndWin;
+    const int nxe = (nx + 1) & ~1;
+    const int rows_per_win = whole ? kBndWin / nxe : 1;
     for (int64_t rw = r0; rw < r1; rw += rows_per_win) {
         const int64_t rend = rw + rows_per_win < r1 ? rw + rows_per_win : r1;
         for (int x0 = 0; x0 < nx; x0 += kBndWin) {
             const int xlen = whole ? nx : (nx - x0 < kBndWin ? nx - x0 : kBndWin);
-            const int64_t len = whole ? (rend - rw) * nx : xlen;
-            const int64_t base = rw * nx + (whole ? 0 : x0);
+            const int xle = (xlen + 1) & ~1;
+            const int len = whole ? (int)(rend - rw) * nxe : xle;
             __syncthreads();
-            for (int64_t i = threadIdx.x; i < len; i += kBndThreads) {
-                const int ix = whole ? (int)(i % nx) : x0 + (int)i;
+            for (int i = threadIdx.x; i < len; i += kBndThreads) {
+                const int rr = whole ? i / nxe : 0;
+                const int k = i - rr * nxe;
+                const bool pad = k >= xlen;
+                const int ix = x0 + (pad ? xlen - 1 : k);
                 wf[4 * (i >> 1) + (i & 1)] = -__fmaf_rn((float)ix + 0.5f, a.g.h[0], a.g.lo[0]);
-                wf[4 * (i >> 1) + 2 + (i & 1)] = a.upstream[base + i];
-            }
-            if (!whole && (len & 1) && threadIdx.x == 0) {  // pad an odd piece with g = 0
-                wf[4 * (len >> 1) + 1] = -__fmaf_rn((float)(x0 + len - 1) + 0.5f, a.g.h[0], a.g.lo[0]);
-                wf[4 * (len >> 1) + 3] = 0.f;
+                wf[4 * (i >> 1) + 2 + (i & 1)] = pad ? 0.f : a.upstream[(rw + rr) * nx + ix];
             }
             __syncthreads();
             const int64_t nr = whole ? rend - rw : 1;
@@ -116,8 +119,8 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_grid_kernel(const BndArgs 
                 const float La = fmaf(ay, ay, az * az), Lb = fmaf(by, by, bz * bz), Pab = fmaf(ay, by, az * bz);
                 const float2 La2 = make_float2(La, La), Lb2 = make_float2(Lb, Lb), Pab2 = make_float2(Pab, Pab);
                 float2 Sp = make_float2(0.f, 0.f), Sr = Sp, Xp = Sp, Xr = Sp;  // X = sum g c a_x (b_x)
-                const int64_t p0 = whole ? rr * nx / 2 : 0;
-                const int np = whole ? nx / 2 : (int)((len + 1) / 2);
+                const int64_t p0 = whole ? rr * nxe / 2 : 0;
+                const int np = xle / 2;
                 const float4 *wp = reinterpret_cast<const float4 *>(wf) + p0;
                 // a row close to the edge segment goes through the guarded path (edge_t)
                 const bool near = row_near_edge(ay, az, by, bz, L2);
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(kBndThreads, 4) bnd_grid_kernel(const BndArgs 
                     // near the segment, or a query on an endpoint or on the segment (those pairs
                     // are skipped)
                     sp = sr = xp = xr = 0.f;
-                    const int cnt = whole ? nx : (int)len;
+                    const int cnt = xle;  // the padding entries carry g = 0
                     for (int i = 0; i < cnt; ++i) {
                         const int64_t wi = 2 * p0 + i;
                         const float nqxs = wf[4 * (wi >> 1) + (wi & 1)], gs = wf[4 * (wi >> 1) + 2 + (wi & 1)];
