@@ -165,25 +165,43 @@ struct EdgeRowConst {
     float2 P[NE];   // (y_p - qy)(y_r - qy) + (z_p - qz)(z_r - qz) of each edge
 };
 
-// One row (or piece) of packed query pairs from the window: every edge's four sums.
+// One row (or piece) of packed query pairs from the window: every edge's four sums. Software
+// pipelined: the next pair's offsets, squared distances and MUFU reciprocal square roots are
+// issued before the current pair's edge work.
 template <int NP, int NE>
 __device__ __forceinline__ void edges_row2(const EdgeRowConst<NP, NE> &C, const float *wf, int64_t i0, int xlen,
                                            EdgeRow2 (&R)[NE]) {
 #pragma unroll
     for (int k = 0; k < NE; ++k) R[k].Sp = R[k].Xp = R[k].Sr = R[k].Xr = make_float2(0.f, 0.f);
     const float4 *wp = reinterpret_cast<const float4 *>(wf) + (i0 >> 1);
-#pragma unroll 2
-    for (int p = 0; p < xlen / 2; ++p) {
-        const float4 q = wp[p];
-        const float2 nqx = make_float2(q.x, q.y), g = make_float2(q.z, q.w);
-        float2 x[NP], l[NP], iv[NP];
+    const int n = xlen / 2;
+    float2 x[NP], m[NP], iv[NP], g;
+    {
+        const float4 q = wp[0];
+        const float2 nqx = make_float2(q.x, q.y);
+        g = make_float2(q.z, q.w);
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             x[k] = __fadd2_rn(C.px[k], nqx);
-            const float2 m = __ffma2_rn(x[k], x[k], C.L[k]);
-            iv[k] = make_float2(rsqrt_approx(m.x), rsqrt_approx(m.y));
-            l[k] = __fmul2_rn(m, iv[k]);
+            m[k] = __ffma2_rn(x[k], x[k], C.L[k]);
+            iv[k] = make_float2(rsqrt_approx(m[k].x), rsqrt_approx(m[k].y));
         }
+    }
+#pragma unroll 1
+    for (int p = 0; p < n; ++p) {
+        // next pair (the last iteration recomputes its own pair; its results are not used)
+        const float4 qn = wp[p + 1 < n ? p + 1 : p];
+        const float2 nqxn = make_float2(qn.x, qn.y), gn = make_float2(qn.z, qn.w);
+        float2 xn[NP], mn[NP], ivn[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            xn[k] = __fadd2_rn(C.px[k], nqxn);
+            mn[k] = __ffma2_rn(xn[k], xn[k], C.L[k]);
+            ivn[k] = make_float2(rsqrt_approx(mn[k].x), rsqrt_approx(mn[k].y));
+        }
+        float2 l[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) l[k] = __fmul2_rn(m[k], iv[k]);
 #pragma unroll
         for (int k = 0; k < NE; ++k) {
             const int s = edge_start<NP>(k), e = edge_end<NP>(k);
@@ -195,6 +213,13 @@ __device__ __forceinline__ void edges_row2(const EdgeRowConst<NP, NE> &C, const 
             R[k].Sr = __fadd2_rn(R[k].Sr, cr);
             R[k].Xr = __ffma2_rn(cr, x[e], R[k].Xr);
         }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            x[k] = xn[k];
+            m[k] = mn[k];
+            iv[k] = ivn[k];
+        }
+        g = gn;
     }
 }
 
