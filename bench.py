@@ -72,9 +72,9 @@ EXECUTED = {
     # 8.255e11 FP32 lane ops / (262 144 x 204 020) pairs; profiles/hot_kernels_shsphere_64_ncu.md
     ("sh_sphere", "fwd_strip_kahan"): (15.44, "paper_2407_11272_b300/csrc/winding_fwd.cu",
                                        "c21070f8ec6075ccb701b639ef36e42e75799744f8df52c1773f722b409f7a49"),
-    # 8.374e13 FP32 lane ops / (16 777 216 x 204 020) pairs, one full-size launch (edge form)
-    ("sh_sphere", "bwd_grid"): (24.47, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "d5776d1ca44e4f0b60fc0584e5e03a440a6cf194e2c5e3ae149b9e20aaed8f65"),
+    # 8.385e13 FP32 lane ops / (16 777 216 x 204 020) pairs, one full-size launch (edge form)
+    ("sh_sphere", "bwd_grid"): (24.50, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                "9c11178ac22c2883d2b7fc0a78864a2a86dc5125a5e46d6b099110ff2403634e"),
     # 3.351e9 FP64 ops / (480 flagged queries x 205 030 events)
     ("sh_sphere", "reeval_fp64"): (34.05, "paper_2407_11272_b300/csrc/winding_fp64.cu",
                                    "8c594e484ada6aa7cf91bbf908944d2813b8df3c27fe0c9620151088ab2747b9"),
@@ -84,10 +84,10 @@ EXECUTED = {
 # the dominant kernel on the full workload, keyed by (workload, kernel), with the same source
 # digest rule as EXECUTED.
 TRAFFIC = {
-    # 87 512 576 B read + 22 927 616 B written, one full-size launch (799 x 5 CTAs);
+    # 87 950 080 B read + 22 867 712 B written, one full-size launch (799 x 5 CTAs);
     # profiles/bwd_grid_shsphere_256_dram.md
-    ("shsphere_256", "bwd_grid"): (110440192, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                   "d5776d1ca44e4f0b60fc0584e5e03a440a6cf194e2c5e3ae149b9e20aaed8f65"),
+    ("shsphere_256", "bwd_grid"): (110817792, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                   "9c11178ac22c2883d2b7fc0a78864a2a86dc5125a5e46d6b099110ff2403634e"),
 }
 
 ACC_QUERIES = 100_000  # seeded voxel-centre sample of the accuracy block

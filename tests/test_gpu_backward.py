@@ -147,17 +147,20 @@ def _long_edge_mesh(y0, z0):
     return np.array([A, B, C, D], dtype=np.float32), np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
 
 
+_H64 = 2.0 / 64
+_Y0, _Z0 = -1 + 40.5 * _H64 + 0.002, -1 + 20.5 * _H64 + 0.001  # 2.2e-3 from a row of the 64^2 (y, z) grid
+
+
+def _backward_form(form):
+    return dv.dv_winding_backward if form == "faces" else dv.dv_winding_backward_boundary
+
+
 @pytest.mark.parametrize("form", ["faces", "boundary"])
 def test_gradient_queries_near_long_edges(cuda_device, form):
-    """Queries 1.5e-3 to 3e-2 from the interior of edges 1.2 to 1.6 long: there |a||b| + a.b
+    """List queries 1.5e-3 to 3e-2 from the interior of edges 1.2 to 1.6 long: there |a||b| + a.b
     cancels in FP32 (relative error ~ eps (L / dist)^2), so the kernels take the guarded path with
-    t = |a x b|^2 / (|a||b| - a.b). List queries are placed around every edge; on the grid one row
-    runs parallel to the edge A-B at 2.2e-3 from it. Both adjoint forms: face pairs and the
-    boundary curve."""
-    backward = dv.dv_winding_backward if form == "faces" else dv.dv_winding_backward_boundary
-    h = 2.0 / 64
-    y0, z0 = -1 + 40.5 * h + 0.002, -1 + 20.5 * h + 0.001
-    V, F = _long_edge_mesh(y0, z0)
+    t = |a x b|^2 / (|a||b| - a.b). Both adjoint forms: face pairs and the boundary curve."""
+    V, F = _long_edge_mesh(_Y0, _Z0)
     mesh = make_mesh(V, F, cuda_device)
     rng = np.random.default_rng(41)
     Vd = V.astype(np.float64)
@@ -175,21 +178,30 @@ def test_gradient_queries_near_long_edges(cuda_device, form):
     g = _masked_upstream(len(Q), d, seed=14)
     assert (g[:1500] != 0).sum() > 1000
     G_ref = oracle.winding_grad(V, F, Q, g)
-    G = backward(mesh, to_dev(g.astype(np.float32), cuda_device), queries=to_dev(Q, cuda_device)).cpu().numpy()
+    G = _backward_form(form)(mesh, to_dev(g.astype(np.float32), cuda_device),
+                             queries=to_dev(Q, cuda_device)).cpu().numpy()
     grad_close(G, G_ref, f"{form} list near long edges", oracle.winding_grad_scale(V, F, Q, g))
 
-    # grid: upstream on the 3 x 3 rows around the near row only (random upstream over the whole
-    # grid would let the far rows' terms, which cancel among themselves, set the error instead)
-    grid = dv.Grid.cube(64)
+
+@pytest.mark.parametrize("form", ["faces", "boundary"])
+@pytest.mark.parametrize("nx", [64, 65])
+def test_gradient_grid_row_near_a_long_edge(cuda_device, form, nx):
+    """A grid row parallel to the edge A-B (length 1.6) at 2.2e-3 from it, even and odd row
+    lengths (an odd row is padded in the adjoint's window). Upstream on the 3 x 3 rows around it
+    only: random upstream over the whole grid would let the far rows' terms, which cancel among
+    themselves, set the error instead."""
+    V, F = _long_edge_mesh(_Y0, _Z0)
+    mesh = make_mesh(V, F, cuda_device)
+    grid = dv.Grid(n=(nx, 64, 64), lo=(-1.0,) * 3, hi=(1.0,) * 3)
     Qg, _, dg = oracle_grid(V, F, grid)
     g = _masked_upstream(len(Qg), dg, seed=15)
-    row = (np.abs(Qg[:, 1] - (y0 - 0.002)) < 1e-6) & (np.abs(Qg[:, 2] - (z0 - 0.001)) < 1e-6)
-    block = (np.abs(Qg[:, 1] - (y0 - 0.002)) < 1.5 * h) & (np.abs(Qg[:, 2] - (z0 - 0.001)) < 1.5 * h)
+    row = (np.abs(Qg[:, 1] - (_Y0 - 0.002)) < 1e-6) & (np.abs(Qg[:, 2] - (_Z0 - 0.001)) < 1e-6)
+    block = (np.abs(Qg[:, 1] - (_Y0 - 0.002)) < 1.5 * _H64) & (np.abs(Qg[:, 2] - (_Z0 - 0.001)) < 1.5 * _H64)
     g[~block] = 0.0
-    assert row.sum() == 64 and block.sum() == 576 and (g[row] != 0).sum() >= 40
+    assert row.sum() == nx and block.sum() == 9 * nx and (g[row] != 0).sum() >= 40
     G_ref = oracle.winding_grad(V, F, Qg, g)
-    G = backward(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
-    grad_close(G, G_ref, f"{form} grid row near a long edge", oracle.winding_grad_scale(V, F, Qg, g))
+    G = _backward_form(form)(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    grad_close(G, G_ref, f"{form} grid row near a long edge (nx={nx})", oracle.winding_grad_scale(V, F, Qg, g))
 
 
 def test_closed_mesh_gradient_is_cancellation_noise(cuda_device):
