@@ -1,8 +1,8 @@
 """Child process of test_gpu_debug_bounds.py: with DV_DEBUG=1 the binding loads the bounds-checked
 debug library. Runs the instrumented entry points on small inputs (ragged grid, split event
-ranges, query lists with queries on the mesh, all precisions, both adjoints, the Eq. 4 kernels,
-one batch) and prints one JSON line: the debug library's bounds report and the largest errors
-against the FP64 oracle."""
+ranges, query lists with queries on the mesh, all precisions, both adjoints on odd rows and on
+rows longer than the adjoint's window, the Eq. 4 kernels, one batch) and prints one JSON line:
+the debug library's bounds report and the largest errors against the FP64 oracle."""
 import json
 import os
 import sys
@@ -47,6 +47,16 @@ def main():
     for name, fn in (("face", dv.dv_winding_backward), ("boundary", dv.dv_winding_backward_boundary)):
         G = fn(mesh, gd, grid=grid).cpu().numpy().astype(np.float64)
         out["errors"][f"grad_grid_{name}"] = float(np.linalg.norm(G - G64) / np.linalg.norm(G64))
+    # rows longer than the adjoint's window: a full piece of 2048 queries and an odd piece of one
+    grid_l = dv.Grid((2049, 3, 2), (-1.0, -0.9, -0.5), (1.0, 0.9, 0.5))
+    Qr = oracle.grid_queries(grid_l.lo, grid_l.hi, grid_l.n)
+    gr = meshgen.upstream_gradient(grid_l.num_queries, seed=4).astype(np.float64)
+    gr *= oracle.point_mesh_distance(V, F, Qr) > 1e-3
+    Gr64 = oracle.winding_grad(V, F, Qr, gr)
+    grd = torch.from_numpy(gr.astype(np.float32)).to(dev)
+    for name, fn in (("face", dv.dv_winding_backward), ("boundary", dv.dv_winding_backward_boundary)):
+        G = fn(mesh, grd, grid=grid_l).cpu().numpy().astype(np.float64)
+        out["errors"][f"grad_long_rows_{name}"] = float(np.linalg.norm(G - Gr64) / np.linalg.norm(Gr64))
     gl = rng.normal(size=len(Ql)) * farl
     Gl64 = oracle.winding_grad(V, F, Ql, gl)
     Gl = dv.dv_winding_backward(mesh, torch.from_numpy(gl.astype(np.float32)).to(dev),

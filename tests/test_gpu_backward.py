@@ -204,6 +204,24 @@ def test_gradient_grid_row_near_a_long_edge(cuda_device, form, nx):
     grad_close(G, G_ref, f"{form} grid row near a long edge (nx={nx})", oracle.winding_grad_scale(V, F, Qg, g))
 
 
+@pytest.mark.parametrize("form", ["faces", "boundary"])
+@pytest.mark.parametrize("n", [(1, 1, 1), (1, 7, 9), (3, 5, 2), (2049, 2, 2)])
+def test_grid_gradient_degenerate_shapes(cuda_device, n, form):
+    """Grids one cell wide (every row is one query and one g = 0 padding entry), tiny grids, and
+    rows of 2049 queries (a full window piece and an odd piece of one), on an open mesh."""
+    V, F = meshgen.icosphere(2, 0.6)
+    F = F[7:]
+    grid = dv.Grid(n, (-0.9, -0.8, -0.7), (0.8, 0.9, 0.6))
+    Q, _, d = oracle_grid(V, F, grid)
+    g = _masked_upstream(len(Q), d, seed=16)
+    assert (g != 0).any()
+    G_ref = oracle.winding_grad(V, F, Q, g)
+    mesh = make_mesh(V, F, cuda_device)
+    G = _backward_form(form)(mesh, to_dev(g.astype(np.float32), cuda_device), grid=grid).cpu().numpy()
+    assert np.all(np.isfinite(G))
+    grad_close(G, G_ref, f"{form} grid {n}", oracle.winding_grad_scale(V, F, Q, g))
+
+
 def test_closed_mesh_gradient_is_cancellation_noise(cuda_device):
     """Closed icosphere: exact dL/dV = 0. Remove one face and the same vertices get O(1) gradients;
     the closed-mesh values must be orders of magnitude below those."""

@@ -29,7 +29,8 @@ def test_debug_build_reports_no_out_of_range_access(cuda_device):
     for k in ("grid_fp32", "grid_kahan", "grid_mixed", "list_kahan", "list_mixed"):
         assert e[k] <= 1e-4, (k, e[k])
     assert e["grid_fp16"] <= 1e-2
-    for k in ("grad_grid_face", "grad_grid_boundary", "grad_list_face"):
+    for k in ("grad_grid_face", "grad_grid_boundary", "grad_long_rows_face", "grad_long_rows_boundary",
+              "grad_list_face"):
         assert e[k] <= 1e-3, (k, e[k])
     assert e["dipole"] <= 1e-4
     assert e["batch_occ_mismatch"] == 0
