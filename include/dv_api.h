@@ -241,9 +241,14 @@ dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_ou
 /* Adjoint: d_dverts float32 [nv][3] is OVERWRITTEN with
  *     sum_q d_upstream[q] * dw(q)/dV,
  * the derivative of Eq. (5) with Eq. (7) (the paper claims differentiability,
- * §1 and §2.4, but gives no formula; this is the analytic chain rule).
- * Queries as in dv_winding (list or grid), d_upstream float32 [nq].
- * FP32 per-pair arithmetic, FP64 cross-block reduction; deterministic
+ * §1 and §2.4, but gives no formula). Every (query, face) pair is evaluated:
+ * each face's derivative is summed over its three directed edges p -> r
+ * (a = p - q, b = r - q): dOmega/dp += (b x a) / (|a| (|a||b| + a.b)),
+ * dOmega/dr += (b x a) / (|b| (|a||b| + a.b)), equal to the chain rule through
+ * Eq. (7) for q off the face; a query on a face's edge or vertex contributes
+ * nothing through that face. Queries as in dv_winding (list or grid),
+ * d_upstream float32 [nq]. FP32 per-pair arithmetic (|a||b| + a.b formed without
+ * cancellation near an edge segment), FP64 cross-block reduction; deterministic
  * (no floating-point atomics). Stream-ordered, no sync. */
 dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                               const float *d_upstream, float *d_dverts, void *stream);
