@@ -245,8 +245,9 @@ dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_ou
  * each face's derivative is summed over its three directed edges p -> r
  * (a = p - q, b = r - q): dOmega/dp += (b x a) / (|a| (|a||b| + a.b)),
  * dOmega/dr += (b x a) / (|b| (|a||b| + a.b)), equal to the chain rule through
- * Eq. (7) for q off the face; a query on a face's edge or vertex contributes
- * nothing through that face. Queries as in dv_winding (list or grid),
+ * Eq. (7) for q off the face; the terms of an edge whose segment contains the
+ * query (the derivative does not exist there) are skipped. Queries as in
+ * dv_winding (list or grid),
  * d_upstream float32 [nq]. FP32 per-pair arithmetic (|a||b| + a.b formed without
  * cancellation near an edge segment), FP64 cross-block reduction; deterministic
  * (no floating-point atomics). Stream-ordered, no sync. */
