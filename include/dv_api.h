@@ -247,10 +247,10 @@ dv_status dv_voxelize_grid(const dv_mesh *mesh, const dv_grid *grid, float *d_ou
  * dOmega/dr += (b x a) / (|b| (|a||b| + a.b)), equal to the chain rule through
  * Eq. (7) for q off the face; the terms of an edge whose segment contains the
  * query (the derivative does not exist there) are skipped. Queries as in
- * dv_winding (list or grid),
- * d_upstream float32 [nq]. FP32 per-pair arithmetic (|a||b| + a.b formed without
- * cancellation near an edge segment), FP64 cross-block reduction; deterministic
- * (no floating-point atomics). Stream-ordered, no sync. */
+ * dv_winding (list or grid), d_upstream float32 [nq]. FP32 per-pair arithmetic
+ * (|a||b| + a.b formed without cancellation near an edge segment), FP64
+ * cross-block reduction; deterministic (no floating-point atomics).
+ * Stream-ordered, no sync. */
 dv_status dv_winding_backward(const dv_mesh *mesh, const float *d_queries, int64_t nq, const dv_grid *grid,
                               const float *d_upstream, float *d_dverts, void *stream);
 
