@@ -183,6 +183,33 @@ __device__ __forceinline__ float edge_t(float ax, float ay, float az, float la, 
     return fmaf(wx, wx, fmaf(wy, wy, wz * wz)) / fmaf(la, lb, -ab);
 }
 
+// edge_t with a MUFU reciprocal in place of the division.
+__device__ __forceinline__ float edge_t_approx(float ax, float ay, float az, float la, float lb, float ab, float dx,
+                                               float dy, float dz) {
+    if (ab >= 0.f) return fmaf(la, lb, ab);
+    const float wx = fmaf(ay, dz, -az * dy), wy = fmaf(az, dx, -ax * dz), wz = fmaf(ax, dy, -ay * dx);
+    return fmaf(wx, wx, fmaf(wy, wy, wz * wz)) * rcp_approx(fmaf(la, lb, -ab));
+}
+
+// Per-pair coefficients of the guarded paths of the list and boundary-form adjoints, from MUFU
+// approximations (the cancellation near the segment is handled by edge_t's form, not by IEEE
+// rounding): for a = p - q, b = r - q with squared lengths la2, lb2, sets ia = 1/|a|, ib = 1/|b|
+// and c = g / t; returns false (skip the pair) for q within 1e-15 of an endpoint or on the
+// segment, where the derivative does not exist. (The grid adjoint's guarded path keeps IEEE
+// square roots and divisions: the same change there slowed that kernel's packed path.)
+__device__ __forceinline__ bool edge_coeffs(float ax, float ay, float az, float bx, float by, float bz, float la2,
+                                            float lb2, float dx, float dy, float dz, float g, float &ia, float &ib,
+                                            float &c) {
+    if (!(la2 > 1e-30f) || !(lb2 > 1e-30f)) return false;
+    ia = rsqrt_approx(la2);
+    ib = rsqrt_approx(lb2);
+    const float la = la2 * ia, lb = lb2 * ib;
+    const float t = edge_t_approx(ax, ay, az, la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)), dx, dy, dz);
+    if (!(t > 1e-30f * la * lb) || !(t >= 1.2e-38f)) return false;
+    c = g * rcp_approx(t);
+    return true;
+}
+
 // Whether the grid row through (qy, qz) passes within kNearEdge |r - p| of the segment p -> r, from
 // the row's offsets (ys, zs) = (p_y - qy, p_z - qz), (ye, ze) likewise for r, and the edge's squared
 // length L2: the row is a line along x, so its distance to the segment is the distance from the

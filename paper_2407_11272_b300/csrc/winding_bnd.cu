@@ -62,13 +62,10 @@ __device__ __forceinline__ void bnd_pair_guarded(float ax, float ay, float az, f
                                                  float &crq) {
     const float la2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
     const float lb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-    if (!(la2 > 0.f) || !(lb2 > 0.f)) return;
-    const float la = sqrtf(la2), lb = sqrtf(lb2);
-    const float De = edge_t(ax, ay, az, la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)), dx, dy, dz);
-    if (!(De > 1e-30f * la * lb)) return;
-    const float gr = g / De;
-    cpq = gr / la;
-    crq = gr / lb;
+    float ia, ib, gr;
+    if (!edge_coeffs(ax, ay, az, bx, by, bz, la2, lb2, dx, dy, dz, g, ia, ib, gr)) return;
+    cpq = gr * ia;
+    crq = gr * ib;
     sp += cpq;
     sr += crq;
 }

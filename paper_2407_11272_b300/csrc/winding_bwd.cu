@@ -565,11 +565,9 @@ __device__ __noinline__ Edge6 edge_chunk_guarded(float px, float py, float pz, f
         const float4 q = list_query(win, i);  // (-x, -y, -z, g)
         const float ax = px + q.x, ay = py + q.y, az = pz + q.z, bx = rx + q.x, by = ry + q.y, bz = rz + q.z;
         const float la2 = fmaf(ax, ax, fmaf(ay, ay, az * az)), lb2 = fmaf(bx, bx, fmaf(by, by, bz * bz));
-        if (!(la2 > 0.f) || !(lb2 > 0.f)) continue;
-        const float la = sqrtf(la2), lb = sqrtf(lb2);
-        const float t = edge_t(ax, ay, az, la, lb, fmaf(ax, bx, fmaf(ay, by, az * bz)), dx, dy, dz);
-        if (!(t > 1e-30f * la * lb)) continue;
-        const float c = q.w / t, cp = c / la, cr = c / lb;
+        float ia, ib, c;
+        if (!edge_coeffs(ax, ay, az, bx, by, bz, la2, lb2, dx, dy, dz, q.w, ia, ib, c)) continue;
+        const float cp = c * ia, cr = c * ib;
         o.v[0] = fmaf(cp, ax, o.v[0]);
         o.v[1] = fmaf(cp, ay, o.v[1]);
         o.v[2] = fmaf(cp, az, o.v[2]);
