@@ -74,7 +74,7 @@ EXECUTED = {
                                        "c21070f8ec6075ccb701b639ef36e42e75799744f8df52c1773f722b409f7a49"),
     # 8.385e13 FP32 lane ops / (16 777 216 x 204 020) pairs, one full-size launch (edge form)
     ("sh_sphere", "bwd_grid"): (24.50, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                "9c11178ac22c2883d2b7fc0a78864a2a86dc5125a5e46d6b099110ff2403634e"),
+                                "6f0f6bd10313ca5aca21cd9b85b164b93a52b8b61bc2d9fca3480a979991b8f6"),
     # 3.351e9 FP64 ops / (480 flagged queries x 205 030 events)
     ("sh_sphere", "reeval_fp64"): (34.05, "paper_2407_11272_b300/csrc/winding_fp64.cu",
                                    "8c594e484ada6aa7cf91bbf908944d2813b8df3c27fe0c9620151088ab2747b9"),
@@ -84,10 +84,10 @@ EXECUTED = {
 # the dominant kernel on the full workload, keyed by (workload, kernel), with the same source
 # digest rule as EXECUTED.
 TRAFFIC = {
-    # 87 950 080 B read + 22 867 712 B written, one full-size launch (799 x 5 CTAs);
+    # 87 481 600 B read + 23 069 440 B written, one full-size launch (799 x 5 CTAs);
     # profiles/bwd_grid_shsphere_256_dram.md
-    ("shsphere_256", "bwd_grid"): (110817792, "paper_2407_11272_b300/csrc/winding_bwd.cu",
-                                   "9c11178ac22c2883d2b7fc0a78864a2a86dc5125a5e46d6b099110ff2403634e"),
+    ("shsphere_256", "bwd_grid"): (110551040, "paper_2407_11272_b300/csrc/winding_bwd.cu",
+                                   "6f0f6bd10313ca5aca21cd9b85b164b93a52b8b61bc2d9fca3480a979991b8f6"),
 }
 
 ACC_QUERIES = 100_000  # seeded voxel-centre sample of the accuracy block
